@@ -1,0 +1,291 @@
+"""FP64 CPU oracle of the downsampled STFT-based synchrosqueezing transform.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain reference the CUDA
+path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it;
+the product library never does, and it shares no code with it.
+
+The arithmetic lives in ``sst_oracle.c`` (plain C, double precision, its own
+radix-2 FFT); this module only marshals numpy arrays through ctypes and maps
+the user-level band in Hz to DFT bins.  Each function names the equation of
+He & Cao (arXiv 2003.07065) it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import sys
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sst_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libsst_oracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build`` (git-ignored)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    lib.oro_window.argtypes = [_int, ctypes.c_double, _dp, _dp]
+    lib.oro_fft.argtypes = [_dp, _dp, _i64, _int]
+    lib.oro_frames.argtypes = [_i64, _int]
+    lib.oro_frames.restype = _i64
+    lib.oro_stft.argtypes = [_dp, _i64, _dp, _dp, _int, _int, _int, _i64, _i64,
+                             _int, _int, _dp, _dp]
+    lib.oro_reassign.argtypes = [_dp, _dp, _i64, _int, _int, _int, _int,
+                                 ctypes.c_double, _dp, _ip, _dp, _dp]
+    lib.oro_normaliser.argtypes = [_dp, _int, _int, _i64, _i64, _i64, _int, _dp]
+    lib.oro_inverse.argtypes = [_dp, _i64, _i64, _int, _int, _int, _int, _dp,
+                                _int, _int, _i64, _i64, _i64, _int, _dp]
+    lib.oro_colsum.argtypes = [_dp, _i64, _int, _int, _int, _int,
+                               ctypes.c_double, _dp]
+    for name in ("oro_sigma_f",):
+        getattr(lib, name).argtypes = [ctypes.c_double]
+        getattr(lib, name).restype = ctypes.c_double
+    for name in ("oro_hf_max_rule1", "oro_hf_max_rule2"):
+        getattr(lib, name).argtypes = [ctypes.c_double] * 3
+        getattr(lib, name).restype = ctypes.c_double
+    lib.oro_delta_f.argtypes = [ctypes.c_double, _int, _int]
+    lib.oro_delta_f.restype = ctypes.c_double
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _c(a, dtype=np.float64) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _cx(a: np.ndarray) -> np.ndarray:
+    """complex128 array -> interleaved float64 view (contiguous)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.view(np.float64)
+
+
+# ---------------------------------------------------------------- primitives
+def window(L: int, sigma: float):
+    """Gaussian g (Sec. 2.1) and g' (Sec. 2.2) on j = -M..M, sigma in samples."""
+    lib = _load()
+    g = np.empty(L)
+    dg = np.empty(L)
+    if lib.oro_window(L, float(sigma), _p(g), _p(dg)) != 0:
+        raise ValueError("bad window parameters")
+    return g, dg
+
+
+def fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """The oracle's own radix-2 FFT (unnormalised, exp(sign 2 pi i k n / n))."""
+    lib = _load()
+    x = np.asarray(x, dtype=np.complex128)
+    re = np.ascontiguousarray(x.real.copy())
+    im = np.ascontiguousarray(x.imag.copy())
+    if lib.oro_fft(_p(re), _p(im), len(x), sign) != 0:
+        raise ValueError("fft size must be a power of two")
+    return re + 1j * im
+
+
+def frames(n: int, hop: int) -> int:
+    return (n + hop - 1) // hop
+
+
+def stft(x, g, dg, hop: int, nfft: int, k_lo: int, k_hi: int, m0: int = 0,
+         nm: int | None = None):
+    """Eq. 9 STFTs with windows g and g' for frames [m0, m0+nm), bins [k_lo, k_hi]."""
+    lib = _load()
+    x = _c(x)
+    g = _c(g)
+    dg = _c(dg)
+    L = len(g)
+    if nm is None:
+        nm = frames(len(x), hop) - m0
+    nb = k_hi - k_lo + 1
+    V = np.zeros((nm, nb), dtype=np.complex128)
+    Vd = np.zeros((nm, nb), dtype=np.complex128)
+    rc = lib.oro_stft(_p(x), len(x), _p(g), _p(dg), L, hop, nfft, m0, nm,
+                      k_lo, k_hi, _p(V.view(np.float64)), _p(Vd.view(np.float64)))
+    if rc != 0:
+        raise ValueError(f"oro_stft failed ({rc})")
+    return V, Vd
+
+
+def reassign(V, Vd, k_lo: int, k_hi: int, nfft: int, z: int, gamma: float):
+    """Eq. 12-13 IF estimate and Eq. 27-29 reassignment.
+
+    Returns (omega [bins], dest, T, leak)."""
+    lib = _load()
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    Vd = np.ascontiguousarray(Vd, dtype=np.complex128)
+    nm, nb = V.shape
+    nbo = z * (k_hi - k_lo) + 1
+    omega = np.empty((nm, nb))
+    dest = np.empty((nm, nb), dtype=np.int32)
+    T = np.zeros((nm, nbo), dtype=np.complex128)
+    leak = np.zeros(nm, dtype=np.complex128)
+    rc = lib.oro_reassign(_p(V.view(np.float64)), _p(Vd.view(np.float64)), nm,
+                          k_lo, k_hi, nfft, z, float(gamma), _p(omega),
+                          dest.ctypes.data_as(_ip), _p(T.view(np.float64)),
+                          _p(leak.view(np.float64)))
+    if rc != 0:
+        raise ValueError("oro_reassign failed")
+    return omega, dest, T, leak
+
+
+def normaliser(g, hop: int, n: int, p0: int = 0, np_: int | None = None,
+               mode: int = 0) -> np.ndarray:
+    """Eq. 26 normaliser D[p] = g[0] sum_m g[p - m hop] (mode 0) or the Eq. 11
+    WOLA normaliser sum_m g[p - m hop]^2 (mode 1)."""
+    lib = _load()
+    g = _c(g)
+    if np_ is None:
+        np_ = n - p0
+    D = np.empty(np_)
+    lib.oro_normaliser(_p(g), len(g), hop, frames(n, hop), p0, np_, mode, _p(D))
+    return D
+
+
+def inverse(T, k_lo: int, nfft: int, z: int, g, hop: int, n: int,
+            p0: int = 0, np_: int | None = None, mt0: int = 0, mode: int = 0):
+    """Eq. 25-26 direct inverse (zNf-point zero-padded IDFT, P. 223).
+
+    T holds frames [mt0, mt0 + len(T)); output samples [p0, p0 + np_)."""
+    lib = _load()
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    g = _c(g)
+    ntf, nbo = T.shape
+    if np_ is None:
+        np_ = n - p0
+    out = np.empty(np_)
+    rc = lib.oro_inverse(_p(T.view(np.float64)), mt0, ntf, k_lo, nbo, nfft, z,
+                         _p(g), len(g), hop, n, p0, np_, mode, _p(out))
+    if rc != 0:
+        raise ValueError(f"oro_inverse failed ({rc})")
+    return out
+
+
+def colsum(T, k_lo: int, nfft: int, z: int, g0: float) -> np.ndarray:
+    """Eq. 15 column-sum inverse over the whole grid (hop = 1)."""
+    lib = _load()
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    nm, nbo = T.shape
+    out = np.empty(nm)
+    lib.oro_colsum(_p(T.view(np.float64)), nm, k_lo, nbo, nfft, z, float(g0), _p(out))
+    return out
+
+
+def sigma_f(sigma_s: float) -> float:
+    """Eq. 35."""
+    return _load().oro_sigma_f(sigma_s)
+
+
+def hf_max_rule1(n: float, sigma_s: float, fs: float) -> float:
+    """Eq. 38."""
+    return _load().oro_hf_max_rule1(n, sigma_s, fs)
+
+
+def hf_max_rule2(n: float, sigma_s: float, fs: float) -> float:
+    """Eq. 46 restated as a bound on Hf."""
+    return _load().oro_hf_max_rule2(n, sigma_s, fs)
+
+
+def delta_f(fs: float, nfft: int, z: int = 1) -> float:
+    """Eq. 12 / Eq. 28 frequency interval in Hz."""
+    return _load().oro_delta_f(fs, nfft, z)
+
+
+# ---------------------------------------------------------------- pipeline
+def band_bins(fs: float, nfft: int, f_lo: float, f_hi: float):
+    """Band [f_lo, f_hi] Hz -> inclusive coarse bins, rounding half up."""
+    k_lo = int(math.floor(f_lo * nfft / fs + 0.5))
+    k_hi = int(math.floor(f_hi * nfft / fs + 0.5))
+    k_hi = min(k_hi, nfft // 2)
+    return k_lo, k_hi
+
+
+@dataclass
+class Result:
+    V: np.ndarray
+    Vd: np.ndarray
+    omega: np.ndarray
+    dest: np.ndarray
+    T: np.ndarray
+    leak: np.ndarray
+    gamma: float
+    k_lo: int
+    k_hi: int
+    m0: int
+    xhat: np.ndarray | None = None
+
+
+def sst(x, fs: float, L: int, sigma: float, hop: int, nfft: int, f_lo: float,
+        f_hi: float, z: int, gamma: float, relative: bool, m0: int = 0,
+        nm: int | None = None, inverse_range: tuple[int, int] | None = None,
+        gamma_abs: float | None = None) -> Result:
+    """Whole path: Eq. 9 STFTs -> Eq. 13 IF + threshold -> Eq. 28 reassignment
+    -> Eq. 25-26 inverse.
+
+    With ``relative`` the threshold is gamma * max|V| over all frames and the
+    in-band bins (computed over every frame even when only [m0, m0+nm) is
+    returned), unless ``gamma_abs`` supplies the absolute threshold directly.
+    ``inverse_range`` = (p0, np) asks for xhat on those samples; the frames
+    [m0, m0+nm) must then cover them."""
+    x = _c(x)
+    n = len(x)
+    g, dg = window(L, sigma)
+    k_lo, k_hi = band_bins(fs, nfft, f_lo, f_hi)
+    F = frames(n, hop)
+    if nm is None:
+        nm = F - m0
+    V, Vd = stft(x, g, dg, hop, nfft, k_lo, k_hi, m0, nm)
+    if gamma_abs is not None:
+        gam = float(gamma_abs)
+    elif relative:
+        gam = gamma * global_max_abs_v(x, g, dg, hop, nfft, k_lo, k_hi)
+    else:
+        gam = float(gamma)
+    omega, dest, T, leak = reassign(V, Vd, k_lo, k_hi, nfft, z, gam)
+    xhat = None
+    if inverse_range is not None:
+        p0, np_ = inverse_range
+        xhat = inverse(T, k_lo, nfft, z, g, hop, n, p0, np_, mt0=m0)
+    return Result(V, Vd, omega, dest, T, leak, gam, k_lo, k_hi, m0, xhat)
+
+
+def global_max_abs_v(x, g, dg, hop, nfft, k_lo, k_hi, chunk: int = 4096) -> float:
+    """max over every frame and in-band bin of |V| (the relative-threshold base)."""
+    n = len(x)
+    F = frames(n, hop)
+    best = 0.0
+    for m0 in range(0, F, chunk):
+        nm = min(chunk, F - m0)
+        V, _ = stft(x, g, dg, hop, nfft, k_lo, k_hi, m0, nm)
+        best = max(best, float(np.abs(V).max()))
+    return best
