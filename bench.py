@@ -1,0 +1,345 @@
+"""Throughput benchmark of the fused SST forward + direct inverse.
+
+One step = sst_forward_inverse over the whole run-up vibration workload
+(N = 2^24 float32 samples at 51.2 kHz, Gaussian window L = 2049, hop 32,
+Nf 4096, band 0-6.4 kHz, subdivision z = 4, gamma = 1e-3 max|V|): threshold
+pre-pass, forward (T written to HBM, 8.6 GB), inverse and overlap-add.
+Metric: input samples/s.  With --gpus N > 1 (torchrun), every rank runs its
+own replica of the workload on its own GPU (weak scaling, no collective on
+the data path).
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample
+of the same workload, and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2003_07065_gb300 import workloads as W  # noqa: E402
+
+METRIC = "input samples/s through SST fwd+inverse"
+UNIT = "samples/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def flops_per_frame(w) -> dict:
+    """Algorithmic FLOPs per frame of each kernel (conventional 5 N log2 N per
+    complex FFT, 2.5 N log2 N per real-output one):
+      absmax : half a packed FFT per frame + window + |V|^2 on the band
+      forward: packed complex FFT + window (x g, x g') + ~20 per band bin
+      inverse: z real-output IFFTs + 8 z L for the sub-grid twiddles and
+               the window / overlap-add."""
+    nf, L, z = w.nfft, w.L, w.z
+    k_lo = int(math.floor(w.f_lo * nf / w.fs + 0.5))
+    k_hi = min(nf // 2, int(math.floor(w.f_hi * nf / w.fs + 0.5)))
+    nb = k_hi - k_lo + 1
+    lg = math.log2(nf)
+    return {
+        "absmax": 2.5 * nf * lg + 2 * L + 4 * nb,
+        "forward": 5 * nf * lg + 4 * L + 20 * nb,
+        "inverse": 2.5 * z * nf * lg + 8 * z * L,
+    }
+
+
+def bytes_per_frame(w) -> dict:
+    """Algorithmic DRAM bytes per frame: x read once (hop new samples per
+    frame), T written by the forward and read by the inverse, xhat written."""
+    nf = w.nfft
+    k_lo = int(math.floor(w.f_lo * nf / w.fs + 0.5))
+    k_hi = min(nf // 2, int(math.floor(w.f_hi * nf / w.fs + 0.5)))
+    nbo = w.z * (k_hi - k_lo) + 1
+    return {"absmax": 4 * w.hop, "forward": 4 * w.hop + 8 * nbo, "inverse": 8 * nbo + 4 * w.hop}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
+    """FP32 ALU peak: 128 FP32 lanes per SM, one FMA (2 FLOPs) per lane per
+    clock."""
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ reference arm
+def oracle_sample_rate(w, budget_s: float = 15.0):
+    """Run the FP64 oracle on a bounded prefix of the workload's signal (the
+    whole path: STFTs, IF, reassignment, inverse) and return samples/s."""
+    import oracle as O
+    noisy, _ = w.signal()
+    n_sample = min(w.n, 1 << 15)
+    x = noisy[:n_sample].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.sst(x, w.fs, w.L, w.sigma, w.hop, w.nfft, w.f_lo, w.f_hi, w.z, w.gamma, w.relative,
+              inverse_range=(0, len(x)))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 64:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return reps * n_sample / el, threads, f"{reps} x first {n_sample} samples of {w.name}", el
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, budget_s=0.0)
+    for _ in range(args.steps):
+        v, threads, sample, _ = oracle_sample_rate(w, budget_s=max(1.0, 30.0 / max(args.steps, 1)))
+        vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "nfft": w.nfft, "hop": w.hop, "L": w.L, "z": w.z,
+                   "band_hz": [w.f_lo, w.f_hi]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="runup_16m", choices=sorted(W.ALL))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = W.ALL[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2003_07065_gb300 import build, sst
+    if rank == 0:
+        build.build()
+    barrier()
+    build.build()
+    sst.load()
+
+    noisy, _ = w.signal()
+    x_host = torch.from_numpy(noisy.astype(np.float32)).pin_memory()
+    x = x_host.cuda()
+    plan = sst.Plan(**w.params())
+    tfr = plan.new_tfr()
+    xhat = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    xhat_host = torch.empty(w.n, dtype=torch.float32).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sst.sst_forward_inverse(plan.handle, x, w.n, tfr, xhat, plan.workspace, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each (outside the events)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = sst.sst_launch_count()
+    sst.sst_profile_enable(True)
+    sst.sst_profile_collect()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    sst.sst_profile_enable(False)
+    prof = sst.sst_profile_collect()
+    launches = sst.sst_launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = sum(step_ms)
+    if dist is not None:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * w.n * args.steps / (t_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers
+    for _ in range(2):
+        sst.sst_forward_inverse_host(plan.handle, x_host, w.n, xhat_host, x, tfr, xhat, plan.workspace, stream)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        sst.sst_forward_inverse_host(plan.handle, x_host, w.n, xhat_host, x, tfr, xhat, plan.workspace, stream)
+    e_s = time.perf_counter() - e0
+    if dist is not None:
+        tt = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_s = float(tt.item())
+    e2e = world * w.n * args.steps / e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel
+    F = plan.frames
+    fl = flops_per_frame(w)
+    by = bytes_per_frame(w)
+    dom = max(prof, key=lambda k: prof[k][0]) if prof else None
+    roof = None
+    peaks = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if dom in fl:
+        tot_ms, cnt = prof[dom]
+        per_launch_ms = tot_ms / cnt
+        units = F
+        flops = fl[dom] * units
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        sm_max = peaks.get("sm_max_mhz") or 2070.0
+        peak = fp32_peak_tflops(num_sms, sm_max)
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": f"FP32 FMA peak {num_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max clock)",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
+                "hbm_gbs_achieved": by[dom] * units / (per_launch_ms / 1e3) / 1e9,
+                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+    kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        v, threads, sample, el = oracle_sample_rate(w, budget_s=12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+               "seconds": el}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "fs": w.fs, "nfft": w.nfft, "hop": w.hop, "L": w.L,
+                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "gamma": "1e-3 max|V|",
+                   "frames": F, "bins": plan.bins, "tfr_bytes": F * plan.bins * 8,
+                   "l2": "flushed before each timed step (2x L2 write); T (8.6 GB) also exceeds L2",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": launches // max(1, 1),
+        "gpu_launches_per_step": launches / args.steps,
+        "kernels": kern,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n, "d2h_bytes_per_step": 4 * w.n},
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

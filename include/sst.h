@@ -1,0 +1,169 @@
+/*
+ * sst.h -- C ABI of libsst.so, the GB300 (sm_103a) implementation of the
+ * downsampled STFT-based synchrosqueezing transform with selective
+ * reassignment, frequency subdivision and the direct approximate inverse
+ * (He & Cao, arXiv 2003.07065).
+ *
+ * Conventions shared by every call
+ *  - Signals are float32.  Complex arrays (TFR, STFT) are interleaved float32
+ *    pairs (re, im), row-major, one row per frame.
+ *  - Frame m (0 <= m < F, F = ceil(n / hop)) is centred on sample m*hop; the
+ *    signal is zero outside [0, n) (Sec. 2.1, Eq. 7-8).
+ *  - Frequencies are in coarse DFT bins: bin k is k*fs/nfft Hz (Eq. 12).  The
+ *    band [f_lo, f_hi] maps to bins k_lo = round(f_lo*nfft/fs),
+ *    k_hi = round(f_hi*nfft/fs) (round half up), inclusive; N_r = k_hi - k_lo.
+ *  - The squeezed TFR T has zN_r + 1 bins per frame: bin l sits at coarse
+ *    frequency k_lo + l/z (Eq. 28-29).
+ *  - Pointers named *_dev are device pointers; the caller allocates and owns
+ *    them (e.g. through PyTorch), and they must stay valid until the work
+ *    enqueued on `stream` has finished.  `stream` is a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream.  Calls enqueue work and return
+ *    without synchronising unless stated otherwise.
+ *  - `workspace_dev` is scratch device memory of at least the size returned
+ *    by sst_plan_query (256-byte aligned).  Concurrent calls on different
+ *    streams need distinct workspaces.
+ *  - Every call validates its arguments before enqueueing anything and
+ *    returns a status; it never throws or aborts.  A failed CUDA launch
+ *    returns SST_ECUDA; asynchronous device faults surface on a later call
+ *    or on sst_sync.  sst_last_error() gives a thread-local message for the
+ *    last failure of the calling thread.
+ *  - A plan is immutable after creation and may be shared by threads and
+ *    streams.  It owns its device tables (window, twiddles, normaliser),
+ *    allocated on the device that is current at creation; calls must be made
+ *    with that device current.
+ */
+#ifndef SST_H
+#define SST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SST_OK = 0,
+    SST_EINVAL = 1,        /* invalid argument (message in sst_last_error) */
+    SST_ENOMEM = 2,        /* host or device allocation failed */
+    SST_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    SST_EBUSY = 4,         /* no capacity (service admission) */
+    SST_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    SST_EUNSUPPORTED = 6,  /* valid parameters this build does not handle */
+    SST_EINTERNAL = 7      /* internal invariant violated */
+} sst_status;
+
+/* flags */
+#define SST_GAMMA_RELATIVE 0x1u  /* gamma is a fraction of max|V| over all frames and in-band bins */
+
+typedef struct sst_plan *sst_plan_t;
+
+/* Parameters: the paper's own quantities (Sec. 2.1-2.4). */
+typedef struct {
+    int64_t n;          /* signal length N (samples), >= 1 */
+    double fs;          /* sample rate in Hz (maps the band to bins, Eq. 12) */
+    int32_t L;          /* odd window length L = 2M + 1, 1 < L <= nfft + 1 */
+    double sigma;       /* Gaussian sigma in samples (Sec. 2.1), used when g == NULL */
+    const double *g;    /* optional host window g[j], j = -M..M (L values), or NULL */
+    const double *dg;   /* optional host derivative window g'[j] (Sec. 2.2); both or neither */
+    int32_t hop;        /* time decimation H_t, 1 <= hop <= M */
+    int32_t nfft;       /* DFT length N_f, a power of two in [64, 8192] (Eq. 9) */
+    double f_lo, f_hi;  /* band of interest in Hz, 0 <= f_lo < f_hi <= fs/2 (Eq. 27) */
+    int32_t z;          /* frequency subdivision factor, 1 <= z <= 16 (Eq. 28-29) */
+    double gamma;       /* threshold on |V| (Eq. 13): absolute, or a fraction if SST_GAMMA_RELATIVE */
+    uint32_t flags;
+} sst_params;
+
+/* Create a plan: validates the parameters, builds the window, twiddle and
+ * inverse-normaliser tables in FP64 on the host, rounds them to FP32 and
+ * uploads them (Sec. 2.1-2.3).  On success *out owns device memory until
+ * sst_plan_destroy.  Errors: SST_EINVAL, SST_EUNSUPPORTED, SST_ENOMEM, SST_ECUDA. */
+sst_status sst_plan_create(const sst_params *params, sst_plan_t *out);
+
+/* Release a plan and its device tables.  NULL is ignored.  The caller must
+ * make sure no enqueued work still uses the plan. */
+void sst_plan_destroy(sst_plan_t plan);
+
+/* Sizes of a plan: F frames, bins = zN_r + 1 TFR bins per frame, the band
+ * k_lo..k_hi (inclusive, coarse bins) and the workspace the compute calls
+ * need.  Any output pointer may be NULL. */
+sst_status sst_plan_query(sst_plan_t plan, int64_t *frames, int32_t *bins,
+                          int32_t *k_lo, int32_t *k_hi, size_t *workspace_bytes);
+
+/* Forward SST (Sec. 2.2, 2.4): per frame, the packed Nf-point FFT of
+ * x*g + i*x*g' gives S^g and S^g' (Eq. 9, split by Hermitian symmetry), the
+ * IF estimate omega = k - (Nf/2pi) Im(S^g'/S^g) (Eq. 13), the threshold
+ * |S^g| > gamma, and the in-band coefficients are summed into
+ * T[m, l], l = floor(z (omega - k_lo) + 1/2) when 0 <= l <= zN_r (Eq. 27-29).
+ * Sums are exact-then-rounded (deterministic, independent of thread order).
+ *   x_dev   : n floats
+ *   tfr_dev : F x bins complex (2*F*bins floats), fully overwritten
+ * n must equal the plan's n. */
+sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                       void *workspace_dev, void *stream);
+
+/* Direct approximate inverse (Sec. 2.3, Eq. 25-26; zero padding and the
+ * zNf-point inverse of Sec. 2.5): per frame
+ *   r[m, j] = (2/Nf) Re sum_l w_l T[m,l] exp(i 2 pi (k_lo + l/z) j / Nf),
+ *   j in [-M, M], w_l = 1/2 at the DC and Nyquist destinations, else 1;
+ * then xhat[p] = sum_m g[p - m hop] r[m, p - m hop] / D[p] with
+ * D[p] = g[0] sum_m g[p - m hop] (the exact discrete form of the 1/sqrt(2)
+ * of Eq. 26).  Overlap-add order is fixed (deterministic).
+ *   tfr_dev : F x bins complex;  xhat_dev : n floats, fully overwritten. */
+sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n, float *xhat_dev,
+                       void *workspace_dev, void *stream);
+
+/* sst_forward followed by sst_inverse.  tfr_dev receives T and may not be
+ * NULL in this version (the inverse reads it back). */
+sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                               float *xhat_dev, void *workspace_dev, void *stream);
+
+/* End-to-end variant with host buffers: copies x_host (n floats, ideally
+ * pinned) into x_dev, runs sst_forward_inverse, copies xhat_dev back into
+ * xhat_host, and synchronises `stream` before returning. */
+sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host, int64_t n,
+                                    float *xhat_host, float *x_dev, float *tfr_dev,
+                                    float *xhat_dev, void *workspace_dev, void *stream);
+
+/* In-band STFTs S^g and S^g' (Eq. 9, centre-referenced: phase factor
+ * exp(i 2 pi k M / Nf) included), no threshold.  V_dev, Vd_dev: F x nb
+ * complex with nb = k_hi - k_lo + 1.  For checking the transform. */
+sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, float *V_dev, float *Vd_dev,
+                    void *workspace_dev, void *stream);
+
+/* The reassignment map of sst_forward: omega_dev[m, k - k_lo] = the IF
+ * estimate in coarse bins (Eq. 13, NaN where S^g = 0) and dest_dev = the
+ * destination l, -1 below the threshold, -2 outside the grid.  F x nb each. */
+sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
+                            int32_t *dest_dev, void *workspace_dev, void *stream);
+
+/* max |S^g| over all frames and in-band bins (the base of a relative
+ * threshold), written as one float to maxv_dev. */
+sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev,
+                         void *workspace_dev, void *stream);
+
+/* Block until `stream` is idle; returns SST_ECUDA with the message of any
+ * pending asynchronous error. */
+sst_status sst_sync(void *stream);
+
+/* Number of kernels this library has launched in this process (all
+ * entry points, all threads). */
+uint64_t sst_launch_count(void);
+
+/* Per-kernel timing.  While enabled, each kernel launch of this library is
+ * bracketed by two CUDA events recorded on the launch's own stream;
+ * sst_profile_collect waits for them, adds the elapsed times per kernel kind
+ * into ms[kind] and counts[kind] (arrays of SST_PROFILE_KINDS entries),
+ * and clears the record.  Kinds: see sst_profile_kind_name. */
+#define SST_PROFILE_KINDS 8
+sst_status sst_profile_enable(int on);
+sst_status sst_profile_collect(double *ms, uint64_t *counts);
+const char *sst_profile_kind_name(int kind);
+
+const char *sst_status_string(sst_status s);
+const char *sst_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SST_H */

@@ -1,0 +1,574 @@
+// C ABI of libsst.so: plan creation (FP64 tables rounded to FP32), argument
+// validation, workspace layout and the launch sequences of each entry point.
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sst.h"
+#include "sst_dev.h"
+#include "sst_launch.h"
+
+#define SST_API extern "C" __attribute__((visibility("default")))
+
+namespace sst {
+
+const KernelTable *table_nf_64();
+const KernelTable *table_nf_128();
+const KernelTable *table_nf_256();
+const KernelTable *table_nf_512();
+const KernelTable *table_nf_1024();
+const KernelTable *table_nf_2048();
+const KernelTable *table_nf_4096();
+const KernelTable *table_nf_8192();
+
+const KernelTable *table_for_nf(int nf) {
+    switch (nf) {
+        case 64: return table_nf_64();
+        case 128: return table_nf_128();
+        case 256: return table_nf_256();
+        case 512: return table_nf_512();
+        case 1024: return table_nf_1024();
+        case 2048: return table_nf_2048();
+        case 4096: return table_nf_4096();
+        case 8192: return table_nf_8192();
+    }
+    return nullptr;
+}
+
+// ------------------------------------------------------------ small kernels
+__global__ void k_gamma(const float *__restrict__ partial, int count, float frac2,
+                        float *__restrict__ gamma2_out, float *__restrict__ maxv_out) {
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmaxf(v, partial[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+        if (gamma2_out) *gamma2_out = frac2 * r;
+        if (maxv_out) *maxv_out = sqrtf(r);
+    }
+}
+
+__device__ __forceinline__ float recip_norm(const SstDev &d, int64_t p) {
+    if (p < d.EL) return d.rD_left[p];
+    if (p >= d.ER) return d.rD_right[p - d.ER];
+    return d.rD_per[p % d.hop];
+}
+
+// xhat[p] = (sum over the tiles whose segment covers p, in tile order) / D[p]
+__global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat) {
+    const int64_t BH = (int64_t)d.B * d.hop;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t num = p + d.M - d.seg_len + 1;
+        const int64_t tlo = num <= 0 ? 0 : (num + BH - 1) / BH;
+        int64_t thi = (p + d.M) / BH;
+        if (thi > d.ntiles - 1) thi = d.ntiles - 1;
+        float s = 0.f;
+        for (int64_t t = tlo; t <= thi; ++t) s += partial[t * d.seg_len + (p + d.M - t * BH)];
+        xhat[p] = s * recip_norm(d, p);
+    }
+}
+
+}  // namespace sst
+
+using namespace sst;
+
+// ------------------------------------------------------------ error state
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+
+static sst_status fail(sst_status s, const char *fmt, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
+    g_err = b;
+    return s;
+}
+
+static sst_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(SST_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define SST_CU(call, what)                                 \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ------------------------------------------------------------ profiling
+enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER };
+static const char *kPkNames[SST_PROFILE_KINDS] = {"absmax", "gamma", "forward", "stft", "map", "inverse",
+                                                  "finalize", "other"};
+struct ProfRec { int kind; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static std::vector<ProfRec> g_prof;
+static std::atomic<int> g_prof_on{0};
+
+struct ProfScope {
+    int kind; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(int k, cudaStream_t s) : kind(k), st(s) {
+        if (g_prof_on.load(std::memory_order_relaxed)) {
+            if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) cudaEventRecord(a, st);
+            else a = b = nullptr;
+        }
+    }
+    void done() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_prof.push_back({kind, a, b});
+            a = b = nullptr;
+        }
+    }
+    ~ProfScope() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+#define SST_LAUNCHED_K(kind, st, call, what)               \
+    do {                                                   \
+        ProfScope ps_(kind, st);                           \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+        ps_.done();                                        \
+        g_launches.fetch_add(1, std::memory_order_relaxed); \
+    } while (0)
+
+// ------------------------------------------------------------ plan
+struct sst_plan {
+    sst_params p;
+    int device = 0;
+    int num_sms = 0;
+    SstDev d;
+    const KernelTable *kt = nullptr;
+    void *dmem = nullptr;
+    float gamma_frac2 = 0.f;
+    size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
+    int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
+    size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
+};
+
+static int64_t round_half_up(double v) { return (int64_t)std::floor(v + 0.5); }
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static sst_status validate(const sst_params *p) {
+    if (!p) return fail(SST_EINVAL, "params is NULL");
+    if (p->n < 1) return fail(SST_EINVAL, "n must be >= 1 (got %lld)", (long long)p->n);
+    if (!(p->fs > 0.0)) return fail(SST_EINVAL, "fs must be > 0");
+    if (p->nfft < 64 || p->nfft > 8192 || (p->nfft & (p->nfft - 1)))
+        return fail(SST_EINVAL, "nfft must be a power of two in [64, 8192] (got %d)", p->nfft);
+    if (p->L < 3 || (p->L % 2) == 0) return fail(SST_EINVAL, "L must be odd and >= 3 (got %d)", p->L);
+    if (p->L > p->nfft + 1)
+        return fail(SST_EUNSUPPORTED, "L = %d exceeds nfft + 1 = %d", p->L, p->nfft + 1);
+    const int M = (p->L - 1) / 2;
+    if (p->hop < 1 || p->hop > M) return fail(SST_EINVAL, "hop must be in [1, M = %d] (got %d)", M, p->hop);
+    if (!(p->f_lo >= 0.0) || !(p->f_hi > p->f_lo) || p->f_hi > p->fs / 2 * (1 + 1e-12))
+        return fail(SST_EINVAL, "band must satisfy 0 <= f_lo < f_hi <= fs/2");
+    if (p->z < 1 || p->z > 16) return fail(SST_EINVAL, "z must be in [1, 16] (got %d)", p->z);
+    if (!(p->gamma >= 0.0) || !std::isfinite(p->gamma)) return fail(SST_EINVAL, "gamma must be finite and >= 0");
+    if ((p->g == nullptr) != (p->dg == nullptr)) return fail(SST_EINVAL, "give both g and dg, or neither");
+    if (!p->g && !(p->sigma > 0.0)) return fail(SST_EINVAL, "sigma must be > 0 when g is not given");
+    if (p->flags & ~SST_GAMMA_RELATIVE) return fail(SST_EINVAL, "unknown flags 0x%x", p->flags);
+    return SST_OK;
+}
+
+SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
+    if (!out) return fail(SST_EINVAL, "out is NULL");
+    *out = nullptr;
+    sst_status st = validate(params);
+    if (st != SST_OK) return st;
+    const sst_params &p = *params;
+
+    int dev = 0;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaDeviceProp prop;
+    SST_CU(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(SST_EUNSUPPORTED, "libsst is built for sm_103a; device %d is sm_%d%d", dev, prop.major,
+                    prop.minor);
+
+    const KernelTable *kt = table_for_nf(p.nfft);
+    if (!kt) return fail(SST_EINTERNAL, "no kernels for nfft %d", p.nfft);
+
+    sst_plan *pl = new (std::nothrow) sst_plan();
+    if (!pl) return fail(SST_ENOMEM, "host allocation failed");
+    pl->p = p;
+    pl->p.g = pl->p.dg = nullptr;
+    pl->device = dev;
+    pl->num_sms = prop.multiProcessorCount;
+    pl->kt = kt;
+
+    const int L = p.L, M = (L - 1) / 2, nf = p.nfft, z = p.z, hop = p.hop;
+    const int64_t n = p.n;
+    const int64_t F = (n + hop - 1) / hop;
+    int64_t k_lo = round_half_up(p.f_lo * nf / p.fs);
+    int64_t k_hi = round_half_up(p.f_hi * nf / p.fs);
+    if (k_hi > nf / 2) k_hi = nf / 2;
+    if (k_lo > k_hi) k_lo = k_hi;
+    const int nb = (int)(k_hi - k_lo + 1);
+    const int nbo = z * (int)(k_hi - k_lo) + 1;
+
+    // ---- FP64 tables
+    std::vector<double> g(L), dg(L);
+    if (params->g) {
+        for (int i = 0; i < L; ++i) { g[i] = params->g[i]; dg[i] = params->dg[i]; }
+    } else {
+        const double amp = std::pow(M_PI * p.sigma * p.sigma, -0.25);
+        for (int j = -M; j <= M; ++j) {
+            const double v = amp * std::exp(-(double)j * j / (2.0 * p.sigma * p.sigma));
+            g[j + M] = v;
+            dg[j + M] = -((double)j / (p.sigma * p.sigma)) * v;
+        }
+    }
+    if (!(g[M] > 0.0)) { delete pl; return fail(SST_EINVAL, "window must have g[0] > 0"); }
+    const int G = z * nf;
+    // inverse normaliser 1 / D[p], D[p] = g[0] sum_{m=0}^{F-1} g[p - m hop]  (Eq. 26)
+    auto Dexact = [&](int64_t q) {
+        int64_t mlo = (q - M > 0) ? (q - M + hop - 1) / hop : 0;
+        int64_t mhi = (q + M) / hop;
+        if (mhi > F - 1) mhi = F - 1;
+        double s = 0.0;
+        for (int64_t m = mlo; m <= mhi; ++m) {
+            const int64_t j = q - m * hop;
+            if (j >= -M && j <= M) s += g[j + M];
+        }
+        return g[M] * s;
+    };
+    const int64_t EL = std::min<int64_t>(n, M);
+    const int64_t ER = std::max<int64_t>(EL, std::min<int64_t>(n, F * hop - M));
+    std::vector<float> rDl(std::max<int64_t>(EL, 1)), rDr(std::max<int64_t>(n - ER, 1)), rDp(hop);
+    for (int64_t q = 0; q < EL; ++q) rDl[q] = (float)(1.0 / Dexact(q));
+    for (int64_t q = ER; q < n; ++q) rDr[q - ER] = (float)(1.0 / Dexact(q));
+    for (int r = 0; r < hop; ++r) {
+        double s = 0.0;
+        for (int j = -M; j <= M; ++j)
+            if ((((j % hop) + hop) % hop) == r) s += g[j + M];
+        rDp[r] = (float)(1.0 / (g[M] * s));
+    }
+    for (int64_t q = 0; q < EL; ++q)
+        if (!std::isfinite(rDl[q])) { delete pl; return fail(SST_EINVAL, "normaliser vanishes at sample %lld", (long long)q); }
+    for (int64_t q = ER; q < n; ++q)
+        if (!std::isfinite(rDr[q - ER])) { delete pl; return fail(SST_EINVAL, "normaliser vanishes at sample %lld", (long long)q); }
+
+    std::vector<float2> win(L), tw(nf), twz(G);
+    std::vector<float> gf(L);
+    for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)dg[i]); gf[i] = (float)g[i]; }
+    for (int q = 0; q < nf; ++q) {
+        const double a = -2.0 * M_PI * (double)q / (double)nf;
+        tw[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    for (int q = 0; q < G; ++q) {
+        const double a = 2.0 * M_PI * (double)q / (double)G;
+        twz[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+
+    // ---- one device allocation for all tables
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    const size_t o_win = take(sizeof(float2) * L), o_g = take(sizeof(float) * L), o_tw = take(sizeof(float2) * nf),
+                 o_twz = take(sizeof(float2) * G), o_rl = take(sizeof(float) * rDl.size()),
+                 o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop);
+    cudaError_t ce = cudaMalloc(&pl->dmem, off);
+    if (ce != cudaSuccess) { delete pl; return fail(SST_ENOMEM, "cudaMalloc of %zu table bytes failed", off); }
+    char *base = (char *)pl->dmem;
+    std::vector<char> host(off, 0);
+    memcpy(host.data() + o_win, win.data(), sizeof(float2) * L);
+    memcpy(host.data() + o_g, gf.data(), sizeof(float) * L);
+    memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * nf);
+    memcpy(host.data() + o_twz, twz.data(), sizeof(float2) * G);
+    memcpy(host.data() + o_rl, rDl.data(), sizeof(float) * rDl.size());
+    memcpy(host.data() + o_rr, rDr.data(), sizeof(float) * rDr.size());
+    memcpy(host.data() + o_rp, rDp.data(), sizeof(float) * hop);
+    ce = cudaMemcpy(base, host.data(), off, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "table upload"); }
+
+    SstDev &d = pl->d;
+    d.win = (const float2 *)(base + o_win);
+    d.g = (const float *)(base + o_g);
+    d.tw = (const float2 *)(base + o_tw);
+    d.twz = (const float2 *)(base + o_twz);
+    d.rD_left = (const float *)(base + o_rl);
+    d.rD_right = (const float *)(base + o_rr);
+    d.rD_per = (const float *)(base + o_rp);
+    d.n = n;
+    d.F = F;
+    d.EL = EL;
+    d.ER = ER;
+    d.L = L;
+    d.M = M;
+    d.hop = hop;
+    d.nf = nf;
+    d.z = z;
+    d.k_lo = (int)k_lo;
+    d.k_hi = (int)k_hi;
+    d.nb = nb;
+    d.nbo = nbo;
+    int lg = 0;
+    while ((1 << lg) < nb) ++lg;
+    d.log2_nb = lg;
+    d.c_if = (float)((double)nf / (2.0 * M_PI));
+    d.relative = (p.flags & SST_GAMMA_RELATIVE) ? 1 : 0;
+    d.gamma2_abs = d.relative ? 0.f : (float)(p.gamma * p.gamma);
+    pl->gamma_frac2 = (float)(p.gamma * p.gamma);
+
+    // inverse tiles: B even, enough tiles to fill the GPU several times over
+    int64_t B = F / (4LL * pl->num_sms);
+    if (B > 64) B = 64;
+    if (B < 2) B = 2;
+    B &= ~1LL;
+    d.B = (int)B;
+    d.seg_len = (int)((B - 1) * hop + L);
+    d.ntiles = (F + B - 1) / B;
+
+    // ---- shared memory and grids
+    pl->smem_fwd_x = kt->smem_frame;
+    pl->smem_fwd_t = kt->smem_frame + 2 * sizeof(unsigned long long) * (size_t)nbo;
+    pl->smem_absmax = kt->smem_frame;
+    pl->smem_inv = kt->smem_frame + sizeof(float) * (size_t)d.seg_len;
+    const size_t smax = prop.sharedMemPerBlockOptin;
+    if (pl->smem_fwd_t > smax || pl->smem_inv > smax) {
+        cudaFree(pl->dmem);
+        delete pl;
+        return fail(SST_EUNSUPPORTED, "shared memory need (%zu / %zu B) exceeds %zu B", pl->smem_fwd_t,
+                    pl->smem_inv, smax);
+    }
+    struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {KIND_FWD_T, pl->smem_fwd_t},
+        {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {KIND_INV, pl->smem_inv}};
+    for (auto &k : kinds) {
+        ce = kt->set_smem(k.kind, k.bytes);
+        if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
+    }
+    auto grid_for = [&](int kind, size_t bytes, int64_t units) {
+        int bl = 1;
+        if (kt->occupancy(kind, bytes, &bl) != cudaSuccess || bl < 1) bl = 1;
+        int64_t g_ = (int64_t)bl * pl->num_sms * 2;
+        if (g_ > units) g_ = units;
+        return (int)std::max<int64_t>(g_, 1);
+    };
+    pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 1) / 2);
+    pl->grid_fwd = grid_for(KIND_FWD_T, pl->smem_fwd_t, F);
+    pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
+
+    // ---- workspace: [scalars 256 B][absmax partials][overlap-add partials]
+    pl->ws_off_partial = 256;
+    pl->ws_off_ola = align256(pl->ws_off_partial + sizeof(float) * pl->grid_absmax);
+    pl->ws_bytes = align256(pl->ws_off_ola + sizeof(float) * (size_t)d.ntiles * d.seg_len);
+    *out = pl;
+    return SST_OK;
+}
+
+SST_API void sst_plan_destroy(sst_plan_t plan) {
+    if (!plan) return;
+    if (plan->dmem) cudaFree(plan->dmem);
+    delete plan;
+}
+
+SST_API sst_status sst_plan_query(sst_plan_t plan, int64_t *frames, int32_t *bins, int32_t *k_lo, int32_t *k_hi,
+                                  size_t *workspace_bytes) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    if (frames) *frames = plan->d.F;
+    if (bins) *bins = plan->d.nbo;
+    if (k_lo) *k_lo = plan->d.k_lo;
+    if (k_hi) *k_hi = plan->d.k_hi;
+    if (workspace_bytes) *workspace_bytes = plan->ws_bytes;
+    return SST_OK;
+}
+
+// ------------------------------------------------------------ launches
+static sst_status check_call(sst_plan_t plan, const void *x, int64_t n, const void *ws) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    if (!x) return fail(SST_EINVAL, "input pointer is NULL");
+    if (n != plan->d.n) return fail(SST_EINVAL, "n = %lld differs from the plan's n = %lld", (long long)n,
+                                    (long long)plan->d.n);
+    if (!ws) return fail(SST_EINVAL, "workspace is NULL");
+    if (((uintptr_t)ws) & 255) return fail(SST_EINVAL, "workspace must be 256-byte aligned");
+    int dev = -1;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != plan->device) return fail(SST_EINVAL, "plan was created on device %d, current is %d", plan->device, dev);
+    return SST_OK;
+}
+
+static float *ws_gamma2(sst_plan_t pl, void *ws) { return (float *)ws; }
+static float *ws_maxv(sst_plan_t pl, void *ws) { return (float *)ws + 1; }
+static float *ws_partial(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_partial); }
+static float *ws_ola(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_ola); }
+
+// relative threshold: gamma^2 = frac^2 max |S^g|^2, left in the workspace
+static sst_status run_gamma(sst_plan_t pl, const float *x, void *ws, cudaStream_t st, float *maxv_out) {
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(pl->d, x, ws_partial(pl, ws), pl->grid_absmax, pl->smem_absmax, st),
+                   "absmax launch");
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   (k_gamma<<<1, 256, 0, st>>>(ws_partial(pl, ws), pl->grid_absmax, pl->gamma_frac2,
+                                               ws_gamma2(pl, ws), maxv_out ? maxv_out : ws_maxv(pl, ws)),
+                    cudaGetLastError()),
+                   "gamma launch");
+    return SST_OK;
+}
+
+static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
+    if (pl->d.relative) {
+        sst_status s = run_gamma(pl, x, ws, st, nullptr);
+        if (s != SST_OK) return s;
+    }
+    SST_LAUNCHED_K(PK_FORWARD, st,
+                   pl->kt->forward(pl->d, KIND_FWD_T, x, ws_gamma2(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   "forward launch");
+    return SST_OK;
+}
+
+static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st) {
+    SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(pl->d, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
+                   "inverse launch");
+    int64_t blocks = (pl->d.n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    SST_LAUNCHED_K(PK_FINALIZE, st,
+                   (k_finalize<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat), cudaGetLastError()),
+                   "finalize launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *ws, void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
+    return run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
+}
+
+SST_API sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n, float *xhat_dev, void *ws,
+                               void *stream) {
+    sst_status s = check_call(plan, tfr_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
+}
+
+SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                                       float *xhat_dev, void *ws, void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
+    if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    s = run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
+    if (s != SST_OK) return s;
+    return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
+}
+
+SST_API sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host, int64_t n, float *xhat_host,
+                                            float *x_dev, float *tfr_dev, float *xhat_dev, void *ws, void *stream) {
+    if (!x_host || !xhat_host) return fail(SST_EINVAL, "host pointer is NULL");
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    SST_CU(cudaMemcpyAsync(x_dev, x_host, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st), "input copy");
+    s = sst_forward_inverse(plan, x_dev, n, tfr_dev, xhat_dev, ws, stream);
+    if (s != SST_OK) return s;
+    SST_CU(cudaMemcpyAsync(xhat_host, xhat_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st), "output copy");
+    SST_CU(cudaStreamSynchronize(st), "stream synchronise");
+    return SST_OK;
+}
+
+SST_API sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, float *V_dev, float *Vd_dev, void *ws,
+                            void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!V_dev || !Vd_dev) return fail(SST_EINVAL, "output pointer is NULL");
+    SST_LAUNCHED_K(PK_STFT, (cudaStream_t)stream,
+                   plan->kt->forward(plan->d, KIND_FWD_STFT, x_dev, ws_gamma2(plan, ws), V_dev, Vd_dev,
+                                     plan->grid_fwd_x, plan->smem_fwd_x, (cudaStream_t)stream),
+                   "stft launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
+                                    int32_t *dest_dev, void *ws, void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->d.relative) {
+        s = run_gamma(plan, x_dev, ws, st, nullptr);
+        if (s != SST_OK) return s;
+    }
+    SST_LAUNCHED_K(PK_MAP, st,
+                   plan->kt->forward(plan->d, KIND_FWD_MAP, x_dev, ws_gamma2(plan, ws), omega_dev, dest_dev,
+                                     plan->grid_fwd_x, plan->smem_fwd_x, st),
+                   "map launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev, void *ws,
+                                 void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!maxv_dev) return fail(SST_EINVAL, "output pointer is NULL");
+    return run_gamma(plan, x_dev, ws, (cudaStream_t)stream, maxv_dev);
+}
+
+SST_API sst_status sst_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return SST_OK;
+}
+
+SST_API uint64_t sst_launch_count(void) { return g_launches.load(); }
+
+SST_API sst_status sst_profile_enable(int on) {
+    g_prof_on.store(on ? 1 : 0);
+    return SST_OK;
+}
+
+SST_API sst_status sst_profile_collect(double *ms, uint64_t *counts) {
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof);
+    }
+    if (ms) for (int i = 0; i < SST_PROFILE_KINDS; ++i) ms[i] = 0.0;
+    if (counts) for (int i = 0; i < SST_PROFILE_KINDS; ++i) counts[i] = 0;
+    sst_status st = SST_OK;
+    for (auto &r : recs) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && st == SST_OK) st = cuda_fail(e, "profile event");
+        if (ms) ms[r.kind] += t;
+        if (counts) counts[r.kind] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    return st;
+}
+
+SST_API const char *sst_profile_kind_name(int kind) {
+    if (kind < 0 || kind >= SST_PROFILE_KINDS) return "";
+    return kPkNames[kind];
+}
+
+SST_API const char *sst_status_string(sst_status s) {
+    switch (s) {
+        case SST_OK: return "SST_OK";
+        case SST_EINVAL: return "SST_EINVAL";
+        case SST_ENOMEM: return "SST_ENOMEM";
+        case SST_ECUDA: return "SST_ECUDA";
+        case SST_EBUSY: return "SST_EBUSY";
+        case SST_ETIMEOUT: return "SST_ETIMEOUT";
+        case SST_EUNSUPPORTED: return "SST_EUNSUPPORTED";
+        case SST_EINTERNAL: return "SST_EINTERNAL";
+    }
+    return "SST_<unknown>";
+}
+
+SST_API const char *sst_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,30 @@
+// Device-side view of a plan, passed to every kernel by value.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sst {
+
+struct SstDev {
+    // tables (device pointers owned by the plan)
+    const float2 *win;  // (g[j], g'[j]) for j = -M..M, L entries
+    const float *g;     // g[j], L entries
+    const float2 *tw;   // exp(-2 pi i q / nf), q in [0, nf)
+    const float2 *twz;  // exp(+2 pi i q / (z nf)), q in [0, z nf)
+    const float *rD_left;   // 1 / D[p] for p in [0, EL)
+    const float *rD_per;    // 1 / D[p] for p in [EL, ER), indexed by p mod hop
+    const float *rD_right;  // 1 / D[p] for p in [ER, n)
+    int64_t n, F;
+    int64_t EL, ER;
+    int L, M, hop, nf, z;
+    int k_lo, k_hi, nb, nbo;
+    int log2_nb;        // ceil(log2(nb))
+    float c_if;         // nf / (2 pi)
+    float gamma2_abs;   // absolute threshold squared
+    int relative;       // threshold from the pre-pass
+    int B;              // frames per inverse tile (even)
+    int seg_len;        // (B - 1) hop + L
+    int64_t ntiles;
+};
+
+}  // namespace sst

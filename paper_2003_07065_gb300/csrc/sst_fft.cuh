@@ -1,0 +1,187 @@
+// Shared-memory Stockham FFT for one frame of NF complex float32 points,
+// executed cooperatively by TPF threads of a CTA.
+//
+// Layout: the frame lives in shared memory as float2 with one pad element
+// after every 16 (index i -> i + i/16), which keeps the stride-16 scatter of
+// the first radix-16 pass free of bank conflicts.  Each pass loads R points
+// per butterfly into registers, applies the Stockham twiddles
+// W_{Ns R}^{r k} (read from a table of W_NF^i = exp(-2 pi i i / NF) built in
+// FP64 on the host and rounded), runs a radix-R DFT in registers and stores
+// the results in autosorted order.  Passes: radix 16 while possible, then one
+// radix 2, 4 or 8 pass; output in natural order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sst {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+__host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+// sqrt(1/2), cos(pi/8), sin(pi/8)
+#define SST_R2 0.70710678118654752440f
+#define SST_C8 0.92387953251128675613f
+#define SST_S8 0.38268343236508977173f
+
+template <bool INV> __device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
+    float2 t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <bool INV> __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    float2 s0 = cadd(a0, a2), d0 = csub(a0, a2);
+    float2 s1 = cadd(a1, a3), d1 = rot90<INV>(csub(a1, a3));
+    a0 = cadd(s0, s1);
+    a2 = csub(s0, s1);
+    a1 = cadd(d0, d1);
+    a3 = csub(d0, d1);
+}
+
+// multiply by W8^k (forward: exp(-i pi k / 4)), k = 1, 3
+template <bool INV> __device__ __forceinline__ float2 w8_1(float2 a) {
+    // forward: (1 - i)/sqrt2 ; inverse: (1 + i)/sqrt2
+    return INV ? make_float2(SST_R2 * (a.x - a.y), SST_R2 * (a.x + a.y))
+               : make_float2(SST_R2 * (a.x + a.y), SST_R2 * (a.y - a.x));
+}
+template <bool INV> __device__ __forceinline__ float2 w8_3(float2 a) {
+    // forward: (-1 - i)/sqrt2 ; inverse: (-1 + i)/sqrt2
+    return INV ? make_float2(-SST_R2 * (a.x + a.y), SST_R2 * (a.x - a.y))
+               : make_float2(SST_R2 * (a.y - a.x), -SST_R2 * (a.x + a.y));
+}
+
+// 8-point DFT: two 4-point DFTs of the even and odd samples, then W8 combine
+template <bool INV> __device__ __forceinline__ void dft8(float2 *v) {
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    float2 o1 = w8_1<INV>(v[3]);
+    float2 o2 = rot90<INV>(v[5]);
+    float2 o3 = w8_3<INV>(v[7]);
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+// multiply by W16^e for e in 0..9 (forward exp(-2 pi i e / 16))
+template <bool INV, int E> __device__ __forceinline__ float2 w16(float2 a) {
+    constexpr float c[10] = {1.f, SST_C8, SST_R2, SST_S8, 0.f, -SST_S8, -SST_R2, -SST_C8, -1.f, -SST_C8};
+    constexpr float s[10] = {0.f, SST_S8, SST_R2, SST_C8, 1.f, SST_C8, SST_R2, SST_S8, 0.f, -SST_S8};
+    // forward multiplier: c - i s ; inverse: c + i s
+    if (E == 0) return a;
+    if (E == 4) return rot90<INV>(a);
+    const float cc = c[E], ss = INV ? s[E] : -s[E];
+    return make_float2(a.x * cc - a.y * ss, a.x * ss + a.y * cc);
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV> __device__ __forceinline__ void dft16(float2 *v) {
+    // step 1: for each n2, DFT4 over n1 of v[4 n1 + n2]; result Y[n2][k1] kept at v[4 k1 + n2]
+    dft4<INV>(v[0], v[4], v[8], v[12]);
+    dft4<INV>(v[1], v[5], v[9], v[13]);
+    dft4<INV>(v[2], v[6], v[10], v[14]);
+    dft4<INV>(v[3], v[7], v[11], v[15]);
+    // step 2: twiddle Y[n2][k1] *= W16^{n2 k1}
+    v[5] = w16<INV, 1>(v[5]);
+    v[9] = w16<INV, 2>(v[9]);
+    v[13] = w16<INV, 3>(v[13]);
+    v[6] = w16<INV, 2>(v[6]);
+    v[10] = w16<INV, 4>(v[10]);
+    v[14] = w16<INV, 6>(v[14]);
+    v[7] = w16<INV, 3>(v[7]);
+    v[11] = w16<INV, 6>(v[11]);
+    v[15] = w16<INV, 9>(v[15]);
+    // step 3: for each k1, DFT4 over n2 of Y[n2][k1] (at v[4 k1 + n2]) -> X[k1 + 4 k2]
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+    dft4<INV>(v[4], v[5], v[6], v[7]);
+    dft4<INV>(v[8], v[9], v[10], v[11]);
+    dft4<INV>(v[12], v[13], v[14], v[15]);
+    // now X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4x4 index
+    float2 t;
+    t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[2]; v[2] = v[8]; v[8] = t;
+    t = v[3]; v[3] = v[12]; v[12] = t;
+    t = v[6]; v[6] = v[9]; v[9] = t;
+    t = v[7]; v[7] = v[13]; v[13] = t;
+    t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <int R, bool INV> __device__ __forceinline__ void dft_r(float2 *v) {
+    if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<INV>(v);
+    else dft16<INV>(v);
+}
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+// One Stockham pass of radix R with span NS (product of earlier radices).
+template <int NF, int TPF, int R, int NS, bool INV>
+__device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    constexpr int NBF = NF / R;                   // butterflies in this pass
+    constexpr int PER = (NBF + TPF - 1) / TPF;    // butterflies per thread
+    constexpr int TWSHIFT = ilog2c(NF / (NS * R));
+    float2 v[PER][R];
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int j = tid + b * TPF;
+        if (PER * TPF == NBF || j < NBF) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = buf[padded(j + r * NBF)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int j = tid + b * TPF;
+        if (PER * TPF == NBF || j < NBF) {
+            const int k = j & (NS - 1);
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[(r * k) << TWSHIFT]);
+                    if (INV) w.y = -w.y;
+                    v[b][r] = cmul(v[b][r], w);
+                }
+            }
+            dft_r<R, INV>(v[b]);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[padded(base + r * NS)] = v[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int NF, int TPF, int NS, bool INV>
+__device__ __forceinline__ void fft_passes(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    if constexpr (NS * 16 <= NF) {
+        stockham_pass<NF, TPF, 16, NS, INV>(buf, tw, tid);
+        fft_passes<NF, TPF, NS * 16, INV>(buf, tw, tid);
+    } else if constexpr (NS < NF) {
+        constexpr int R = NF / NS;  // 2, 4 or 8
+        stockham_pass<NF, TPF, R, NS, INV>(buf, tw, tid);
+    }
+}
+
+// In-place FFT of buf (padded layout). Caller must __syncthreads() after
+// writing buf; the FFT ends with a __syncthreads().  Forward uses
+// exp(-2 pi i k n / NF), inverse exp(+...), both unnormalised.
+template <int NF, int TPF, bool INV>
+__device__ __forceinline__ void fft(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    fft_passes<NF, TPF, 1, INV>(buf, tw, tid);
+}
+
+}  // namespace sst

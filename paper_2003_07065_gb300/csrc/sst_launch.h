@@ -1,0 +1,31 @@
+// Per-NF launcher table: every NF-templated kernel is instantiated in its own
+// translation unit (sst_inst.cu compiled once per NF) and reached through
+// this table, so the host code needs no templates.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "sst_dev.h"
+
+namespace sst {
+
+enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_COUNT = 5 };
+
+struct KernelTable {
+    int nf;
+    int tpf;             // threads per CTA
+    size_t smem_frame;   // bytes of the padded frame buffer plus reduction scratch
+    // raise the dynamic shared-memory limit of a kernel kind
+    cudaError_t (*set_smem)(int kind, size_t bytes);
+    // resident CTAs per SM for a kernel kind at a dynamic shared-memory size
+    cudaError_t (*occupancy)(int kind, size_t bytes, int *blocks);
+    cudaError_t (*absmax)(const SstDev &d, const float *x, float *partial, int grid, size_t smem,
+                          cudaStream_t st);
+    cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const float *gamma2, void *out0,
+                           void *out1, int grid, size_t smem, cudaStream_t st);
+    cudaError_t (*inverse)(const SstDev &d, const float2 *T, float *partial, size_t smem, cudaStream_t st);
+};
+
+const KernelTable *table_for_nf(int nf);
+
+}  // namespace sst

@@ -1,0 +1,280 @@
+"""ctypes binding of libsst.so (declared in include/sst.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name, passing device pointers (``tensor.data_ptr()``) and the
+``cudaStream_t`` of a torch stream.  The library must have been built
+(``paper_2003_07065_gb300.build.build()``); loading fails loudly otherwise,
+and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SST_GAMMA_RELATIVE = 0x1
+STATUS = {0: "SST_OK", 1: "SST_EINVAL", 2: "SST_ENOMEM", 3: "SST_ECUDA", 4: "SST_EBUSY",
+          5: "SST_ETIMEOUT", 6: "SST_EUNSUPPORTED", 7: "SST_EINTERNAL"}
+
+
+class SstError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sst_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("fs", ctypes.c_double), ("L", ctypes.c_int32),
+                ("sigma", ctypes.c_double), ("g", ctypes.POINTER(ctypes.c_double)),
+                ("dg", ctypes.POINTER(ctypes.c_double)), ("hop", ctypes.c_int32),
+                ("nfft", ctypes.c_int32), ("f_lo", ctypes.c_double), ("f_hi", ctypes.c_double),
+                ("z", ctypes.c_int32), ("gamma", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsst.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsst.so not built at {path}: run paper_2003_07065_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "sst_plan_create": ([ctypes.POINTER(sst_params), ctypes.POINTER(_vp)], ctypes.c_int),
+        "sst_plan_destroy": ([_vp], None),
+        "sst_plan_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sst_forward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_forward_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_forward_inverse_host": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_stft": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_sync": ([_vp], ctypes.c_int),
+        "sst_launch_count": ([], ctypes.c_uint64),
+        "sst_profile_enable": ([ctypes.c_int], ctypes.c_int),
+        "sst_profile_collect": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+                                ctypes.c_int),
+        "sst_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
+        "sst_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "sst_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SstError(status, load().sst_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
+                    z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
+                    g=None, dg=None) -> int:
+    """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows."""
+    lib = load()
+    p = sst_params()
+    p.n, p.fs, p.L = int(n), float(fs), int(L)
+    p.sigma = float(sigma) if sigma is not None else 0.0
+    keep = []
+    if g is not None:
+        import numpy as np
+        ga = np.ascontiguousarray(g, dtype=np.float64)
+        da = np.ascontiguousarray(dg, dtype=np.float64)
+        keep = [ga, da]
+        p.g = ga.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.dg = da.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.hop, p.nfft = int(hop), int(nfft)
+    p.f_lo, p.f_hi, p.z = float(f_lo), float(f_hi), int(z)
+    p.gamma = float(gamma)
+    p.flags = SST_GAMMA_RELATIVE if relative else 0
+    out = _vp()
+    _check(lib.sst_plan_create(ctypes.byref(p), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def sst_plan_destroy(plan: int) -> None:
+    load().sst_plan_destroy(plan)
+
+
+def sst_plan_query(plan: int) -> dict:
+    f, b, lo, hi, ws = _i64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _check(load().sst_plan_query(plan, ctypes.byref(f), ctypes.byref(b), ctypes.byref(lo),
+                                 ctypes.byref(hi), ctypes.byref(ws)))
+    return {"frames": f.value, "bins": b.value, "k_lo": lo.value, "k_hi": hi.value,
+            "workspace_bytes": ws.value}
+
+
+def sst_forward(plan, x, n, tfr, workspace, stream=None):
+    _check(load().sst_forward(plan, _ptr(x), n, _ptr(tfr), _ptr(workspace), _stream(stream)))
+
+
+def sst_inverse(plan, tfr, n, xhat, workspace, stream=None):
+    _check(load().sst_inverse(plan, _ptr(tfr), n, _ptr(xhat), _ptr(workspace), _stream(stream)))
+
+
+def sst_forward_inverse(plan, x, n, tfr, xhat, workspace, stream=None):
+    _check(load().sst_forward_inverse(plan, _ptr(x), n, _ptr(tfr), _ptr(xhat), _ptr(workspace),
+                                      _stream(stream)))
+
+
+def sst_forward_inverse_host(plan, x_host, n, xhat_host, x_dev, tfr_dev, xhat_dev, workspace,
+                             stream=None):
+    _check(load().sst_forward_inverse_host(plan, _ptr(x_host), n, _ptr(xhat_host), _ptr(x_dev),
+                                           _ptr(tfr_dev), _ptr(xhat_dev), _ptr(workspace),
+                                           _stream(stream)))
+
+
+def sst_stft(plan, x, n, V, Vd, workspace, stream=None):
+    _check(load().sst_stft(plan, _ptr(x), n, _ptr(V), _ptr(Vd), _ptr(workspace), _stream(stream)))
+
+
+def sst_reassign_map(plan, x, n, omega, dest, workspace, stream=None):
+    _check(load().sst_reassign_map(plan, _ptr(x), n, _ptr(omega), _ptr(dest), _ptr(workspace),
+                                   _stream(stream)))
+
+
+def sst_max_abs_v(plan, x, n, maxv, workspace, stream=None):
+    _check(load().sst_max_abs_v(plan, _ptr(x), n, _ptr(maxv), _ptr(workspace), _stream(stream)))
+
+
+def sst_sync(stream=None):
+    _check(load().sst_sync(_stream(stream)))
+
+
+def sst_launch_count() -> int:
+    return int(load().sst_launch_count())
+
+
+PROFILE_KINDS = 8
+
+
+def sst_profile_enable(on: bool = True):
+    _check(load().sst_profile_enable(1 if on else 0))
+
+
+def sst_profile_collect() -> dict:
+    """{kind name: (total ms, launches)} since the last collect."""
+    ms = (ctypes.c_double * PROFILE_KINDS)()
+    ct = (ctypes.c_uint64 * PROFILE_KINDS)()
+    _check(load().sst_profile_collect(ms, ct))
+    out = {}
+    for i in range(PROFILE_KINDS):
+        if ct[i]:
+            out[load().sst_profile_kind_name(i).decode()] = (ms[i], int(ct[i]))
+    return out
+
+
+def sst_status_string(s: int) -> str:
+    return load().sst_status_string(s).decode()
+
+
+def sst_last_error() -> str:
+    return load().sst_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ torch helper
+class Plan:
+    """Owns a plan handle and the device buffers one signal needs (torch
+    tensors on the current device): workspace, TFR and reconstruction."""
+
+    def __init__(self, **kw):
+        import torch
+        self.handle = sst_plan_create(**kw)
+        q = sst_plan_query(self.handle)
+        self.frames, self.bins = q["frames"], q["bins"]
+        self.k_lo, self.k_hi = q["k_lo"], q["k_hi"]
+        self.nb = self.k_hi - self.k_lo + 1
+        self.n = int(kw["n"])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(q["workspace_bytes"], 256), dtype=torch.uint8, device=dev)
+        self.device = dev
+
+    def new_tfr(self):
+        import torch
+        return torch.empty((self.frames, self.bins, 2), dtype=torch.float32, device=self.device)
+
+    def forward(self, x, tfr=None):
+        tfr = self.new_tfr() if tfr is None else tfr
+        sst_forward(self.handle, x, self.n, tfr, self.workspace)
+        return tfr
+
+    def inverse(self, tfr, xhat=None):
+        import torch
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
+        sst_inverse(self.handle, tfr, self.n, xhat, self.workspace)
+        return xhat
+
+    def forward_inverse(self, x, tfr=None, xhat=None):
+        import torch
+        tfr = self.new_tfr() if tfr is None else tfr
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
+        sst_forward_inverse(self.handle, x, self.n, tfr, xhat, self.workspace)
+        return tfr, xhat
+
+    def stft(self, x):
+        import torch
+        V = torch.empty((self.frames, self.nb, 2), dtype=torch.float32, device=self.device)
+        Vd = torch.empty_like(V)
+        sst_stft(self.handle, x, self.n, V, Vd, self.workspace)
+        return V, Vd
+
+    def reassign_map(self, x):
+        import torch
+        om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
+        de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
+        sst_reassign_map(self.handle, x, self.n, om, de, self.workspace)
+        return om, de
+
+    def max_abs_v(self, x):
+        import torch
+        out = torch.empty(1, dtype=torch.float32, device=self.device)
+        sst_max_abs_v(self.handle, x, self.n, out, self.workspace)
+        return out
+
+    def close(self):
+        if self.handle:
+            sst_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,90 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/sst.h declares, and validates arguments on the host
+(no GPU is touched: invalid parameters are rejected before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2003_07065_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sst_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build.build()
+    from paper_2003_07065_gb300 import sst as S
+    S.load()
+    return S
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("sst_plan_create", "sst_forward", "sst_inverse", "sst_forward_inverse", "sst_plan_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(build.LIB)
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.sst_status_string(0) == "SST_OK"
+    assert lib.sst_status_string(1) == "SST_EINVAL"
+    assert lib.sst_status_string(6) == "SST_EUNSUPPORTED"
+
+
+BAD = [
+    (dict(L=64), "L must be odd"),
+    (dict(nfft=1000), "power of two"),
+    (dict(nfft=32), "power of two"),
+    (dict(hop=0), "hop"),
+    (dict(hop=40), "hop"),
+    (dict(f_lo=300.0, f_hi=200.0), "band"),
+    (dict(f_hi=600.0), "band"),
+    (dict(z=0), "z must"),
+    (dict(z=17), "z must"),
+    (dict(gamma=-1.0), "gamma"),
+    (dict(n=0), "n must"),
+    (dict(sigma=0.0), "sigma"),
+]
+
+
+@pytest.mark.parametrize("change,msg", BAD)
+def test_invalid_parameters_rejected_on_host(lib, change, msg):
+    kw = dict(n=1000, fs=1000.0, L=65, sigma=8.0, hop=8, nfft=64, f_lo=0.0, f_hi=500.0, z=1,
+              gamma=1e-3, relative=True)
+    kw.update(change)
+    with pytest.raises(lib.SstError) as e:
+        lib.sst_plan_create(**kw)
+    assert e.value.status == 1
+    assert msg in str(e.value)
+
+
+def test_window_longer_than_nfft_plus_one_unsupported(lib):
+    with pytest.raises(lib.SstError) as e:
+        lib.sst_plan_create(n=1000, fs=1000.0, L=67, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
+    assert e.value.status == 6
+
+
+def test_null_arguments(lib):
+    L = lib.load()
+    assert L.sst_plan_create(None, None) == 1
+    assert L.sst_forward(None, None, 0, None, None, None) == 1
+    assert L.sst_plan_query(None, None, None, None, None, None) == 1
+    L.sst_plan_destroy(None)

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (the oracle reads the same float32 samples, widened).
+
+Covers the small chirp/FM workload and the run-up workload at 2^18 - 37
+samples (many inverse tiles and a ragged tail) element by element, the
+degenerate cases (tiny signals, a one-bin band, the Nyquist band, L = Nf + 1
+folding, zero threshold), and run-to-run bit determinism."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_07065_gb300 import workloads as W
+
+from parity import (SNR_DB, XHAT_RTOL, as_complex, check_map, check_mass, check_stft,
+                    check_tfr, snr_db)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_07065_gb300 import build, sst as S
+    build.build()
+    S.load()
+    return S
+
+
+def run_gpu(S, params, x32):
+    plan = S.Plan(**params)
+    x = torch.from_numpy(x32).cuda()
+    V, Vd = plan.stft(x)
+    om, dest = plan.reassign_map(x)
+    tfr, xhat = plan.forward_inverse(x)
+    maxv = plan.max_abs_v(x)
+    torch.cuda.synchronize()
+    out = dict(V=as_complex(V.cpu().numpy()), Vd=as_complex(Vd.cpu().numpy()),
+               omega=om.cpu().numpy(), dest=dest.cpu().numpy(), T=as_complex(tfr.cpu().numpy()),
+               xhat=xhat.cpu().numpy().astype(np.float64), maxv=float(maxv.item()),
+               k_lo=plan.k_lo, k_hi=plan.k_hi, bins=plan.bins)
+    plan.close()
+    return out
+
+
+def run_oracle(params, x32):
+    p = dict(params)
+    x = x32.astype(np.float64)
+    r = O.sst(x, p["fs"], p["L"], p["sigma"], p["hop"], p["nfft"], p["f_lo"], p["f_hi"], p["z"],
+              p["gamma"], p["relative"], inverse_range=(0, len(x)))
+    return r
+
+
+def compare(g, r, params, clean=None):
+    assert (g["k_lo"], g["k_hi"]) == (r.k_lo, r.k_hi)
+    assert g["bins"] == r.T.shape[1]
+    stats = {}
+    stats["stft"] = check_stft(g["V"], r.V, "V")
+    stats["stft_d"] = check_stft(g["Vd"], r.Vd, "Vd")
+    if params["relative"]:
+        vmax = np.abs(r.V).max()
+        assert abs(g["maxv"] - vmax) <= 1e-5 * vmax
+    moved, rate = check_map(g["dest"], r.dest, r.V, r.gamma, r.T.shape[1])
+    stats["map_rate"] = rate
+    stats["tfr"] = check_tfr(g["T"], r.T, r.V, moved, g["dest"], r.dest)
+    stats["mass"] = check_mass(g["T"], r.T, r.V, r.gamma, moved)
+    # reconstruction
+    xo = r.xhat
+    allow = 0.0
+    if moved.any():
+        # a source moved by one fine bin changes r~ by at most
+        # (2/Nf) |V| |1 - exp(i 2 pi j / (z Nf))| <= (2/Nf) |V| 2 pi M / (z Nf) per frame,
+        # summed over the <= L/hop frames covering a sample, divided by min D
+        nf, z, M, hop = params["nfft"], params["z"], (params["L"] - 1) // 2, params["hop"]
+        per = (2.0 / nf) * np.abs(r.V[moved]).max() * min(2.0, 2 * np.pi * M / (z * nf))
+        allow = per * np.ceil(params["L"] / hop) / (np.sqrt(2.0) / hop * 0.5)
+    err = np.abs(g["xhat"] - xo)
+    stats["xhat"] = err.max() / np.abs(xo).max()
+    assert err.max() <= XHAT_RTOL * np.abs(xo).max() + allow, f"xhat max err {err.max():.3e}"
+    if clean is not None:
+        s_g, s_o = snr_db(clean, g["xhat"]), snr_db(clean, xo)
+        stats["snr_gpu"], stats["snr_oracle"] = s_g, s_o
+        assert abs(s_g - s_o) <= SNR_DB, (s_g, s_o)
+    return stats
+
+
+@pytest.mark.parametrize("name", ["chirp_fm_64k", "runup_256k"])
+def test_workload_parity(sst, name):
+    w = W.ALL[name]
+    noisy, clean = w.signal()
+    x32 = noisy.astype(np.float32)
+    params = w.params()
+    g = run_gpu(sst, params, x32)
+    r = run_oracle(params, x32)
+    stats = compare(g, r, params, clean)
+    print(name, stats)
+
+
+EDGE = [
+    # n, fs, L, sigma, hop, nfft, f_lo, f_hi, z, gamma, relative
+    dict(n=1, fs=1000.0, L=65, sigma=8.0, hop=8, nfft=64, f_lo=0.0, f_hi=500.0, z=1, gamma=0.0, relative=False),
+    dict(n=100, fs=1000.0, L=65, sigma=8.0, hop=8, nfft=64, f_lo=0.0, f_hi=500.0, z=2, gamma=1e-3, relative=True),
+    dict(n=999, fs=1000.0, L=129, sigma=16.0, hop=5, nfft=128, f_lo=100.0, f_hi=100.0 + 1e-9, z=3,
+         gamma=1e-3, relative=True),
+    dict(n=3001, fs=2000.0, L=257, sigma=32.0, hop=7, nfft=256, f_lo=700.0, f_hi=1000.0, z=4, gamma=1e-3,
+         relative=True),
+    dict(n=5000, fs=8000.0, L=1025, sigma=128.0, hop=16, nfft=1024, f_lo=0.0, f_hi=4000.0, z=2, gamma=1e-4,
+         relative=True),
+    dict(n=7777, fs=8000.0, L=513, sigma=64.0, hop=31, nfft=512, f_lo=1000.0, f_hi=3000.0, z=1, gamma=0.0,
+         relative=False),
+    dict(n=20000, fs=16000.0, L=4097, sigma=512.0, hop=64, nfft=8192, f_lo=0.0, f_hi=2000.0, z=2, gamma=1e-3,
+         relative=True),
+    dict(n=12000, fs=16000.0, L=2049, sigma=256.0, hop=16, nfft=2048, f_lo=3000.0, f_hi=8000.0, z=1,
+         gamma=1e-3, relative=True),
+]
+
+
+@pytest.mark.parametrize("params", EDGE, ids=[f"n{p['n']}_nf{p['nfft']}_z{p['z']}" for p in EDGE])
+def test_edge_cases(sst, params):
+    gen = np.random.default_rng(params["n"])
+    t = np.arange(params["n"]) / params["fs"]
+    mid = 0.5 * (params["f_lo"] + params["f_hi"])
+    x = np.cos(2 * np.pi * mid * t + 0.3) + 0.3 * gen.standard_normal(params["n"])
+    x32 = x.astype(np.float32)
+    g = run_gpu(sst, params, x32)
+    r = run_oracle(params, x32)
+    compare(g, r, params)
+
+
+def test_deterministic(sst):
+    w = W.CHIRP_FM_64K
+    x = torch.from_numpy(w.signal()[0].astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    t1, x1 = plan.forward_inverse(x)
+    t2, x2 = plan.forward_inverse(x)
+    torch.cuda.synchronize()
+    assert torch.equal(t1, t2) and torch.equal(x1, x2)
+    plan.close()
+
+
+def test_plan_errors(sst):
+    with pytest.raises(sst.SstError) as e:
+        sst.sst_plan_create(n=100, fs=1000.0, L=64, hop=8, nfft=64, f_lo=0, f_hi=500, sigma=8.0)
+    assert e.value.status == 1
+    p = sst.Plan(n=1000, fs=1000.0, L=65, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
+    x = torch.zeros(999, device="cuda")
+    with pytest.raises(sst.SstError):
+        sst.sst_forward(p.handle, x, 999, p.new_tfr(), p.workspace)
+    p.close()
