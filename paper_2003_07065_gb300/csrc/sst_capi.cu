@@ -263,9 +263,17 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     for (int64_t q = ER; q < n; ++q)
         if (!std::isfinite(rDr[q - ER])) { delete pl; return fail(SST_EINVAL, "normaliser vanishes at sample %lld", (long long)q); }
 
+    // S^g' is packed as the imaginary part with the window s g', s = 2^round(log2(|g| / |g'|)),
+    // so both halves of the packed FFT carry similar norms; 1/s is applied exactly afterwards
+    double ng = 0.0, ndg = 0.0;
+    for (int i = 0; i < L; ++i) { ng += g[i] * g[i]; ndg += dg[i] * dg[i]; }
+    int sexp = (ndg > 0.0) ? (int)std::lround(0.5 * std::log2(ng / ndg)) : 0;
+    if (sexp < -60) sexp = -60;
+    if (sexp > 60) sexp = 60;
+    const double dsc = std::ldexp(1.0, sexp);
     std::vector<float2> win(L), tw(nf), twz(G);
     std::vector<float> gf(L);
-    for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)dg[i]); gf[i] = (float)g[i]; }
+    for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)(dg[i] * dsc)); gf[i] = (float)g[i]; }
     for (int q = 0; q < nf; ++q) {
         const double a = -2.0 * M_PI * (double)q / (double)nf;
         tw[q] = make_float2((float)std::cos(a), (float)std::sin(a));
@@ -319,7 +327,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     int lg = 0;
     while ((1 << lg) < nb) ++lg;
     d.log2_nb = lg;
-    d.c_if = (float)((double)nf / (2.0 * M_PI));
+    d.c_if = (float)((double)nf / (2.0 * M_PI) / dsc);
+    d.dscale = (float)(1.0 / dsc);
     d.relative = (p.flags & SST_GAMMA_RELATIVE) ? 1 : 0;
     d.gamma2_abs = d.relative ? 0.f : (float)(p.gamma * p.gamma);
     pl->gamma_frac2 = (float)(p.gamma * p.gamma);

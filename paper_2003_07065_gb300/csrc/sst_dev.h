@@ -19,7 +19,8 @@ struct SstDev {
     int L, M, hop, nf, z;
     int k_lo, k_hi, nb, nbo;
     int log2_nb;        // ceil(log2(nb))
-    float c_if;         // nf / (2 pi)
+    float c_if;         // nf / (2 pi s): IF offset factor for the packed, scaled S^g'
+    float dscale;       // 1 / s: the packed imaginary part carries s g' (s a power of two)
     float gamma2_abs;   // absolute threshold squared
     int relative;       // threshold from the pre-pass
     int B;              // frames per inverse tile (even)

@@ -39,7 +39,9 @@ template <int NWARP> __device__ __forceinline__ float block_max(float v, float *
 
 // Gather frame m (or the pair m, m2 into re/im) with window folding mod NF:
 // buf[p] = sum_{j = p mod NF, |j| <= M} x[m hop + j] * win[j]   (Eq. 8-9).
-// PAIR = false: win = (g, g'), value = x (g + i g')
+// PAIR = false: win = (g, s g'), value = x (g + i s g'); s is a power of two
+//               that equalises the two halves' norms (so neither half's FFT
+//               rounding swamps the other) and is undone exactly afterwards
 // PAIR = true : value = (x_m + i x_m2) g
 template <int NF, bool PAIR>
 __device__ __forceinline__ void gather_frame(float2 *buf, const SstDev &d, const float *__restrict__ x,
@@ -166,7 +168,7 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
                 const size_t o = (size_t)m * d.nb + kk;
                 if (MODE == MODE_STFT) {
                     out0[o] = V;
-                    reinterpret_cast<float2 *>(out1)[o] = Vd;
+                    reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
                     continue;
                 }
                 const float mag2 = V.x * V.x + V.y * V.y;
