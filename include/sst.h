@@ -142,6 +142,28 @@ sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, floa
 sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev,
                          void *workspace_dev, void *stream);
 
+/* Forward SST (as sst_forward) that allocates nothing and takes no
+ * workspace.  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc at the point where they run the transform, e.g. a
+ * plug-in inside a host application whose device memory is entirely owned by
+ * that application's own pool, or a latency-critical loop that must not hit
+ * cudaMalloc's implicit device synchronisation.  (Creating the plan still
+ * allocates its tables; do that at set-up time.)
+ *   x_dev   : n floats; tfr_dev : F x bins complex, fully overwritten.
+ * Scratch (the relative-threshold pre-pass's per-CTA maxima and gamma^2)
+ * lives in one file-scope device array of SST_STATIC_SCRATCH_BYTES inside
+ * libsst.so; every GPU that loads the library holds it until the process
+ * exits.  Plans whose pre-pass needs more than the array holds are rejected
+ * with SST_EUNSUPPORTED and a message giving both sizes.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; every
+ * element a call reads is written earlier in the same call, so nothing needs
+ * clearing.  Calls whose work overlaps on the GPU (other streams, other
+ * threads, other plans) race on the array: serialise them. */
+#define SST_STATIC_SCRATCH_BYTES 65536
+sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *stream);
+
 /* Block until `stream` is idle; returns SST_ECUDA with the message of any
  * pending asynchronous error. */
 sst_status sst_sync(void *stream);

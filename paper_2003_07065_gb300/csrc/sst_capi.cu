@@ -526,6 +526,61 @@ SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n,
     return run_gamma(plan, x_dev, ws, (cudaStream_t)stream, maxv_dev);
 }
 
+// ------------------------------------------------------------ no-allocation forward
+// Scratch for sst_forward_static: [0] gamma^2, [1] max |S^g|, [64 ...) one
+// pre-pass maximum per CTA.  Host code must not use the symbol itself as an
+// address (on the host it names a shadow variable); the device address is
+// looked up once per device and cached.
+static constexpr size_t kStaticFloats = SST_STATIC_SCRATCH_BYTES / sizeof(float);
+static constexpr size_t kStaticHeader = 64;
+static __device__ __align__(256) float g_static_scratch[kStaticFloats];
+static std::mutex g_static_mu;
+static float *g_static_addr[256];
+
+static sst_status static_scratch_address(int dev, float **out) {
+    if (dev < 0 || dev >= 256) return fail(SST_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
+        g_static_addr[dev] = (float *)p;
+    }
+    *out = g_static_addr[dev];
+    return SST_OK;
+}
+
+SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                                      void *stream) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    if (!x_dev || !tfr_dev) return fail(SST_EINVAL, "input or output pointer is NULL");
+    if (n != plan->d.n)
+        return fail(SST_EINVAL, "n = %lld differs from the plan's n = %lld", (long long)n, (long long)plan->d.n);
+    const size_t need = kStaticHeader + (size_t)plan->grid_absmax;
+    if (need > kStaticFloats)
+        return fail(SST_EUNSUPPORTED, "this plan's pre-pass needs %zu scratch floats; the static array holds %zu",
+                    need, kStaticFloats);
+    int dev = -1;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != plan->device) return fail(SST_EINVAL, "plan was created on device %d, current is %d", plan->device, dev);
+    float *scratch = nullptr;
+    sst_status s = static_scratch_address(dev, &scratch);
+    if (s != SST_OK) return s;
+    float *gamma2 = scratch, *maxv = scratch + 1, *partial = scratch + kStaticHeader;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->d.relative) {
+        SST_CU(plan->kt->absmax(plan->d, x_dev, partial, plan->grid_absmax, plan->smem_absmax, st), "absmax launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        k_gamma<<<1, 256, 0, st>>>(partial, plan->grid_absmax, plan->gamma_frac2, gamma2, maxv);
+        SST_CU(cudaGetLastError(), "gamma launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, gamma2, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
+           "forward launch");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return SST_OK;
+}
+
 SST_API sst_status sst_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");

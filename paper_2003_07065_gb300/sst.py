@@ -63,6 +63,7 @@ def load():
         "sst_stft": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
         "sst_sync": ([_vp], ctypes.c_int),
         "sst_launch_count": ([], ctypes.c_uint64),
         "sst_profile_enable": ([ctypes.c_int], ctypes.c_int),
@@ -172,6 +173,10 @@ def sst_reassign_map(plan, x, n, omega, dest, workspace, stream=None):
 
 def sst_max_abs_v(plan, x, n, maxv, workspace, stream=None):
     _check(load().sst_max_abs_v(plan, _ptr(x), n, _ptr(maxv), _ptr(workspace), _stream(stream)))
+
+
+def sst_forward_static(plan, x, n, tfr, stream=None):
+    _check(load().sst_forward_static(plan, _ptr(x), n, _ptr(tfr), _stream(stream)))
 
 
 def sst_sync(stream=None):

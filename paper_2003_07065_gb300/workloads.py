@@ -10,6 +10,7 @@ runup_16m      N = 2^24 at 51.2 kHz run-up vibration (orders 1, 2, 3.5, 7 of a
                gamma = 1e-3 max|V|.
 runup_256k     the run-up recipe and parameters at N = 2^18 - 37 (a ragged
                tail), small enough for the oracle to check every output.
+runup_4m       the run-up recipe at N = 2^22 (profiling-sized: 2.1 GB TFR).
 precision_64k  chirp_fm_64k's signal with Nf 4096, L = 2049, sigma = 256,
                hop 16, band 0-6.4 kHz (bins 0..1024), z = 1.
 """
@@ -63,7 +64,8 @@ CHIRP_FM_64K = Workload("chirp_fm_64k", 65536, 25600.0, 1025, 128.0, 16, 1024, 0
 RUNUP_16M = Workload("runup_16m", 1 << 24, 51200.0, 2049, 256.0, 32, 4096, 0.0, 6400.0, 4,
                      1e-3, True, "runup")
 RUNUP_256K = RUNUP_16M.with_n((1 << 18) - 37, "runup_256k")
+RUNUP_4M = RUNUP_16M.with_n(1 << 22, "runup_4m")
 PRECISION_64K = Workload("precision_64k", 65536, 25600.0, 2049, 256.0, 16, 4096, 0.0, 6400.0, 1,
                          1e-3, True, "chirp_fm")
 
-ALL = {w.name: w for w in (CHIRP_FM_64K, RUNUP_16M, RUNUP_256K, PRECISION_64K)}
+ALL = {w.name: w for w in (CHIRP_FM_64K, RUNUP_16M, RUNUP_256K, RUNUP_4M, PRECISION_64K)}
