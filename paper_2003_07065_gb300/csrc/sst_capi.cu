@@ -157,6 +157,7 @@ struct sst_plan {
     void *dmem = nullptr;
     float gamma_frac2 = 0.f;
     size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
+    int inv_kind = KIND_INV;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
     size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
 };
@@ -271,23 +272,39 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     if (sexp < -60) sexp = -60;
     if (sexp > 60) sexp = 60;
     const double dsc = std::ldexp(1.0, sexp);
-    std::vector<float2> win(L), tw(nf), twz(G);
+    std::vector<float2> win(L);
     std::vector<float> gf(L);
     for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)(dg[i] * dsc)); gf[i] = (float)g[i]; }
-    for (int q = 0; q < nf; ++q) {
-        const double a = -2.0 * M_PI * (double)q / (double)nf;
-        tw[q] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    for (int q = 0; q < G; ++q) {
-        const double a = 2.0 * M_PI * (double)q / (double)G;
-        twz[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+    // Stockham twiddles, per radix-16 pass of span Ns (Ns = R1, 16 R1, ..., nf/16):
+    // entry (Ns - R1) + (r - 1) Ns + k = exp(-2 pi i r k / (16 Ns)), r in [1, 16), k in [0, Ns)
+    int lg2 = 0;
+    while ((1 << lg2) < nf) ++lg2;
+    const int R1 = (lg2 % 4 == 0) ? 16 : (1 << (lg2 % 4));
+    std::vector<float2> tw(std::max(nf - R1, 1));
+    for (int Ns = R1; Ns < nf; Ns *= 16)
+        for (int r = 1; r < 16; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                const double a = -2.0 * M_PI * (double)r * (double)k / (16.0 * Ns);
+                tw[(Ns - R1) + (r - 1) * Ns + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+    // inverse sub-grid twiddles exp(+2 pi i s n / (z nf)) by output slot q of the last pass
+    std::vector<float2> twq(G), twn(z);
+    for (int s_ = 0; s_ < z; ++s_) {
+        for (int q = 0; q < nf; ++q) {
+            const int nq_ = (q <= nf / 2) ? q : q - nf;
+            const double a = 2.0 * M_PI * (double)s_ * (double)nq_ / (double)G;
+            twq[s_ * nf + q] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        const double a = -2.0 * M_PI * (double)s_ * (double)(nf / 2) / (double)G;
+        twn[s_] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
 
     // ---- one device allocation for all tables
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    const size_t o_win = take(sizeof(float2) * L), o_g = take(sizeof(float) * L), o_tw = take(sizeof(float2) * nf),
-                 o_twz = take(sizeof(float2) * G), o_rl = take(sizeof(float) * rDl.size()),
+    const size_t o_win = take(sizeof(float2) * L), o_g = take(sizeof(float) * L),
+                 o_tw = take(sizeof(float2) * tw.size()), o_twq = take(sizeof(float2) * G),
+                 o_twn = take(sizeof(float2) * z), o_rl = take(sizeof(float) * rDl.size()),
                  o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop);
     cudaError_t ce = cudaMalloc(&pl->dmem, off);
     if (ce != cudaSuccess) { delete pl; return fail(SST_ENOMEM, "cudaMalloc of %zu table bytes failed", off); }
@@ -295,8 +312,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     std::vector<char> host(off, 0);
     memcpy(host.data() + o_win, win.data(), sizeof(float2) * L);
     memcpy(host.data() + o_g, gf.data(), sizeof(float) * L);
-    memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * nf);
-    memcpy(host.data() + o_twz, twz.data(), sizeof(float2) * G);
+    memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * tw.size());
+    memcpy(host.data() + o_twq, twq.data(), sizeof(float2) * G);
+    memcpy(host.data() + o_twn, twn.data(), sizeof(float2) * z);
     memcpy(host.data() + o_rl, rDl.data(), sizeof(float) * rDl.size());
     memcpy(host.data() + o_rr, rDr.data(), sizeof(float) * rDr.size());
     memcpy(host.data() + o_rp, rDp.data(), sizeof(float) * hop);
@@ -307,7 +325,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     d.win = (const float2 *)(base + o_win);
     d.g = (const float *)(base + o_g);
     d.tw = (const float2 *)(base + o_tw);
-    d.twz = (const float2 *)(base + o_twz);
+    d.twq = (const float2 *)(base + o_twq);
+    d.twn = (const float2 *)(base + o_twn);
     d.rD_left = (const float *)(base + o_rl);
     d.rD_right = (const float *)(base + o_rr);
     d.rD_per = (const float *)(base + o_rp);
@@ -346,7 +365,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->smem_fwd_x = kt->smem_frame;
     pl->smem_fwd_t = kt->smem_frame + 2 * sizeof(unsigned long long) * (size_t)nbo;
     pl->smem_absmax = kt->smem_frame;
-    pl->smem_inv = kt->smem_frame + sizeof(float) * (size_t)d.seg_len;
+    // inverse: frame buffer, the pair's two T rows regrouped by sub-grid, overlap-add segment
+    pl->smem_inv = kt->smem_frame + 2 * sizeof(float2) * (size_t)z * nb + sizeof(float) * (size_t)d.seg_len;
+    pl->inv_kind = (L <= nf / 2 + 1) ? KIND_INV : KIND_INV_WIDE;
     const size_t smax = prop.sharedMemPerBlockOptin;
     if (pl->smem_fwd_t > smax || pl->smem_inv > smax) {
         cudaFree(pl->dmem);
@@ -355,7 +376,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
                     pl->smem_inv, smax);
     }
     struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {KIND_FWD_T, pl->smem_fwd_t},
-        {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {KIND_INV, pl->smem_inv}};
+        {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {pl->inv_kind, pl->smem_inv}};
     for (auto &k : kinds) {
         ce = kt->set_smem(k.kind, k.bytes);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
@@ -439,7 +460,7 @@ static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *w
 }
 
 static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st) {
-    SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(pl->d, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
+    SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(pl->d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
                    "inverse launch");
     int64_t blocks = (pl->d.n + 255) / 256;
     if (blocks > 4096) blocks = 4096;

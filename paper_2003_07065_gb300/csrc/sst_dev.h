@@ -9,8 +9,10 @@ struct SstDev {
     // tables (device pointers owned by the plan)
     const float2 *win;  // (g[j], g'[j]) for j = -M..M, L entries
     const float *g;     // g[j], L entries
-    const float2 *tw;   // exp(-2 pi i q / nf), q in [0, nf)
-    const float2 *twz;  // exp(+2 pi i q / (z nf)), q in [0, z nf)
+    const float2 *tw;   // Stockham twiddles per pass, [Ns - R1 + (r - 1) Ns + k] = W_{16 Ns}^{r k}
+    const float2 *twq;  // inverse sub-grid twiddles [s nf + q] = exp(+2 pi i s n(q) / (z nf)),
+                        // n(q) = q for q <= nf/2, else q - nf
+    const float2 *twn;  // [s] = exp(-2 pi i s (nf/2) / (z nf)), for the tap n = -nf/2
     const float *rD_left;   // 1 / D[p] for p in [0, EL)
     const float *rD_per;    // 1 / D[p] for p in [EL, ER), indexed by p mod hop
     const float *rD_right;  // 1 / D[p] for p in [ER, n)

@@ -1,14 +1,19 @@
 // Shared-memory Stockham FFT for one frame of NF complex float32 points,
-// executed cooperatively by TPF threads of a CTA.
+// executed cooperatively by TPF >= NF/16 threads of a CTA.
 //
 // Layout: the frame lives in shared memory as float2 with one pad element
 // after every 16 (index i -> i + i/16), which keeps the stride-16 scatter of
 // the first radix-16 pass free of bank conflicts.  Each pass loads R points
 // per butterfly into registers, applies the Stockham twiddles
-// W_{Ns R}^{r k} (read from a table of W_NF^i = exp(-2 pi i i / NF) built in
-// FP64 on the host and rounded), runs a radix-R DFT in registers and stores
-// the results in autosorted order.  Passes: radix 16 while possible, then one
-// radix 2, 4 or 8 pass; output in natural order.
+// W_{Ns R}^{r k} = exp(-2 pi i r k / (Ns R)), runs a radix-R DFT in registers
+// and stores the results in autosorted order.  The twiddles come from a table
+// built in FP64 on the host and rounded, laid out per pass as [r - 1][k]
+// (k = butterfly mod Ns, fastest), so a warp's load for one r is contiguous:
+// the pass of span Ns (radix 16, Ns >= R1) starts at entry Ns - R1, and the
+// whole table has NF - R1 entries.  Passes: one radix 2, 4, 8 or 16 pass,
+// then radix-16 passes; output in natural order.  The first and last passes
+// are also offered with their inputs / outputs in registers so that kernels
+// can fuse the frame gather into the first and their epilogue into the last.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -132,7 +137,8 @@ template <int NF, int TPF, int R, int NS, bool INV>
 __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {
     constexpr int NBF = NF / R;                   // butterflies in this pass
     constexpr int PER = (NBF + TPF - 1) / TPF;    // butterflies per thread
-    constexpr int TWSHIFT = ilog2c(NF / (NS * R));
+    constexpr int R1 = (ilog2c(NF) % 4 == 0) ? 16 : (1 << (ilog2c(NF) % 4));
+    static_assert(NS == 1 || R == 16, "passes after the first are radix 16");
     float2 v[PER][R];
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
@@ -151,7 +157,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[(r * k) << TWSHIFT]);
+                    float2 w = __ldg(&tw[(NS - R1) + (r - 1) * NS + k]);
                     if (INV) w.y = -w.y;
                     v[b][r] = cmul(v[b][r], w);
                 }
@@ -165,23 +171,75 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
     __syncthreads();
 }
 
+// Pass plan: log2(NF) = 4a + b.  The first pass has radix R1 = 2^b (or 16
+// when b = 0) and span 1; every later pass has radix 16; the last pass has
+// span NF/16, so its butterfly j holds the outputs q = j + r NF/16.
+template <int NF> struct FftPlan {
+    static constexpr int LOG = ilog2c(NF);
+    static constexpr int R1 = (LOG % 4 == 0) ? 16 : (1 << (LOG % 4));
+    static constexpr int NS_LAST = NF / 16;
+};
+
+// Middle passes: radix 16, spans R1, 16 R1, ..., up to (not including) NF/16.
 template <int NF, int TPF, int NS, bool INV>
-__device__ __forceinline__ void fft_passes(float2 *buf, const float2 *__restrict__ tw, int tid) {
-    if constexpr (NS * 16 <= NF) {
+__device__ __forceinline__ void fft_middle(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    if constexpr (NS < NF / 16) {
         stockham_pass<NF, TPF, 16, NS, INV>(buf, tw, tid);
-        fft_passes<NF, TPF, NS * 16, INV>(buf, tw, tid);
-    } else if constexpr (NS < NF) {
-        constexpr int R = NF / NS;  // 2, 4 or 8
-        stockham_pass<NF, TPF, R, NS, INV>(buf, tw, tid);
+        fft_middle<NF, TPF, NS * 16, INV>(buf, tw, tid);
     }
 }
 
-// In-place FFT of buf (padded layout). Caller must __syncthreads() after
-// writing buf; the FFT ends with a __syncthreads().  Forward uses
-// exp(-2 pi i k n / NF), inverse exp(+...), both unnormalised.
+// First pass from registers: butterfly j = tid + b TPF holds the inputs
+// x[j + r NF/R1] in v[b][r]; the R1-point DFT is applied and the results
+// stored in autosorted order (span 1: x'[j R1 + r]).  No barrier inside;
+// the caller must __syncthreads() before the next pass.
+template <int NF, int TPF, bool INV>
+__device__ __forceinline__ void fft_first_from_regs(float2 *buf, float2 (*v)[FftPlan<NF>::R1], int tid) {
+    constexpr int R1 = FftPlan<NF>::R1;
+    constexpr int NBF = NF / R1;
+    constexpr int PER = (NBF + TPF - 1) / TPF;
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int j = tid + b * TPF;
+        if (PER * TPF == NBF || j < NBF) {
+            dft_r<R1, INV>(v[b]);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) buf[padded(j * R1 + r)] = v[b][r];
+        }
+    }
+}
+
+// Last pass into registers: butterfly j (< NF/16) loads x[j + r NF/16],
+// applies W_NF^{r j}, and leaves the outputs X[j + r NF/16] in v[r].  Ends
+// with a __syncthreads(), after which buf may be reused.
+template <int NF, int TPF, bool INV>
+__device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2 *__restrict__ tw, int tid,
+                                                 float2 (&v)[16]) {
+    constexpr int NS = NF / 16;
+    const int j = tid;
+    if (TPF == NS || j < NS) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = buf[padded(j + r * NS)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            float2 w = __ldg(&tw[(NS - FftPlan<NF>::R1) + (r - 1) * NS + j]);
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        dft16<INV>(v);
+    }
+    __syncthreads();
+}
+
+// Whole in-place FFT of buf (natural order in and out), for callers that do
+// not fuse the first or last pass.  Caller syncs after writing buf; ends with
+// a __syncthreads().
 template <int NF, int TPF, bool INV>
 __device__ __forceinline__ void fft(float2 *buf, const float2 *__restrict__ tw, int tid) {
-    fft_passes<NF, TPF, 1, INV>(buf, tw, tid);
+    constexpr int R1 = FftPlan<NF>::R1;
+    stockham_pass<NF, TPF, R1, 1, INV>(buf, tw, tid);
+    fft_middle<NF, TPF, R1, INV>(buf, tw, tid);
+    stockham_pass<NF, TPF, 16, NF / 16, INV>(buf, tw, tid);
 }
 
 }  // namespace sst

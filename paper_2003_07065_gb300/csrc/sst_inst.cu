@@ -19,7 +19,8 @@ const void *kernel_of(int kind) {
         case KIND_FWD_T: return (const void *)k_forward<NF, MODE_T>;
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
-        case KIND_INV: return (const void *)k_inverse<NF>;
+        case KIND_INV: return (const void *)k_inverse<NF, true>;
+        case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
     }
     return nullptr;
 }
@@ -58,8 +59,13 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const float *gamm
     return cudaGetLastError();
 }
 
-cudaError_t inverse(const SstDev &d, const float2 *T, float *partial, size_t smem, cudaStream_t st) {
-    k_inverse<NF><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
+cudaError_t inverse(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st) {
+    if (kind == KIND_INV)
+        k_inverse<NF, true><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
+    else if (kind == KIND_INV_WIDE)
+        k_inverse<NF, false><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -1,7 +1,11 @@
 // Kernels of the downsampled synchrosqueezing transform, templated on the
 // DFT length NF.  One CTA of TPF threads works on one frame (forward) or one
-// pair of frames (threshold pre-pass, inverse) at a time.
+// pair of frames (threshold pre-pass, inverse) at a time.  The frame gather
+// (and, in the inverse, the spectrum build) is fused into the first FFT pass
+// and the epilogue into the last one, so a frame makes three trips through
+// shared memory for a 4096-point transform.
 #pragma once
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,11 +16,14 @@ namespace sst {
 
 template <int NF> struct Cfg {
     static constexpr int TPF = (NF / 16 < 32) ? 32 : NF / 16;  // threads per CTA
-    static constexpr int PPT = NF / TPF;                          // FFT points per thread
     static constexpr int BUF = padded_len(NF);                    // float2 per frame buffer
+    static constexpr int R1 = FftPlan<NF>::R1;                    // radix of the first pass
+    static constexpr int PER1 = (NF / R1 + TPF - 1) / TPF;        // first-pass butterflies per thread
+    static constexpr int NSL = NF / 16;                           // span of the last pass
     static constexpr int KMAX = (NF / 2 + 1 + TPF - 1) / TPF;     // band bins per thread
-    static constexpr int NMAX = (NF + 1 + TPF - 1) / TPF;         // window taps per thread (L <= NF+1)
     static constexpr int NWARP = TPF / 32;
+    // resident CTAs per SM the forward kernels are register-budgeted for
+    static constexpr int MINB = (768 / TPF < 1) ? 1 : ((768 / TPF > 8) ? 8 : 768 / TPF);
 };
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -37,37 +44,70 @@ template <int NWARP> __device__ __forceinline__ float block_max(float v, float *
     return r;
 }
 
-// Gather frame m (or the pair m, m2 into re/im) with window folding mod NF:
-// buf[p] = sum_{j = p mod NF, |j| <= M} x[m hop + j] * win[j]   (Eq. 8-9).
-// PAIR = false: win = (g, s g'), value = x (g + i s g'); s is a power of two
-//               that equalises the two halves' norms (so neither half's FFT
-//               rounding swamps the other) and is undone exactly afterwards
-// PAIR = true : value = (x_m + i x_m2) g
+// Windowed, folded frame sample at FFT position p (Eq. 8-9):
+//   sum_{j = p mod NF, |j| <= M} x[c + j] * win[j]
+// PAIR = false: win = (g, s g')  -> x (g + i s g');  s a power of two that
+//               equalises the two halves' norms (undone exactly afterwards)
+// PAIR = true : value (x[c1 + j] + i x[c2 + j]) g
 template <int NF, bool PAIR>
-__device__ __forceinline__ void gather_frame(float2 *buf, const SstDev &d, const float *__restrict__ x,
-                                             int64_t m, int64_t m2, bool has2, int tid) {
-    constexpr int TPF = Cfg<NF>::TPF;
-    const int64_t c1 = m * d.hop, c2 = m2 * d.hop;
-#pragma unroll 4
-    for (int i = 0; i < Cfg<NF>::PPT; ++i) {
-        const int p = tid + i * TPF;
-        float2 acc = make_float2(0.f, 0.f);
-        const int jmin = p - NF * ((p + d.M) / NF);
-        for (int j = jmin; j <= d.M; j += NF) {
-            const float2 w = __ldg(&d.win[j + d.M]);
-            const int64_t s1 = c1 + j;
-            const float x1 = (s1 >= 0 && s1 < d.n) ? __ldg(&x[s1]) : 0.f;
-            if (!PAIR) {
-                acc.x = fmaf(x1, w.x, acc.x);
-                acc.y = fmaf(x1, w.y, acc.y);
-            } else {
-                const int64_t s2 = c2 + j;
-                const float x2 = (has2 && s2 >= 0 && s2 < d.n) ? __ldg(&x[s2]) : 0.f;
-                acc.x = fmaf(x1, w.x, acc.x);
-                acc.y = fmaf(x2, w.x, acc.y);
-            }
+__device__ __forceinline__ float2 frame_sample(const SstDev &d, const float *__restrict__ x, int p, int64_t c1,
+                                               int64_t c2, bool has2) {
+    float2 acc = make_float2(0.f, 0.f);
+    const int jmin = p - NF * ((p + d.M) / NF);
+    for (int j = jmin; j <= d.M; j += NF) {
+        const float2 w = __ldg(&d.win[j + d.M]);
+        const int64_t s1 = c1 + j;
+        const float x1 = (s1 >= 0 && s1 < d.n) ? __ldg(&x[s1]) : 0.f;
+        if (!PAIR) {
+            acc.x = fmaf(x1, w.x, acc.x);
+            acc.y = fmaf(x1, w.y, acc.y);
+        } else {
+            const int64_t s2 = c2 + j;
+            const float x2 = (has2 && s2 >= 0 && s2 < d.n) ? __ldg(&x[s2]) : 0.f;
+            acc.x = fmaf(x1, w.x, acc.x);
+            acc.y = fmaf(x2, w.x, acc.y);
         }
-        buf[padded(p)] = acc;
+    }
+    return acc;
+}
+
+// Forward FFT of frame(s) (c1, c2 are frame centres): gather fused into the
+// first pass, outputs X[j + r NF/16] left in v (thread j = tid < NF/16).
+template <int NF, bool PAIR>
+__device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const float *__restrict__ x, int64_t c1,
+                                            int64_t c2, bool has2, int tid, float2 (&v)[16]) {
+    using C = Cfg<NF>;
+    float2 u[C::PER1][C::R1];
+#pragma unroll
+    for (int b = 0; b < C::PER1; ++b) {
+        const int j = tid + b * C::TPF;
+        if (C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1) {
+#pragma unroll
+            for (int r = 0; r < C::R1; ++r) u[b][r] = frame_sample<NF, PAIR>(d, x, j + r * (NF / C::R1), c1, c2, has2);
+        }
+    }
+    fft_first_from_regs<NF, C::TPF, false>(buf, u, tid);
+    __syncthreads();
+    fft_middle<NF, C::TPF, C::R1, false>(buf, d.tw, tid);
+    fft_last_to_regs<NF, C::TPF, false>(buf, d.tw, tid, v);
+}
+
+// Scatter the last-pass outputs needed by the Hermitian split into buf:
+// zc[k - k_lo] = X[k] and zm[k - k_lo] = X[(NF - k) mod NF] for k in the band.
+// Caller syncs afterwards.
+template <int NF>
+__device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDev &d, int tid, const float2 (&v)[16]) {
+    constexpr int NS = NF / 16;
+    if (Cfg<NF>::TPF == NS || tid < NS) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int q = tid + r * NS;
+            const int kb = q - d.k_lo;
+            if (kb >= 0 && q <= d.k_hi) zc[kb] = v[r];
+            const int qm = (NF - q) & (NF - 1);
+            const int km = qm - d.k_lo;
+            if (km >= 0 && qm <= d.k_hi) zm[km] = v[r];
+        }
     }
 }
 
@@ -77,7 +117,7 @@ __device__ __forceinline__ void gather_frame(float2 *buf, const SstDev &d, const
 // conj Z[-k]) / 2, S_b = (Z[k] - conj Z[-k]) / 2i.  One partial max per CTA.
 // ---------------------------------------------------------------------------
 template <int NF>
-__global__ void __launch_bounds__(Cfg<NF>::TPF)
+__global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
 k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     using C = Cfg<NF>;
     extern __shared__ float4 smem4[];
@@ -89,17 +129,17 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     for (int64_t q = blockIdx.x; q < npairs; q += gridDim.x) {
         const int64_t a = 2 * q, b = a + 1;
         const bool hasb = b < d.F;
-        gather_frame<NF, true>(buf, d, x, a, b, hasb, tid);
+        float2 v[16];
+        forward_fft<NF, true>(buf, d, x, a * d.hop, b * d.hop, hasb, tid, v);
+        float2 *zc = buf, *zm = buf + d.nb;
+        scatter_band<NF>(zc, zm, d, tid, v);
         __syncthreads();
-        fft<NF, C::TPF, false>(buf, d.tw, tid);
         for (int kk = tid; kk < d.nb; kk += C::TPF) {
-            const int k = d.k_lo + kk;
-            const float2 zk = buf[padded(k)];
-            const float2 zm = buf[padded((NF - k) & (NF - 1))];
-            const float ar = 0.5f * (zk.x + zm.x), ai = 0.5f * (zk.y - zm.y);
+            const float2 zk = zc[kk], zn = zm[kk];
+            const float ar = 0.5f * (zk.x + zn.x), ai = 0.5f * (zk.y - zn.y);
             best = fmaxf(best, ar * ar + ai * ai);
             if (hasb) {
-                const float br = 0.5f * (zk.y + zm.y), bi = 0.5f * (zm.x - zk.x);
+                const float br = 0.5f * (zk.y + zn.y), bi = 0.5f * (zn.x - zk.x);
                 best = fmaxf(best, br * br + bi * bi);
             }
         }
@@ -114,8 +154,8 @@ __global__ void k_gamma(const float *__restrict__ partial, int count, float frac
                         float *__restrict__ gamma2_out, float *__restrict__ maxv_out);
 
 // ---------------------------------------------------------------------------
-// Forward: per frame, packed FFT of x (g + i g'), Hermitian split into S^g and
-// S^g' for the band bins, IF estimate, threshold, destination, and the
+// Forward: per frame, packed FFT of x (g + i s g'), Hermitian split into S^g
+// and S^g' for the band bins, IF estimate, threshold, destination, and the
 // deterministic per-frame accumulation of T in shared memory.
 //   MODE_T   : T rows (F x nbo complex)
 //   MODE_STFT: S^g, S^g' rows (F x nb complex each), no threshold
@@ -129,7 +169,7 @@ __global__ void k_gamma(const float *__restrict__ partial, int count, float frac
 enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2 };
 
 template <int NF, int MODE>
-__global__ void __launch_bounds__(Cfg<NF>::TPF)
+__global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
 k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma2_dev,
           float2 *__restrict__ out0, void *__restrict__ out1) {
     using C = Cfg<NF>;
@@ -147,9 +187,11 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
     // (the first __syncthreads below orders this before any atomic)
 
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x) {
-        gather_frame<NF, false>(buf, d, x, m, 0, false, tid);
+        float2 v[16];
+        forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);
+        float2 *zc = buf, *zm = buf + d.nb;
+        scatter_band<NF>(zc, zm, d, tid, v);
         __syncthreads();
-        fft<NF, TPF, false>(buf, d.tw, tid);
 
         float2 Vv[C::KMAX];
         int li[C::KMAX];
@@ -161,10 +203,10 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
             Vv[i] = make_float2(0.f, 0.f);
             if (kk < d.nb) {
                 const int k = d.k_lo + kk;
-                const float2 zk = buf[padded(k)];
-                const float2 zm = buf[padded((NF - k) & (NF - 1))];
-                const float2 V = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-                const float2 Vd = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+                const float2 zk = zc[kk];
+                const float2 zn = zm[kk];
+                const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                const float2 Vd = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
                 const size_t o = (size_t)m * d.nb + kk;
                 if (MODE == MODE_STFT) {
                     out0[o] = V;
@@ -194,10 +236,10 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
             }
         }
         if (MODE != MODE_T) {
-            __syncthreads();  // buf reads done before the next gather
+            __syncthreads();  // band reads done before the next frame's first pass writes buf
             continue;
         }
-        maxc = block_max<C::NWARP>(maxc, red, tid);  // also orders buf reads before next gather
+        maxc = block_max<C::NWARP>(maxc, red, tid);  // also orders band reads before the next frame
         int e = 0;
         if (maxc > 0.f) {
             int ex;
@@ -222,47 +264,66 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
             acc[2 * l + 1] = 0ull;
         }
         // the zeroing above is ordered before the next frame's atomics by the
-        // __syncthreads inside the next gather/FFT
+        // __syncthreads inside the next frame's FFT
     }
 }
 
 // ---------------------------------------------------------------------------
 // Inverse, one CTA per tile of B consecutive frames (B even), frames taken in
-// pairs (a, b = a + 1).  For a pair, r_a + i r_b comes out of z complex
-// inverse FFTs of length NF: sub-grid s (fine bins l = z q + s) is placed at
-// coarse bin k_lo + q together with the Hermitian image of sub-grid
-// (z - s) mod z, and the result is multiplied by exp(i 2 pi s j / (z NF))
-// (Eq. 25, with the zNf-point zero-padded inverse of Sec. 2.5 split into its
-// z interleaved sub-grids).  The windowed frames are overlap-added into a
+// pairs (a, b = a + 1).  r_a + i r_b comes out of z complex inverse FFTs of
+// length NF: sub-grid s (fine bins l = z q + s) is placed at coarse bin
+// k_lo + q together with the Hermitian image of sub-grid (z - s) mod z, and
+// the result at tap j is multiplied by exp(i 2 pi s j / (z NF)) (Eq. 25, with
+// the zNf-point zero-padded inverse of Sec. 2.5 split into its z interleaved
+// sub-grids).  The pair's two T rows are staged in shared memory by
+// sub-grid; the spectrum build is fused into the first FFT pass and the tap
+// accumulation into the last, whose thread j holds the outputs
+// q = j + r NF/16.  NARROW (L <= NF/2 + 1) keeps the 9 accumulators of
+// r in [0, 4] and [12, 15]; otherwise all 16 plus the tap -NF/2 (which shares
+// q = NF/2 with +NF/2).  The windowed frames are overlap-added into a
 // shared-memory segment in ascending frame order, written to the partial
 // buffer, and k_finalize sums overlapping segments in tile order and applies
 // 1 / D[p] (Eq. 26).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 tfr_value(const float2 *__restrict__ Trow, const SstDev &d, int k, int s,
-                                            int nf) {
-    // w_l T[l] for the fine bin l = z (k - k_lo) + s, zero outside the grid
-    const int q = k - d.k_lo;
-    if (q < 0 || q > d.k_hi - d.k_lo) return make_float2(0.f, 0.f);
-    const int l = d.z * q + s;
-    if (l >= d.nbo) return make_float2(0.f, 0.f);
-    float2 t = __ldg(&Trow[l]);
-    if (s == 0 && (k == 0 || 2 * k == nf)) t = cscale(t, 0.5f);
-    return t;
-}
+template <bool NARROW> struct InvTaps {
+    static constexpr int NACC = NARROW ? 9 : 17;
+    // r of accumulator i (i = 16 is the extra tap -NF/2 at r = 8)
+    __host__ __device__ static constexpr int r_of(int i) { return NARROW ? (i <= 4 ? i : i + 7) : (i < 16 ? i : 8); }
+};
 
-template <int NF>
+template <int NF, bool NARROW>
 __global__ void __launch_bounds__(Cfg<NF>::TPF)
 k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
     using C = Cfg<NF>;
+    using TP = InvTaps<NARROW>;
     constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    float *seg = reinterpret_cast<float *>(buf + C::BUF);
+    // staged rows: Tst[f][s][q] = w T_f[z q + s], q in [0, nq), nq = N_r + 1
+    const int nq = d.k_hi - d.k_lo + 1;
+    float2 *Tst = buf + C::BUF;
+    float *seg = reinterpret_cast<float *>(Tst + 2 * d.z * nq);
     const int tid = threadIdx.x;
     const int64_t tile = blockIdx.x;
     const int64_t m0 = tile * d.B;
     const float cnorm = 1.0f / (float)NF;
-    const int G = d.z * NF;
+    const bool live = (TPF == NS) || tid < NS;
+
+    // per-thread taps of the last pass: n_i = q or q - NF, window g[n_i + M]
+    int tap[TP::NACC];
+    float gw[TP::NACC];
+#pragma unroll
+    for (int i = 0; i < TP::NACC; ++i) {
+        const int r = TP::r_of(i);
+        const int q = tid + r * NS;
+        int n;
+        if (i == 16) n = -NF / 2;
+        else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
+        const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
+        tap[i] = ok ? n : INT_MIN;
+        gw[i] = ok ? __ldg(&d.g[n + d.M]) : 0.f;
+    }
 
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
 
@@ -270,68 +331,97 @@ k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
         const int64_t a = m0 + 2 * pr, b = a + 1;
         if (a >= d.F) break;
         const bool hasb = b < d.F;
-        const float2 *Ta = T + (size_t)a * d.nbo;
-        const float2 *Tb = T + (size_t)(hasb ? b : a) * d.nbo;
-        float2 racc[C::NMAX];
+        // stage both rows (contiguous in T), regrouped by sub-grid, with the
+        // 1/2 weight of the DC and Nyquist destinations (Hermitian completion)
+        {
+            const float2 *src = T + (size_t)a * d.nbo;
+            const int cnt = (hasb ? 2 : 1) * d.nbo;
+            for (int i = tid; i < 2 * d.nbo; i += TPF) {
+                const int f = i >= d.nbo;
+                const int l = i - f * d.nbo;
+                float2 t = (i < cnt) ? __ldg(&src[i]) : make_float2(0.f, 0.f);
+                const int s = l % d.z, q = l / d.z;
+                const int k = d.k_lo + q;
+                if (s == 0 && (k == 0 || 2 * k == NF)) t = cscale(t, 0.5f);
+                Tst[(f * d.z + s) * nq + q] = t;
+            }
+        }
+        __syncthreads();
+
+        float2 racc[TP::NACC];
 #pragma unroll
-        for (int i = 0; i < C::NMAX; ++i) racc[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < TP::NACC; ++i) racc[i] = make_float2(0.f, 0.f);
 
         for (int s = 0; s < d.z; ++s) {
             const int sb = (s == 0) ? 0 : d.z - s;
             const int dl = (s == 0) ? 0 : 1;
+            const int nqs = (s == 0) ? nq : nq - 1;     // sub-grid s holds q in [0, nqs)
+            const int nqb = (sb == 0) ? nq : nq - 1;
+            const float2 *Ta = Tst + s * nq, *Tam = Tst + sb * nq;
+            const float2 *Tb = Tst + (d.z + s) * nq, *Tbm = Tst + (d.z + sb) * nq;
+            // first pass with the spectrum built in registers:
             // Y_s[k] = (1/NF) (X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl]))
-#pragma unroll 4
-            for (int i = 0; i < C::PPT; ++i) {
-                const int k = tid + i * TPF;
-                const int km = (NF - k - dl) & (NF - 1);
-                float2 xa = tfr_value(Ta, d, k, s, NF);
-                float2 xam = tfr_value(Ta, d, km, sb, NF);
-                float2 y = make_float2(xa.x + xam.x, xa.y - xam.y);
-                if (hasb) {
-                    const float2 xb = tfr_value(Tb, d, k, s, NF);
-                    const float2 xbm = tfr_value(Tb, d, km, sb, NF);
-                    // i * (xb + conj xbm)
-                    y.x -= xb.y - xbm.y;
-                    y.y += xb.x + xbm.x;
-                }
-                buf[padded(k)] = cscale(y, cnorm);
-            }
-            __syncthreads();
-            fft<NF, TPF, true>(buf, d.tw, tid);
+            float2 u[C::PER1][C::R1];
 #pragma unroll
-            for (int i = 0; i < C::NMAX; ++i) {
-                const int t = tid + i * TPF;  // t = j + M
-                if (t < d.L) {
-                    const int j = t - d.M;
-                    const float2 yv = buf[padded(j & (NF - 1))];
-                    if (s == 0) {
-                        racc[i] = cadd(racc[i], yv);
-                    } else {
-                        int qi = (s * j) % G;
-                        if (qi < 0) qi += G;
-                        racc[i] = cadd(racc[i], cmul(yv, __ldg(&d.twz[qi])));
+            for (int bb = 0; bb < C::PER1; ++bb) {
+                const int j = tid + bb * TPF;
+#pragma unroll
+                for (int r = 0; r < C::R1; ++r) {
+                    const int k = j + r * (NF / C::R1);
+                    float2 y = make_float2(0.f, 0.f);
+                    if (C::PER1 * TPF == NF / C::R1 || j < NF / C::R1) {
+                        const int q = k - d.k_lo;
+                        if (q >= 0 && q < nqs) {
+                            const float2 xa = Ta[q], xb = Tb[q];
+                            y.x += xa.x - xb.y;
+                            y.y += xa.y + xb.x;
+                        }
+                        const int qm = ((NF - k - dl) & (NF - 1)) - d.k_lo;
+                        if (qm >= 0 && qm < nqb) {
+                            const float2 xa = Tam[qm], xb = Tbm[qm];
+                            // conj(xa) + i conj(xb)
+                            y.x += xa.x + xb.y;
+                            y.y += -xa.y + xb.x;
+                        }
+                    }
+                    u[bb][r] = cscale(y, cnorm);
+                }
+            }
+            fft_first_from_regs<NF, TPF, true>(buf, u, tid);
+            __syncthreads();
+            fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
+            float2 v[16];
+            fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
+            // accumulate the taps, with the sub-grid twiddle exp(i 2 pi s n / (z NF))
+            if (live) {
+                if (s == 0) {
+#pragma unroll
+                    for (int i = 0; i < TP::NACC; ++i) racc[i] = cadd(racc[i], v[TP::r_of(i)]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < TP::NACC; ++i) {
+                        if (tap[i] != INT_MIN) {
+                            const float2 w = (i == 16) ? __ldg(&d.twn[s])
+                                                       : __ldg(&d.twq[s * NF + tid + TP::r_of(i) * NS]);
+                            racc[i] = cadd(racc[i], cmul(v[TP::r_of(i)], w));
+                        }
                     }
                 }
             }
-            __syncthreads();
         }
         // overlap-add a, then b (ascending frame order at every sample)
-        const int oa = (int)(a - m0) * d.hop;
+        const int oa = (int)(a - m0) * d.hop + d.M;
 #pragma unroll
-        for (int i = 0; i < C::NMAX; ++i) {
-            const int t = tid + i * TPF;
-            if (t < d.L) seg[oa + t] += __ldg(&d.g[t]) * racc[i].x;
-        }
+        for (int i = 0; i < TP::NACC; ++i)
+            if (tap[i] != INT_MIN) seg[oa + tap[i]] += gw[i] * racc[i].x;
         __syncthreads();
         if (hasb) {
             const int ob = oa + d.hop;
 #pragma unroll
-            for (int i = 0; i < C::NMAX; ++i) {
-                const int t = tid + i * TPF;
-                if (t < d.L) seg[ob + t] += __ldg(&d.g[t]) * racc[i].y;
-            }
-            __syncthreads();
+            for (int i = 0; i < TP::NACC; ++i)
+                if (tap[i] != INT_MIN) seg[ob + tap[i]] += gw[i] * racc[i].y;
         }
+        __syncthreads();
     }
     float *out = partial + (size_t)tile * d.seg_len;
     for (int i = tid; i < d.seg_len; i += TPF) out[i] = seg[i];

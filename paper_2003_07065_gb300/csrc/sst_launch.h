@@ -9,7 +9,8 @@
 
 namespace sst {
 
-enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_COUNT = 5 };
+enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
+       KIND_COUNT = 6 };
 
 struct KernelTable {
     int nf;
@@ -23,7 +24,8 @@ struct KernelTable {
                           cudaStream_t st);
     cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const float *gamma2, void *out0,
                            void *out1, int grid, size_t smem, cudaStream_t st);
-    cudaError_t (*inverse)(const SstDev &d, const float2 *T, float *partial, size_t smem, cudaStream_t st);
+    // kind: KIND_INV (window L <= nf/2 + 1) or KIND_INV_WIDE (L <= nf + 1)
+    cudaError_t (*inverse)(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st);
 };
 
 const KernelTable *table_for_nf(int nf);
