@@ -41,8 +41,14 @@ const KernelTable *table_for_nf(int nf) {
 }
 
 // ------------------------------------------------------------ small kernels
-__global__ void k_gamma(const float *__restrict__ partial, int count, float frac2,
-                        float *__restrict__ gamma2_out, float *__restrict__ maxv_out) {
+// Reduce the pre-pass partials.  Relative plans (from_x = 0): the partials are
+// max |S^g|^2 per CTA; gamma^2 = frac^2 max, maxv = sqrt(max).  Absolute plans
+// (from_x = 1): the partials are max |x| per CTA and |S^g| <= max|x| sum|g|.
+// Either way the bound B on |S^g| (0.1% margin for the forward kernel's own
+// rounding) gives the fixed-point scale 2^e, e = 61 - ceil(log2 B) -
+// ceil(log2 nb): a frame's at most nb terms then sum below 2^62 in int64.
+__global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
+                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out) {
     __shared__ float red[32];
     float v = 0.f;
     for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmaxf(v, partial[i]);
@@ -53,8 +59,43 @@ __global__ void k_gamma(const float *__restrict__ partial, int count, float frac
     if (threadIdx.x == 0) {
         float r = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
-        if (gamma2_out) *gamma2_out = frac2 * r;
-        if (maxv_out) *maxv_out = sqrtf(r);
+        float bound;
+        if (!from_x) {
+            const float mv = sqrtf(r);
+            sc->gamma2 = frac2 * r;
+            sc->maxv = mv;
+            if (maxv_out) *maxv_out = mv;
+            bound = mv * 1.001f;
+        } else {
+            bound = r * bound_mul;
+        }
+        int e = 0;
+        if (bound > 0.f && bound < 3.0e38f) {
+            int ex;
+            frexpf(bound, &ex);  // bound < 2^ex
+            e = 61 - ex - log2_nb;
+        }
+        const int e1 = e / 2, e2 = e - e / 2;
+        sc->s1 = ldexpf(1.f, e1);
+        sc->s2 = ldexpf(1.f, e2);
+        sc->r1 = ldexpf(1.f, -e1);
+        sc->r2 = ldexpf(1.f, -e2);
+    }
+}
+
+__global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict__ partial) {
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v = fmaxf(v, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+        partial[blockIdx.x] = r;
     }
 }
 
@@ -156,6 +197,7 @@ struct sst_plan {
     const KernelTable *kt = nullptr;
     void *dmem = nullptr;
     float gamma_frac2 = 0.f;
+    float sum_abs_g = 0.f;   // bound factor |S^g| <= max|x| sum|g| (rounded up)
     size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
     int inv_kind = KIND_INV;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
@@ -275,26 +317,33 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     std::vector<float2> win(L);
     std::vector<float> gf(L);
     for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)(dg[i] * dsc)); gf[i] = (float)g[i]; }
-    // Stockham twiddles, per radix-16 pass of span Ns (Ns = R1, 16 R1, ..., nf/16):
-    // entry (Ns - R1) + (r - 1) Ns + k = exp(-2 pi i r k / (16 Ns)), r in [1, 16), k in [0, Ns)
+    // Stockham twiddles, per radix-16 pass of span Ns (Ns = R1, 16 R1, ..., nf/16): rows
+    // m = 1, 2, 4, 8 of exp(-2 pi i m k / (16 Ns)), k in [0, Ns), from entry 4 (Ns - R1) / 15
     int lg2 = 0;
     while ((1 << lg2) < nf) ++lg2;
     const int R1 = (lg2 % 4 == 0) ? 16 : (1 << (lg2 % 4));
-    std::vector<float2> tw(std::max(nf - R1, 1));
-    for (int Ns = R1; Ns < nf; Ns *= 16)
-        for (int r = 1; r < 16; ++r)
+    std::vector<float2> tw(std::max(4 * (nf - R1) / 15, 1));
+    for (int Ns = R1; Ns < nf; Ns *= 16) {
+        const int off = 4 * (Ns - R1) / 15;
+        for (int mi = 0; mi < 4; ++mi)
             for (int k = 0; k < Ns; ++k) {
-                const double a = -2.0 * M_PI * (double)r * (double)k / (16.0 * Ns);
-                tw[(Ns - R1) + (r - 1) * Ns + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+                const double a = -2.0 * M_PI * (double)(1 << mi) * (double)k / (16.0 * Ns);
+                tw[off + mi * Ns + k] = make_float2((float)std::cos(a), (float)std::sin(a));
             }
-    // inverse sub-grid twiddles exp(+2 pi i s n / (z nf)) by output slot q of the last pass
-    std::vector<float2> twq(G), twn(z);
+    }
+    // inverse sub-grid twiddles exp(+2 pi i s n / (z nf)), factored per last-pass output slot
+    const int nsl = nf / 16;
+    std::vector<float2> twb(z * nsl), twc(z * 32), twn(z);
     for (int s_ = 0; s_ < z; ++s_) {
-        for (int q = 0; q < nf; ++q) {
-            const int nq_ = (q <= nf / 2) ? q : q - nf;
-            const double a = 2.0 * M_PI * (double)s_ * (double)nq_ / (double)G;
-            twq[s_ * nf + q] = make_float2((float)std::cos(a), (float)std::sin(a));
+        for (int j = 0; j < nsl; ++j) {
+            const double a = 2.0 * M_PI * (double)s_ * (double)j / (double)G;
+            twb[s_ * nsl + j] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
+        for (int w = 0; w < 2; ++w)
+            for (int r = 0; r < 16; ++r) {
+                const double a = 2.0 * M_PI * (double)s_ * (double)r / (16.0 * z) - (w ? 2.0 * M_PI * (double)s_ / z : 0.0);
+                twc[(2 * s_ + w) * 16 + r] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
         const double a = -2.0 * M_PI * (double)s_ * (double)(nf / 2) / (double)G;
         twn[s_] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
@@ -303,8 +352,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t o_win = take(sizeof(float2) * L), o_g = take(sizeof(float) * L),
-                 o_tw = take(sizeof(float2) * tw.size()), o_twq = take(sizeof(float2) * G),
-                 o_twn = take(sizeof(float2) * z), o_rl = take(sizeof(float) * rDl.size()),
+                 o_tw = take(sizeof(float2) * tw.size()), o_twb = take(sizeof(float2) * twb.size()),
+                 o_twc = take(sizeof(float2) * twc.size()), o_twn = take(sizeof(float2) * z),
+                 o_rl = take(sizeof(float) * rDl.size()),
                  o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop);
     cudaError_t ce = cudaMalloc(&pl->dmem, off);
     if (ce != cudaSuccess) { delete pl; return fail(SST_ENOMEM, "cudaMalloc of %zu table bytes failed", off); }
@@ -313,7 +363,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     memcpy(host.data() + o_win, win.data(), sizeof(float2) * L);
     memcpy(host.data() + o_g, gf.data(), sizeof(float) * L);
     memcpy(host.data() + o_tw, tw.data(), sizeof(float2) * tw.size());
-    memcpy(host.data() + o_twq, twq.data(), sizeof(float2) * G);
+    memcpy(host.data() + o_twb, twb.data(), sizeof(float2) * twb.size());
+    memcpy(host.data() + o_twc, twc.data(), sizeof(float2) * twc.size());
     memcpy(host.data() + o_twn, twn.data(), sizeof(float2) * z);
     memcpy(host.data() + o_rl, rDl.data(), sizeof(float) * rDl.size());
     memcpy(host.data() + o_rr, rDr.data(), sizeof(float) * rDr.size());
@@ -325,7 +376,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     d.win = (const float2 *)(base + o_win);
     d.g = (const float *)(base + o_g);
     d.tw = (const float2 *)(base + o_tw);
-    d.twq = (const float2 *)(base + o_twq);
+    d.twb = (const float2 *)(base + o_twb);
+    d.twc = (const float2 *)(base + o_twc);
     d.twn = (const float2 *)(base + o_twn);
     d.rD_left = (const float *)(base + o_rl);
     d.rD_right = (const float *)(base + o_rr);
@@ -351,6 +403,11 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     d.relative = (p.flags & SST_GAMMA_RELATIVE) ? 1 : 0;
     d.gamma2_abs = d.relative ? 0.f : (float)(p.gamma * p.gamma);
     pl->gamma_frac2 = (float)(p.gamma * p.gamma);
+    {
+        double sg = 0.0;
+        for (int i = 0; i < L; ++i) sg += std::fabs(g[i]);
+        pl->sum_abs_g = (float)(sg * 1.001);
+    }
 
     // inverse tiles: B even, enough tiles to fill the GPU several times over
     int64_t B = F / (4LL * pl->num_sms);
@@ -431,30 +488,56 @@ static sst_status check_call(sst_plan_t plan, const void *x, int64_t n, const vo
     return SST_OK;
 }
 
-static float *ws_gamma2(sst_plan_t pl, void *ws) { return (float *)ws; }
-static float *ws_maxv(sst_plan_t pl, void *ws) { return (float *)ws + 1; }
+static SstScalars *ws_scalars(sst_plan_t, void *ws) { return (SstScalars *)ws; }
 static float *ws_partial(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_partial); }
 static float *ws_ola(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_ola); }
 
-// relative threshold: gamma^2 = frac^2 max |S^g|^2, left in the workspace
-static sst_status run_gamma(sst_plan_t pl, const float *x, void *ws, cudaStream_t st, float *maxv_out) {
-    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(pl->d, x, ws_partial(pl, ws), pl->grid_absmax, pl->smem_absmax, st),
-                   "absmax launch");
-    SST_LAUNCHED_K(PK_GAMMA, st,
-                   (k_gamma<<<1, 256, 0, st>>>(ws_partial(pl, ws), pl->grid_absmax, pl->gamma_frac2,
-                                               ws_gamma2(pl, ws), maxv_out ? maxv_out : ws_maxv(pl, ws)),
-                    cudaGetLastError()),
-                   "gamma launch");
+// The pre-pass of a forward call: for relative plans the max |S^g| pre-pass,
+// for absolute plans a max |x| reduction (only needed for the T scale).
+// Fills the SstScalars at sc; partial holds grid_absmax floats.
+static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, float *partial, cudaStream_t st,
+                              float *maxv_out, bool profile = true) {
+    if (pl->d.relative) {
+        cudaError_t e;
+        if (profile) {
+            SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(pl->d, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+                           "absmax launch");
+        } else {
+            e = pl->kt->absmax(pl->d, x, partial, pl->grid_absmax, pl->smem_absmax, st);
+            if (e != cudaSuccess) return cuda_fail(e, "absmax launch");
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+        }
+    } else {
+        int64_t blocks = (pl->d.n + 255) / 256;
+        if (blocks > pl->grid_absmax) blocks = pl->grid_absmax;
+        k_absx<<<(unsigned)blocks, 256, 0, st>>>(x, pl->d.n, partial);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "absx launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    const int count = pl->d.relative ? pl->grid_absmax
+                                     : (int)std::min<int64_t>((pl->d.n + 255) / 256, pl->grid_absmax);
+    if (profile) {
+        SST_LAUNCHED_K(PK_GAMMA, st,
+                       (k_gamma<<<1, 256, 0, st>>>(partial, count, pl->gamma_frac2, pl->d.relative ? 0 : 1,
+                                                   pl->sum_abs_g, pl->d.log2_nb, sc, maxv_out),
+                        cudaGetLastError()),
+                       "gamma launch");
+    } else {
+        k_gamma<<<1, 256, 0, st>>>(partial, count, pl->gamma_frac2, pl->d.relative ? 0 : 1, pl->sum_abs_g,
+                                   pl->d.log2_nb, sc, maxv_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "gamma launch");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
     return SST_OK;
 }
 
 static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
-    if (pl->d.relative) {
-        sst_status s = run_gamma(pl, x, ws, st, nullptr);
-        if (s != SST_OK) return s;
-    }
+    sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
+    if (s != SST_OK) return s;
     SST_LAUNCHED_K(PK_FORWARD, st,
-                   pl->kt->forward(pl->d, KIND_FWD_T, x, ws_gamma2(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   pl->kt->forward(pl->d, KIND_FWD_T, x, ws_scalars(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
                    "forward launch");
     return SST_OK;
 }
@@ -516,7 +599,7 @@ SST_API sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, floa
     if (s != SST_OK) return s;
     if (!V_dev || !Vd_dev) return fail(SST_EINVAL, "output pointer is NULL");
     SST_LAUNCHED_K(PK_STFT, (cudaStream_t)stream,
-                   plan->kt->forward(plan->d, KIND_FWD_STFT, x_dev, ws_gamma2(plan, ws), V_dev, Vd_dev,
+                   plan->kt->forward(plan->d, KIND_FWD_STFT, x_dev, ws_scalars(plan, ws), V_dev, Vd_dev,
                                      plan->grid_fwd_x, plan->smem_fwd_x, (cudaStream_t)stream),
                    "stft launch");
     return SST_OK;
@@ -529,11 +612,11 @@ SST_API sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t
     if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if (plan->d.relative) {
-        s = run_gamma(plan, x_dev, ws, st, nullptr);
+        s = run_prepass(plan, x_dev, ws_scalars(plan, ws), ws_partial(plan, ws), st, nullptr);
         if (s != SST_OK) return s;
     }
     SST_LAUNCHED_K(PK_MAP, st,
-                   plan->kt->forward(plan->d, KIND_FWD_MAP, x_dev, ws_gamma2(plan, ws), omega_dev, dest_dev,
+                   plan->kt->forward(plan->d, KIND_FWD_MAP, x_dev, ws_scalars(plan, ws), omega_dev, dest_dev,
                                      plan->grid_fwd_x, plan->smem_fwd_x, st),
                    "map launch");
     return SST_OK;
@@ -544,12 +627,21 @@ SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n,
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!maxv_dev) return fail(SST_EINVAL, "output pointer is NULL");
-    return run_gamma(plan, x_dev, ws, (cudaStream_t)stream, maxv_dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    SST_LAUNCHED_K(PK_ABSMAX, st,
+                   plan->kt->absmax(plan->d, x_dev, ws_partial(plan, ws), plan->grid_absmax, plan->smem_absmax, st),
+                   "absmax launch");
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   (k_gamma<<<1, 256, 0, st>>>(ws_partial(plan, ws), plan->grid_absmax, plan->gamma_frac2, 0, 1.f,
+                                               plan->d.log2_nb, ws_scalars(plan, ws), maxv_dev),
+                    cudaGetLastError()),
+                   "gamma launch");
+    return SST_OK;
 }
 
 // ------------------------------------------------------------ no-allocation forward
-// Scratch for sst_forward_static: [0] gamma^2, [1] max |S^g|, [64 ...) one
-// pre-pass maximum per CTA.  Host code must not use the symbol itself as an
+// Scratch for sst_forward_static: [0, 8) the call's SstScalars (threshold,
+// fixed-point scale), [64 ...) one pre-pass maximum per CTA.  Host code must not use the symbol itself as an
 // address (on the host it names a shadow variable); the device address is
 // looked up once per device and cached.
 static constexpr size_t kStaticFloats = SST_STATIC_SCRATCH_BYTES / sizeof(float);
@@ -587,16 +679,12 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     float *scratch = nullptr;
     sst_status s = static_scratch_address(dev, &scratch);
     if (s != SST_OK) return s;
-    float *gamma2 = scratch, *maxv = scratch + 1, *partial = scratch + kStaticHeader;
+    SstScalars *sc = (SstScalars *)scratch;
+    float *partial = scratch + kStaticHeader;
     cudaStream_t st = (cudaStream_t)stream;
-    if (plan->d.relative) {
-        SST_CU(plan->kt->absmax(plan->d, x_dev, partial, plan->grid_absmax, plan->smem_absmax, st), "absmax launch");
-        g_launches.fetch_add(1, std::memory_order_relaxed);
-        k_gamma<<<1, 256, 0, st>>>(partial, plan->grid_absmax, plan->gamma_frac2, gamma2, maxv);
-        SST_CU(cudaGetLastError(), "gamma launch");
-        g_launches.fetch_add(1, std::memory_order_relaxed);
-    }
-    SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, gamma2, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
+    s = run_prepass(plan, x_dev, sc, partial, st, nullptr, false);
+    if (s != SST_OK) return s;
+    SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
            "forward launch");
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return SST_OK;

@@ -10,8 +10,10 @@ struct SstDev {
     const float2 *win;  // (g[j], g'[j]) for j = -M..M, L entries
     const float *g;     // g[j], L entries
     const float2 *tw;   // Stockham twiddles per pass, [Ns - R1 + (r - 1) Ns + k] = W_{16 Ns}^{r k}
-    const float2 *twq;  // inverse sub-grid twiddles [s nf + q] = exp(+2 pi i s n(q) / (z nf)),
-                        // n(q) = q for q <= nf/2, else q - nf
+    // inverse sub-grid twiddle exp(+2 pi i s n / (z nf)) for the last-pass output slot
+    // q = j + r nf/16 (n = q, or q - nf when wrapped) = twb[s nf/16 + j] * twc[(2 s + wrapped) 16 + r]
+    const float2 *twb;  // [s nf/16 + j] = exp(2 pi i s j / (z nf))
+    const float2 *twc;  // [(2 s + w) 16 + r] = exp(2 pi i s r / (16 z)) * (w ? exp(-2 pi i s / z) : 1)
     const float2 *twn;  // [s] = exp(-2 pi i s (nf/2) / (z nf)), for the tap n = -nf/2
     const float *rD_left;   // 1 / D[p] for p in [0, EL)
     const float *rD_per;    // 1 / D[p] for p in [EL, ER), indexed by p mod hop
@@ -28,6 +30,16 @@ struct SstDev {
     int B;              // frames per inverse tile (even)
     int seg_len;        // (B - 1) hop + L
     int64_t ntiles;
+};
+
+// Per-call scalars produced on the device before the forward kernel runs
+// (at the start of the workspace, or of the static scratch array).
+struct SstScalars {
+    float gamma2;   // threshold squared (relative plans)
+    float maxv;     // max |S^g| over frames and band bins (relative plans)
+    float s1, s2;   // fixed-point scale 2^e = s1 s2 for the exact T sums
+    float r1, r2;   // its inverse 2^-e = r1 r2
+    float pad[2];
 };
 
 }  // namespace sst

@@ -6,14 +6,18 @@
 // the first radix-16 pass free of bank conflicts.  Each pass loads R points
 // per butterfly into registers, applies the Stockham twiddles
 // W_{Ns R}^{r k} = exp(-2 pi i r k / (Ns R)), runs a radix-R DFT in registers
-// and stores the results in autosorted order.  The twiddles come from a table
-// built in FP64 on the host and rounded, laid out per pass as [r - 1][k]
-// (k = butterfly mod Ns, fastest), so a warp's load for one r is contiguous:
-// the pass of span Ns (radix 16, Ns >= R1) starts at entry Ns - R1, and the
-// whole table has NF - R1 entries.  Passes: one radix 2, 4, 8 or 16 pass,
-// then radix-16 passes; output in natural order.  The first and last passes
-// are also offered with their inputs / outputs in registers so that kernels
-// can fuse the frame gather into the first and their epilogue into the last.
+// and stores the results in autosorted order.  Passes: one radix 2, 4, 8 or
+// 16 pass, then radix-16 passes; output in natural order.  The first and last
+// passes are also offered with their inputs / outputs in registers so that
+// kernels can fuse the frame gather into the first and their epilogue into
+// the last.
+//
+// Twiddles: a table built in FP64 on the host and rounded holds, for each
+// radix-16 pass of span Ns (Ns = R1, 16 R1, ..., NF/16), the four rows
+// W^{m k}, m = 1, 2, 4, 8, k in [0, Ns) (k fastest, so a warp's load is
+// contiguous), starting at entry 4 (Ns - R1) / 15.  A butterfly loads its four
+// values and forms the other eleven powers with at most three complex
+// products, so every twiddle is within a few ulp of the exact value.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -132,12 +136,40 @@ template <int R, bool INV> __device__ __forceinline__ void dft_r(float2 *v) {
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 
+template <int NF> __host__ __device__ constexpr int first_radix() {
+    return (ilog2c(NF) % 4 == 0) ? 16 : (1 << (ilog2c(NF) % 4));
+}
+template <int NF, int NS> __host__ __device__ constexpr int tw_offset() { return 4 * (NS - first_radix<NF>()) / 15; }
+
+// v[r] *= W^{r k} for r = 1..15, W = exp(-+2 pi i / (16 NS)), from the four
+// table rows of the pass at t (see the header)
+template <bool INV>
+__device__ __forceinline__ void twiddle16(float2 *v, const float2 *__restrict__ t, int NS, int k) {
+    float2 w1 = __ldg(&t[k]), w2 = __ldg(&t[NS + k]), w4 = __ldg(&t[2 * NS + k]), w8 = __ldg(&t[3 * NS + k]);
+    if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; w8.y = -w8.y; }
+    const float2 w3 = cmul(w2, w1), w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    v[4] = cmul(v[4], w4);
+    v[5] = cmul(v[5], w5);
+    v[6] = cmul(v[6], w6);
+    v[7] = cmul(v[7], w7);
+    v[8] = cmul(v[8], w8);
+    v[9] = cmul(v[9], cmul(w8, w1));
+    v[10] = cmul(v[10], cmul(w8, w2));
+    v[11] = cmul(v[11], cmul(w8, w3));
+    v[12] = cmul(v[12], cmul(w8, w4));
+    v[13] = cmul(v[13], cmul(w8, w5));
+    v[14] = cmul(v[14], cmul(w8, w6));
+    v[15] = cmul(v[15], cmul(w8, w7));
+}
+
 // One Stockham pass of radix R with span NS (product of earlier radices).
 template <int NF, int TPF, int R, int NS, bool INV>
 __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {
     constexpr int NBF = NF / R;                   // butterflies in this pass
     constexpr int PER = (NBF + TPF - 1) / TPF;    // butterflies per thread
-    constexpr int R1 = (ilog2c(NF) % 4 == 0) ? 16 : (1 << (ilog2c(NF) % 4));
     static_assert(NS == 1 || R == 16, "passes after the first are radix 16");
     float2 v[PER][R];
 #pragma unroll
@@ -154,14 +186,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
         const int j = tid + b * TPF;
         if (PER * TPF == NBF || j < NBF) {
             const int k = j & (NS - 1);
-            if constexpr (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[(NS - R1) + (r - 1) * NS + k]);
-                    if (INV) w.y = -w.y;
-                    v[b][r] = cmul(v[b][r], w);
-                }
-            }
+            if constexpr (NS > 1) twiddle16<INV>(v[b], tw + tw_offset<NF, NS>(), NS, k);
             dft_r<R, INV>(v[b]);
             const int base = (j - k) * R + k;
 #pragma unroll
@@ -176,7 +201,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
 // span NF/16, so its butterfly j holds the outputs q = j + r NF/16.
 template <int NF> struct FftPlan {
     static constexpr int LOG = ilog2c(NF);
-    static constexpr int R1 = (LOG % 4 == 0) ? 16 : (1 << (LOG % 4));
+    static constexpr int R1 = first_radix<NF>();
     static constexpr int NS_LAST = NF / 16;
 };
 
@@ -220,12 +245,7 @@ __device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2
     if (TPF == NS || j < NS) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = buf[padded(j + r * NS)];
-#pragma unroll
-        for (int r = 1; r < 16; ++r) {
-            float2 w = __ldg(&tw[(NS - FftPlan<NF>::R1) + (r - 1) * NS + j]);
-            if (INV) w.y = -w.y;
-            v[r] = cmul(v[r], w);
-        }
+        twiddle16<INV>(v, tw + tw_offset<NF, NS>(), NS, j);
         dft16<INV>(v);
     }
     __syncthreads();

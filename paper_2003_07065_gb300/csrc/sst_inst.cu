@@ -42,17 +42,17 @@ cudaError_t absmax(const SstDev &d, const float *x, float *partial, int grid, si
     return cudaGetLastError();
 }
 
-cudaError_t forward(const SstDev &d, int kind, const float *x, const float *gamma2, void *out0, void *out1,
+cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0, void *out1,
                     int grid, size_t smem, cudaStream_t st) {
     switch (kind) {
         case KIND_FWD_T:
-            k_forward<NF, MODE_T><<<grid, C::TPF, smem, st>>>(d, x, gamma2, (float2 *)out0, out1);
+            k_forward<NF, MODE_T><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         case KIND_FWD_STFT:
-            k_forward<NF, MODE_STFT><<<grid, C::TPF, smem, st>>>(d, x, gamma2, (float2 *)out0, out1);
+            k_forward<NF, MODE_STFT><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         case KIND_FWD_MAP:
-            k_forward<NF, MODE_MAP><<<grid, C::TPF, smem, st>>>(d, x, gamma2, (float2 *)out0, out1);
+            k_forward<NF, MODE_MAP><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         default: return cudaErrorInvalidValue;
     }

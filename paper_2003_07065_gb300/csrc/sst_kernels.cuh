@@ -149,9 +149,13 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     if (tid == 0) partial[blockIdx.x] = best;
 }
 
-// gamma^2 = frac^2 * max over partials; also stores max |S^g|
-__global__ void k_gamma(const float *__restrict__ partial, int count, float frac2,
-                        float *__restrict__ gamma2_out, float *__restrict__ maxv_out);
+// Reduce the pre-pass partial maxima into the call's scalars (see k_gamma in
+// sst_capi.cu): threshold, max |S^g| and the fixed-point scale of the T sums.
+__global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
+                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out);
+
+// Pre-pass of absolute-threshold plans: max |x| per CTA (bounds |S^g| by max|x| sum|g|).
+__global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict__ partial);
 
 // ---------------------------------------------------------------------------
 // Forward: per frame, packed FFT of x (g + i s g'), Hermitian split into S^g
@@ -160,30 +164,33 @@ __global__ void k_gamma(const float *__restrict__ partial, int count, float frac
 //   MODE_T   : T rows (F x nbo complex)
 //   MODE_STFT: S^g, S^g' rows (F x nb complex each), no threshold
 //   MODE_MAP : omega (F x nb float) and dest (F x nb int32)
-// The T sum is exact: every contribution is scaled by a per-frame power of
-// two 2^e, chosen so that any sum of the frame's terms stays below 2^62, and
-// converted to int64 (exactly, for all but sub-2^-39-relative terms);
-// shared-memory 64-bit integer adds are order independent, so the rounded
-// result does not depend on thread scheduling.
+// The T sum is exact: every contribution is scaled by the call's power of two
+// 2^e (from the pre-pass bound on |S^g|, chosen so that any sum of a frame's
+// terms stays below 2^62) and converted to int64 (exactly, for every term
+// above 2^-39 of the bound); shared-memory 64-bit integer adds are order
+// independent, so the rounded result does not depend on thread scheduling.
 // ---------------------------------------------------------------------------
 enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2 };
 
 template <int NF, int MODE>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
-k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma2_dev,
+k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
           float2 *__restrict__ out0, void *__restrict__ out1) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    float *red = reinterpret_cast<float *>(buf + C::BUF);
-    // after the frame buffer (BUF float2 = BUF x 8 bytes) and 128 bytes of reduction scratch
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
+    // after the frame buffer (BUF float2 = BUF x 8 bytes) and 128 bytes of slack:
+    // the T accumulators, real parts then imaginary parts
+    unsigned long long *acc_re = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
+    unsigned long long *acc_im = acc_re + d.nbo;
     const int tid = threadIdx.x;
-    const float gamma2 = d.relative ? __ldg(gamma2_dev) : d.gamma2_abs;
-
-    if (MODE == MODE_T)
-        for (int i = tid; i < 2 * d.nbo; i += TPF) acc[i] = 0ull;
+    const float gamma2 = d.relative ? sc->gamma2 : d.gamma2_abs;
+    float s1 = 1.f, s2 = 1.f, r1 = 1.f, r2 = 1.f;
+    if (MODE == MODE_T) {
+        s1 = sc->s1; s2 = sc->s2; r1 = sc->r1; r2 = sc->r2;
+        for (int i = tid; i < 2 * d.nbo; i += TPF) acc_re[i] = 0ull;
+    }
     // (the first __syncthreads below orders this before any atomic)
 
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x) {
@@ -193,14 +200,9 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
         scatter_band<NF>(zc, zm, d, tid, v);
         __syncthreads();
 
-        float2 Vv[C::KMAX];
-        int li[C::KMAX];
-        float maxc = 0.f;
 #pragma unroll
         for (int i = 0; i < C::KMAX; ++i) {
             const int kk = tid + i * TPF;
-            li[i] = -1;
-            Vv[i] = make_float2(0.f, 0.f);
             if (kk < d.nb) {
                 const int k = d.k_lo + kk;
                 const float2 zk = zc[kk];
@@ -230,38 +232,22 @@ k_forward(SstDev d, const float *__restrict__ x, const float *__restrict__ gamma
                     reinterpret_cast<int32_t *>(out1)[o] = l;
                     continue;
                 }
-                li[i] = l;
-                Vv[i] = V;
-                if (l >= 0) maxc = fmaxf(maxc, fmaxf(fabsf(V.x), fabsf(V.y)));
-            }
-        }
-        if (MODE != MODE_T) {
-            __syncthreads();  // band reads done before the next frame's first pass writes buf
-            continue;
-        }
-        maxc = block_max<C::NWARP>(maxc, red, tid);  // also orders band reads before the next frame
-        int e = 0;
-        if (maxc > 0.f) {
-            int ex;
-            frexpf(maxc, &ex);  // maxc < 2^ex
-            e = 62 - ex - d.log2_nb;
-#pragma unroll
-            for (int i = 0; i < C::KMAX; ++i) {
-                if (li[i] >= 0) {
-                    const long long qr = __float2ll_rn(ldexpf(Vv[i].x, e));
-                    const long long qi = __float2ll_rn(ldexpf(Vv[i].y, e));
-                    atomicAdd(&acc[2 * li[i]], (unsigned long long)qr);
-                    atomicAdd(&acc[2 * li[i] + 1], (unsigned long long)qi);
+                if (l >= 0) {
+                    atomicAdd(&acc_re[l], (unsigned long long)__float2ll_rn((V.x * s1) * s2));
+                    atomicAdd(&acc_im[l], (unsigned long long)__float2ll_rn((V.y * s1) * s2));
                 }
             }
         }
+        // all band reads and atomics done before the T row is read and the
+        // next frame's first pass overwrites buf
         __syncthreads();
+        if (MODE != MODE_T) continue;
         float2 *Trow = out0 + (size_t)m * d.nbo;
         for (int l = tid; l < d.nbo; l += TPF) {
-            const long long ar = (long long)acc[2 * l], ai = (long long)acc[2 * l + 1];
-            Trow[l] = make_float2(ldexpf(__ll2float_rn(ar), -e), ldexpf(__ll2float_rn(ai), -e));
-            acc[2 * l] = 0ull;
-            acc[2 * l + 1] = 0ull;
+            const long long ar = (long long)acc_re[l], ai = (long long)acc_im[l];
+            Trow[l] = make_float2((__ll2float_rn(ar) * r1) * r2, (__ll2float_rn(ai) * r1) * r2);
+            acc_re[l] = 0ull;
+            acc_im[l] = 0ull;
         }
         // the zeroing above is ordered before the next frame's atomics by the
         // __syncthreads inside the next frame's FFT
@@ -292,7 +278,7 @@ template <bool NARROW> struct InvTaps {
 };
 
 template <int NF, bool NARROW>
-__global__ void __launch_bounds__(Cfg<NF>::TPF)
+__global__ void __launch_bounds__(Cfg<NF>::TPF, (512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
 k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
     using C = Cfg<NF>;
     using TP = InvTaps<NARROW>;
@@ -398,11 +384,13 @@ k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
 #pragma unroll
                     for (int i = 0; i < TP::NACC; ++i) racc[i] = cadd(racc[i], v[TP::r_of(i)]);
                 } else {
+                    // exp(i 2 pi s n / (z NF)) = base_s(j) * c_s(r, wrapped) for n = j + r NF/16 (- NF)
+                    const float2 bs = __ldg(&d.twb[s * NS + tid]);
 #pragma unroll
                     for (int i = 0; i < TP::NACC; ++i) {
                         if (tap[i] != INT_MIN) {
                             const float2 w = (i == 16) ? __ldg(&d.twn[s])
-                                                       : __ldg(&d.twq[s * NF + tid + TP::r_of(i) * NS]);
+                                                       : cmul(bs, __ldg(&d.twc[(2 * s + (tap[i] < 0)) * 16 + TP::r_of(i)]));
                             racc[i] = cadd(racc[i], cmul(v[TP::r_of(i)], w));
                         }
                     }

@@ -22,7 +22,7 @@ struct KernelTable {
     cudaError_t (*occupancy)(int kind, size_t bytes, int *blocks);
     cudaError_t (*absmax)(const SstDev &d, const float *x, float *partial, int grid, size_t smem,
                           cudaStream_t st);
-    cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const float *gamma2, void *out0,
+    cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0,
                            void *out1, int grid, size_t smem, cudaStream_t st);
     // kind: KIND_INV (window L <= nf/2 + 1) or KIND_INV_WIDE (L <= nf + 1)
     cudaError_t (*inverse)(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st);
