@@ -421,7 +421,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     // ---- shared memory and grids
     pl->smem_fwd_x = kt->smem_frame;
     pl->smem_fwd_t = kt->smem_frame + 2 * sizeof(unsigned long long) * (size_t)nbo;
-    pl->smem_absmax = kt->smem_frame;
+    pl->smem_absmax = kt->smem_frame + sizeof(float2) * (kt->smem_frame - 128) / sizeof(float2);  // two frame buffers
     // inverse: frame buffer, the pair's two T rows regrouped by sub-grid, overlap-add segment
     pl->smem_inv = kt->smem_frame + 2 * sizeof(float2) * (size_t)z * nb + sizeof(float) * (size_t)d.seg_len;
     pl->inv_kind = (L <= nf / 2 + 1) ? KIND_INV : KIND_INV_WIDE;
@@ -445,7 +445,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         if (g_ > units) g_ = units;
         return (int)std::max<int64_t>(g_, 1);
     };
-    pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 1) / 2);
+    pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 3) / 4);
     pl->grid_fwd = grid_for(KIND_FWD_T, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
 

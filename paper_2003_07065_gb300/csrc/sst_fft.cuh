@@ -165,6 +165,81 @@ __device__ __forceinline__ void twiddle16(float2 *v, const float2 *__restrict__ 
     v[15] = cmul(v[15], cmul(w8, w7));
 }
 
+// The fifteen twiddles W^{r k}, r = 1..15, of a radix-16 butterfly (w[0] unused)
+template <bool INV>
+__device__ __forceinline__ void twiddles16(float2 (&w)[16], const float2 *__restrict__ t, int NS, int k) {
+    float2 w1 = __ldg(&t[k]), w2 = __ldg(&t[NS + k]), w4 = __ldg(&t[2 * NS + k]), w8 = __ldg(&t[3 * NS + k]);
+    if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; w8.y = -w8.y; }
+    w[1] = w1; w[2] = w2; w[4] = w4; w[8] = w8;
+    w[3] = cmul(w2, w1); w[5] = cmul(w4, w1); w[6] = cmul(w4, w2); w[7] = cmul(w4, w[3]);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w8, w[r]);
+}
+
+// ---- several independent frames per thread (instruction-level parallelism)
+// Frame f of NB lives at buf + f * BS (BS float2 apart).  Every routine below
+// assumes TPF >= NF / 16 (one radix-16 butterfly per thread and pass).
+
+// radix-16 pass with span NS > 1 on NB frames; twiddles shared by the frames
+template <int NF, int TPF, int NS, bool INV, int NB, int BS>
+__device__ __forceinline__ void stockham16_multi(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    constexpr int NBF = NF / 16;
+    const bool live = (TPF == NBF) || tid < NBF;
+    float2 v[NB][16];
+    if (live) {
+#pragma unroll
+        for (int f = 0; f < NB; ++f)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded(tid + r * NBF)];
+    }
+    __syncthreads();
+    if (live) {
+        const int k = tid & (NS - 1);
+        float2 w[16];
+        twiddles16<INV>(w, tw + tw_offset<NF, NS>(), NS, k);
+        const int base = (tid - k) * 16 + k;
+#pragma unroll
+        for (int f = 0; f < NB; ++f) {
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[f][r] = cmul(v[f][r], w[r]);
+            dft16<INV>(v[f]);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) buf[f * BS + padded(base + r * NS)] = v[f][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int NF, int TPF, int NS, bool INV, int NB, int BS>
+__device__ __forceinline__ void fft_middle_multi(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    if constexpr (NS < NF / 16) {
+        stockham16_multi<NF, TPF, NS, INV, NB, BS>(buf, tw, tid);
+        fft_middle_multi<NF, TPF, NS * 16, INV, NB, BS>(buf, tw, tid);
+    }
+}
+
+// last pass of NB frames into registers (see fft_last_to_regs); ends with a barrier
+template <int NF, int TPF, bool INV, int NB, int BS>
+__device__ __forceinline__ void fft_last_multi(const float2 *buf, const float2 *__restrict__ tw, int tid,
+                                               float2 (&v)[NB][16]) {
+    constexpr int NS = NF / 16;
+    if (TPF == NS || tid < NS) {
+#pragma unroll
+        for (int f = 0; f < NB; ++f)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded(tid + r * NS)];
+        float2 w[16];
+        twiddles16<INV>(w, tw + tw_offset<NF, NS>(), NS, tid);
+#pragma unroll
+        for (int f = 0; f < NB; ++f) {
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[f][r] = cmul(v[f][r], w[r]);
+            dft16<INV>(v[f]);
+        }
+    }
+    __syncthreads();
+}
+
 // One Stockham pass of radix R with span NS (product of earlier radices).
 template <int NF, int TPF, int R, int NS, bool INV>
 __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {

@@ -71,6 +71,52 @@ __device__ __forceinline__ float2 frame_sample(const SstDev &d, const float *__r
     return acc;
 }
 
+// First-pass inputs of one frame (or pair): u[b][r] = sample at FFT position
+// j + r NF/R1, j = tid + b TPF.  Interior frames (window inside [0, n)) with
+// L <= NF take a fast path: each position holds at most one tap, j = p or
+// p - NF, read through 32-bit offsets from the frame centre.
+template <int NF, bool PAIR>
+__device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>::R1], const SstDev &d,
+                                             const float *__restrict__ x, int64_t c1, int64_t c2, bool has2,
+                                             int tid) {
+    using C = Cfg<NF>;
+    const bool in1 = c1 - d.M >= 0 && c1 + d.M < d.n;
+    const bool in2 = !PAIR || (has2 && c2 - d.M >= 0 && c2 + d.M < d.n);
+    if (in1 && in2 && d.L <= NF) {
+        const float *x1 = x + c1;
+        const float *x2 = x + (PAIR ? c2 : c1);
+        const float2 *w = d.win + d.M;
+#pragma unroll
+        for (int b = 0; b < C::PER1; ++b) {
+            const int j = tid + b * C::TPF;
+#pragma unroll
+            for (int r = 0; r < C::R1; ++r) {
+                const int p = j + r * (NF / C::R1);
+                const bool lo = p <= d.M, hi = p >= NF - d.M;
+                const int jj = lo ? p : p - NF;
+                float2 val = make_float2(0.f, 0.f);
+                if ((C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1) && (lo || hi)) {
+                    const float2 wv = __ldg(&w[jj]);
+                    const float a = __ldg(&x1[jj]);
+                    if (!PAIR) val = make_float2(a * wv.x, a * wv.y);
+                    else val = make_float2(a * wv.x, __ldg(&x2[jj]) * wv.x);
+                }
+                u[b][r] = val;
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int b = 0; b < C::PER1; ++b) {
+        const int j = tid + b * C::TPF;
+#pragma unroll
+        for (int r = 0; r < C::R1; ++r)
+            u[b][r] = (C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1)
+                          ? frame_sample<NF, PAIR>(d, x, j + r * (NF / C::R1), c1, c2, has2)
+                          : make_float2(0.f, 0.f);
+    }
+}
+
 // Forward FFT of frame(s) (c1, c2 are frame centres): gather fused into the
 // first pass, outputs X[j + r NF/16] left in v (thread j = tid < NF/16).
 template <int NF, bool PAIR>
@@ -78,14 +124,7 @@ __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const 
                                             int64_t c2, bool has2, int tid, float2 (&v)[16]) {
     using C = Cfg<NF>;
     float2 u[C::PER1][C::R1];
-#pragma unroll
-    for (int b = 0; b < C::PER1; ++b) {
-        const int j = tid + b * C::TPF;
-        if (C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1) {
-#pragma unroll
-            for (int r = 0; r < C::R1; ++r) u[b][r] = frame_sample<NF, PAIR>(d, x, j + r * (NF / C::R1), c1, c2, has2);
-        }
-    }
+    gather_first<NF, PAIR>(u, d, x, c1, c2, has2, tid);
     fft_first_from_regs<NF, C::TPF, false>(buf, u, tid);
     __syncthreads();
     fft_middle<NF, C::TPF, C::R1, false>(buf, d.tw, tid);
@@ -114,33 +153,51 @@ __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDe
 // ---------------------------------------------------------------------------
 // Threshold pre-pass: max |S^g|^2 over in-band bins of every frame.  Two real
 // frames share one complex FFT: Z = FFT((x_a + i x_b) g), S_a = (Z[k] +
-// conj Z[-k]) / 2, S_b = (Z[k] - conj Z[-k]) / 2i.  One partial max per CTA.
+// conj Z[-k]) / 2, S_b = (Z[k] - conj Z[-k]) / 2i.  Each thread carries two
+// such FFTs at once (four frames per CTA iteration) to hide latency.  One
+// partial max per CTA.
 // ---------------------------------------------------------------------------
 template <int NF>
-__global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
+__global__ void __launch_bounds__(Cfg<NF>::TPF, (512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
 k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    constexpr int NB = 2;
+    constexpr int BS = C::BUF;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    float *red = reinterpret_cast<float *>(buf + C::BUF);
+    float *red = reinterpret_cast<float *>(buf + NB * C::BUF);
     const int tid = threadIdx.x;
     const int64_t npairs = (d.F + 1) / 2;
+    const int64_t nquads = (npairs + 1) / 2;
     float best = 0.f;
-    for (int64_t q = blockIdx.x; q < npairs; q += gridDim.x) {
-        const int64_t a = 2 * q, b = a + 1;
-        const bool hasb = b < d.F;
-        float2 v[16];
-        forward_fft<NF, true>(buf, d, x, a * d.hop, b * d.hop, hasb, tid, v);
-        float2 *zc = buf, *zm = buf + d.nb;
-        scatter_band<NF>(zc, zm, d, tid, v);
+    for (int64_t qq = blockIdx.x; qq < nquads; qq += gridDim.x) {
+        // FFT f (0, 1) packs frames a_f = 4 qq + 2 f and a_f + 1
+        float2 u[NB][C::PER1][C::R1];
+#pragma unroll
+        for (int f = 0; f < NB; ++f) {
+            const int64_t a = 4 * qq + 2 * f;
+            const bool hasa = a < d.F, hasb = a + 1 < d.F;
+            const int64_t ca = hasa ? a * d.hop : -(int64_t)4 * NF - d.n;   // absent frame: all taps outside [0, n)
+            gather_first<NF, true>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
+        }
+#pragma unroll
+        for (int f = 0; f < NB; ++f) fft_first_from_regs<NF, TPF, false>(buf + f * BS, u[f], tid);
         __syncthreads();
-        for (int kk = tid; kk < d.nb; kk += C::TPF) {
-            const float2 zk = zc[kk], zn = zm[kk];
-            const float ar = 0.5f * (zk.x + zn.x), ai = 0.5f * (zk.y - zn.y);
-            best = fmaxf(best, ar * ar + ai * ai);
-            if (hasb) {
+        fft_middle_multi<NF, TPF, C::R1, false, NB, BS>(buf, d.tw, tid);
+        float2 v[NB][16];
+        fft_last_multi<NF, TPF, false, NB, BS>(buf, d.tw, tid, v);
+#pragma unroll
+        for (int f = 0; f < NB; ++f) scatter_band<NF>(buf + f * BS, buf + f * BS + d.nb, d, tid, v[f]);
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < NB; ++f) {
+            const float2 *zc = buf + f * BS, *zm = zc + d.nb;
+            for (int kk = tid; kk < d.nb; kk += TPF) {
+                const float2 zk = zc[kk], zn = zm[kk];
+                const float ar = 0.5f * (zk.x + zn.x), ai = 0.5f * (zk.y - zn.y);
                 const float br = 0.5f * (zk.y + zn.y), bi = 0.5f * (zn.x - zk.x);
-                best = fmaxf(best, br * br + bi * bi);
+                best = fmaxf(best, fmaxf(ar * ar + ai * ai, br * br + bi * bi));
             }
         }
         __syncthreads();
@@ -319,17 +376,18 @@ k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
         const bool hasb = b < d.F;
         // stage both rows (contiguous in T), regrouped by sub-grid, with the
         // 1/2 weight of the DC and Nyquist destinations (Hermitian completion)
-        {
-            const float2 *src = T + (size_t)a * d.nbo;
-            const int cnt = (hasb ? 2 : 1) * d.nbo;
-            for (int i = tid; i < 2 * d.nbo; i += TPF) {
-                const int f = i >= d.nbo;
-                const int l = i - f * d.nbo;
-                float2 t = (i < cnt) ? __ldg(&src[i]) : make_float2(0.f, 0.f);
-                const int s = l % d.z, q = l / d.z;
+        for (int f = 0; f < 2; ++f) {
+            const float2 *src = T + (size_t)(a + f) * d.nbo;
+            const bool have = f == 0 || hasb;
+            for (int q = tid; q < nq; q += TPF) {
                 const int k = d.k_lo + q;
-                if (s == 0 && (k == 0 || 2 * k == NF)) t = cscale(t, 0.5f);
-                Tst[(f * d.z + s) * nq + q] = t;
+                const float w0 = (k == 0 || 2 * k == NF) ? 0.5f : 1.f;
+                for (int s = 0; s < d.z; ++s) {
+                    const int l = d.z * q + s;
+                    float2 t = (have && l < d.nbo) ? __ldg(&src[l]) : make_float2(0.f, 0.f);
+                    if (s == 0) t = cscale(t, w0);
+                    Tst[(f * d.z + s) * nq + q] = t;
+                }
             }
         }
         __syncthreads();
@@ -357,13 +415,13 @@ k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
                     float2 y = make_float2(0.f, 0.f);
                     if (C::PER1 * TPF == NF / C::R1 || j < NF / C::R1) {
                         const int q = k - d.k_lo;
-                        if (q >= 0 && q < nqs) {
+                        if ((unsigned)q < (unsigned)nqs) {
                             const float2 xa = Ta[q], xb = Tb[q];
                             y.x += xa.x - xb.y;
                             y.y += xa.y + xb.x;
                         }
                         const int qm = ((NF - k - dl) & (NF - 1)) - d.k_lo;
-                        if (qm >= 0 && qm < nqb) {
+                        if ((unsigned)qm < (unsigned)nqb) {
                             const float2 xa = Tam[qm], xb = Tbm[qm];
                             // conj(xa) + i conj(xb)
                             y.x += xa.x + xb.y;
