@@ -164,6 +164,48 @@ sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *
 #define SST_STATIC_SCRATCH_BYTES 65536
 sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *stream);
 
+/* ---- Batched execution (many channels, uneven lengths, mixed parameters).
+ * A batch groups the channels' work by DFT length and runs each group as one
+ * persistent launch over a device table of work items (frame ranges,
+ * inverse tiles); groups of the same phase run on parallel streams.  The
+ * per-channel results are bit-identical to sst_forward_inverse on each item.
+ * With SST_BATCH_GRAPH the whole launch sequence is captured into a CUDA
+ * graph on the first sst_batch_run and replayed afterwards (re-captured if
+ * the workspace or stream changes).  Plans and buffers must outlive the
+ * batch. */
+typedef struct {
+    sst_plan_t plan;   /* the channel's plan */
+    const float *x;    /* device, n floats */
+    int64_t n;         /* must equal the plan's n */
+    float *tfr;        /* device, F x bins complex */
+    float *xhat;       /* device, n floats */
+} sst_batch_item;
+typedef struct sst_batch *sst_batch_t;
+#define SST_BATCH_GRAPH 0x1u
+
+/* Build the work tables (device memory owned by the batch).  Knobs come from
+ * the tuning cache (in memory; also the file named by SST_TUNE_CACHE) when
+ * a batch of the same shape class was tuned before, else defaults. */
+sst_status sst_batch_create(const sst_batch_item *items, int32_t count, uint32_t flags, sst_batch_t *out);
+/* Workspace bytes sst_batch_run needs (valid for every knob setting). */
+sst_status sst_batch_workspace(sst_batch_t b, size_t *bytes);
+/* Enqueue the whole batch (pre-pass, per-channel thresholds, forward,
+ * inverse, finalize) on `stream`. */
+sst_status sst_batch_run(sst_batch_t b, void *workspace_dev, void *stream);
+/* Autotuner: times candidate work granularities and grid sizes on this
+ * batch (runs it ~4 times per candidate; synchronises), keeps the fastest,
+ * stores it in the tuning cache, and reports the untuned (default) and tuned
+ * milliseconds per run. */
+sst_status sst_batch_tune(sst_batch_t b, void *workspace_dev, void *stream, double *untuned_ms, double *tuned_ms);
+/* Current knobs: frames per forward item, frame quads per pre-pass item, CTAs per SM multiplier. */
+sst_status sst_batch_knobs(sst_batch_t b, int32_t *fwd_frames, int32_t *abs_quads, int32_t *grid_mul);
+void sst_batch_destroy(sst_batch_t b);
+/* One-shot: create, run, synchronise `stream`, destroy. */
+sst_status sst_batch_submit(const sst_batch_item *items, int32_t count, void *workspace_dev, size_t workspace_bytes,
+                            void *stream);
+/* Workspace bytes sst_batch_submit needs for these items. */
+sst_status sst_batch_workspace_for(const sst_batch_item *items, int32_t count, size_t *bytes);
+
 /* Block until `stream` is idle; returns SST_ECUDA with the message of any
  * pending asynchronous error. */
 sst_status sst_sync(void *stream);

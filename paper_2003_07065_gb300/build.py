@@ -20,6 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsst.so")
 NFS = (64, 128, 256, 512, 1024, 2048, 4096, 8192)
+HOST_UNITS = ("sst_capi", "sst_batch")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -61,8 +62,9 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     os.makedirs(objdir, exist_ok=True)
     jobs = [([nvcc] + flags + [f"-DSST_NF={nf}", "-c", os.path.join(CSRC, "sst_inst.cu"),
                                "-o", os.path.join(objdir, f"inst_{nf}.o")]) for nf in NFS]
-    jobs.append([nvcc] + flags + ["-c", os.path.join(CSRC, "sst_capi.cu"),
-                                  "-o", os.path.join(objdir, "capi.o")])
+    for name in HOST_UNITS:
+        jobs.append([nvcc] + flags + ["-c", os.path.join(CSRC, name + ".cu"),
+                                      "-o", os.path.join(objdir, name + ".o")])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -75,7 +77,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    objs = [os.path.join(objdir, f"inst_{nf}.o") for nf in NFS] + [os.path.join(objdir, "capi.o")]
+    objs = [os.path.join(objdir, f"inst_{nf}.o") for nf in NFS] + \
+        [os.path.join(objdir, name + ".o") for name in HOST_UNITS]
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -9,11 +9,8 @@
 #include <string>
 #include <vector>
 
-#include "sst.h"
-#include "sst_dev.h"
-#include "sst_launch.h"
-
-#define SST_API extern "C" __attribute__((visibility("default")))
+#include "sst_internal.h"
+#include "sst_kernels.cuh"
 
 namespace sst {
 
@@ -99,25 +96,9 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
     }
 }
 
-__device__ __forceinline__ float recip_norm(const SstDev &d, int64_t p) {
-    if (p < d.EL) return d.rD_left[p];
-    if (p >= d.ER) return d.rD_right[p - d.ER];
-    return d.rD_per[p % d.hop];
-}
-
-// xhat[p] = (sum over the tiles whose segment covers p, in tile order) / D[p]
 __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat) {
-    const int64_t BH = (int64_t)d.B * d.hop;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t num = p + d.M - d.seg_len + 1;
-        const int64_t tlo = num <= 0 ? 0 : (num + BH - 1) / BH;
-        int64_t thi = (p + d.M) / BH;
-        if (thi > d.ntiles - 1) thi = d.ntiles - 1;
-        float s = 0.f;
-        for (int64_t t = tlo; t <= thi; ++t) s += partial[t * d.seg_len + (p + d.M - t * BH)];
-        xhat[p] = s * recip_norm(d, p);
-    }
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.n; p += (int64_t)gridDim.x * blockDim.x)
+        xhat[p] = finalize_value(d, partial, p);
 }
 
 }  // namespace sst
@@ -125,10 +106,11 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
 using namespace sst;
 
 // ------------------------------------------------------------ error state
+namespace sst {
 static thread_local std::string g_err;
 static std::atomic<uint64_t> g_launches{0};
 
-static sst_status fail(sst_status s, const char *fmt, ...) {
+sst_status fail(sst_status s, const char *fmt, ...) {
     char b[512];
     va_list ap;
     va_start(ap, fmt);
@@ -138,18 +120,13 @@ static sst_status fail(sst_status s, const char *fmt, ...) {
     return s;
 }
 
-static sst_status cuda_fail(cudaError_t e, const char *what) {
+sst_status cuda_fail(cudaError_t e, const char *what) {
     return fail(SST_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define SST_CU(call, what)                                 \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ------------------------------------------------------------ profiling
-enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER };
 static const char *kPkNames[SST_PROFILE_KINDS] = {"absmax", "gamma", "forward", "stft", "map", "inverse",
                                                   "finalize", "other"};
 struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -157,52 +134,12 @@ static std::mutex g_prof_mu;
 static std::vector<ProfRec> g_prof;
 static std::atomic<int> g_prof_on{0};
 
-struct ProfScope {
-    int kind; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(int k, cudaStream_t s) : kind(k), st(s) {
-        if (g_prof_on.load(std::memory_order_relaxed)) {
-            if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) cudaEventRecord(a, st);
-            else a = b = nullptr;
-        }
-    }
-    void done() {
-        if (a && b) {
-            cudaEventRecord(b, st);
-            std::lock_guard<std::mutex> lk(g_prof_mu);
-            g_prof.push_back({kind, a, b});
-            a = b = nullptr;
-        }
-    }
-    ~ProfScope() {
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
-    }
-};
-
-#define SST_LAUNCHED_K(kind, st, call, what)               \
-    do {                                                   \
-        ProfScope ps_(kind, st);                           \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-        ps_.done();                                        \
-        g_launches.fetch_add(1, std::memory_order_relaxed); \
-    } while (0)
-
-// ------------------------------------------------------------ plan
-struct sst_plan {
-    sst_params p;
-    int device = 0;
-    int num_sms = 0;
-    SstDev d;
-    const KernelTable *kt = nullptr;
-    void *dmem = nullptr;
-    float gamma_frac2 = 0.f;
-    float sum_abs_g = 0.f;   // bound factor |S^g| <= max|x| sum|g| (rounded up)
-    size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
-    int inv_kind = KIND_INV;
-    int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
-    size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
-};
+bool profiling_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+void profile_record(int kind, cudaEvent_t a, cudaEvent_t b) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back({kind, a, b});
+}
+}  // namespace sst
 
 static int64_t round_half_up(double v) { return (int64_t)std::floor(v + 0.5); }
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -505,7 +442,7 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
         } else {
             e = pl->kt->absmax(pl->d, x, partial, pl->grid_absmax, pl->smem_absmax, st);
             if (e != cudaSuccess) return cuda_fail(e, "absmax launch");
-            g_launches.fetch_add(1, std::memory_order_relaxed);
+            count_launch();
         }
     } else {
         int64_t blocks = (pl->d.n + 255) / 256;
@@ -513,7 +450,7 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
         k_absx<<<(unsigned)blocks, 256, 0, st>>>(x, pl->d.n, partial);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "absx launch");
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        count_launch();
     }
     const int count = pl->d.relative ? pl->grid_absmax
                                      : (int)std::min<int64_t>((pl->d.n + 255) / 256, pl->grid_absmax);
@@ -528,7 +465,7 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
                                    pl->d.log2_nb, sc, maxv_out);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "gamma launch");
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        count_launch();
     }
     return SST_OK;
 }
@@ -686,7 +623,7 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     if (s != SST_OK) return s;
     SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
            "forward launch");
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_launch();
     return SST_OK;
 }
 
@@ -696,7 +633,7 @@ SST_API sst_status sst_sync(void *stream) {
     return SST_OK;
 }
 
-SST_API uint64_t sst_launch_count(void) { return g_launches.load(); }
+SST_API uint64_t sst_launch_count(void) { return sst::g_launches.load(); }
 
 SST_API sst_status sst_profile_enable(int on) {
     g_prof_on.store(on ? 1 : 0);

@@ -42,4 +42,28 @@ struct SstScalars {
     float pad[2];
 };
 
+// One channel of a batch (sst_batch_*): its plan's device view (with the
+// batch's own inverse tiling), its buffers and its slice of the workspace.
+struct BatchChan {
+    SstDev d;
+    const float *x;
+    float2 *T;
+    float *xhat;
+    SstScalars *sc;
+    float *ola;        // overlap-add partials, d.ntiles x d.seg_len
+    float frac2;       // relative threshold fraction squared
+    float sum_abs_g;   // |S^g| <= max|x| sum|g| (absolute-threshold channels)
+    int part0;         // first pre-pass partial of this channel
+    int nparts;        // number of pre-pass partials of this channel
+};
+
+// A unit of batched work: channel `chan`, units [begin, end) -- quads of
+// frames (pre-pass, relative channels), samples (pre-pass of absolute
+// channels, finalize), frames (forward) or one inverse tile (begin).
+struct BatchItem {
+    int chan;
+    int pad;
+    int64_t begin, end;
+};
+
 }  // namespace sst

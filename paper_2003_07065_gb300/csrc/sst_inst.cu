@@ -21,6 +21,10 @@ const void *kernel_of(int kind) {
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
         case KIND_INV: return (const void *)k_inverse<NF, true>;
         case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
+        case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
+        case KIND_B_FWD: return (const void *)k_forward_batch<NF>;
+        case KIND_B_INV: return (const void *)k_inverse_batch<NF, true>;
+        case KIND_B_INV_WIDE: return (const void *)k_inverse_batch<NF, false>;
     }
     return nullptr;
 }
@@ -69,8 +73,20 @@ cudaError_t inverse(const SstDev &d, int kind, const float2 *T, float *partial, 
     return cudaGetLastError();
 }
 
+cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nitems, int max_nbo, int grid,
+                  size_t smem, float *partial, cudaStream_t st) {
+    switch (kind) {
+        case KIND_B_ABSMAX: k_absmax_batch<NF><<<grid, C::TPF, smem, st>>>(ch, items, nitems, partial); break;
+        case KIND_B_FWD: k_forward_batch<NF><<<grid, C::TPF, smem, st>>>(ch, items, nitems, max_nbo); break;
+        case KIND_B_INV: k_inverse_batch<NF, true><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
+        case KIND_B_INV_WIDE: k_inverse_batch<NF, false><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 const KernelTable table = {NF, C::TPF, (size_t)C::BUF * sizeof(float2) + 128, set_smem, occupancy,
-                           absmax, forward, inverse};
+                           absmax, forward, inverse, batch};
 
 }  // namespace
 

@@ -1,0 +1,81 @@
+// Internal declarations shared by the host translation units of libsst.so
+// (plan object, error reporting, launch accounting, per-kernel profiling).
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "sst.h"
+#include "sst_dev.h"
+#include "sst_launch.h"
+
+#define SST_API extern "C" __attribute__((visibility("default")))
+
+namespace sst {
+
+// error reporting: sets the thread-local message returned by sst_last_error
+sst_status fail(sst_status s, const char *fmt, ...);
+sst_status cuda_fail(cudaError_t e, const char *what);
+void count_launch();
+
+#define SST_CU(call, what)                                      \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::sst::cuda_fail(e_, what); \
+    } while (0)
+
+// per-kernel timing (sst_profile_enable): events around each launch
+enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER };
+bool profiling_on();
+void profile_record(int kind, cudaEvent_t a, cudaEvent_t b);
+
+struct ProfScope {
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(int k, cudaStream_t s) : kind(k), st(s) {
+        if (profiling_on()) {
+            if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) cudaEventRecord(a, st);
+            else a = b = nullptr;
+        }
+    }
+    void done() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            profile_record(kind, a, b);
+            a = b = nullptr;
+        }
+    }
+    ~ProfScope() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+#define SST_LAUNCHED_K(kind, st, call, what)                      \
+    do {                                                          \
+        ::sst::ProfScope ps_(kind, st);                           \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::sst::cuda_fail(e_, what); \
+        ps_.done();                                               \
+        ::sst::count_launch();                                    \
+    } while (0)
+
+}  // namespace sst
+
+// ------------------------------------------------------------ plan
+struct sst_plan {
+    sst_params p;
+    int device = 0;
+    int num_sms = 0;
+    sst::SstDev d;
+    const sst::KernelTable *kt = nullptr;
+    void *dmem = nullptr;
+    float gamma_frac2 = 0.f;
+    float sum_abs_g = 0.f;   // bound factor |S^g| <= max|x| sum|g| (rounded up)
+    size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
+    int inv_kind = sst::KIND_INV;
+    int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
+    size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
+};

@@ -158,50 +158,57 @@ __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDe
 // partial max per CTA.
 // ---------------------------------------------------------------------------
 template <int NF>
-__global__ void __launch_bounds__(Cfg<NF>::TPF, (512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
-k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
+__device__ __forceinline__ float absmax_quad(const SstDev &d, const float *__restrict__ x, int64_t qq, float2 *buf,
+                                             int tid, float best) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     constexpr int NB = 2;
     constexpr int BS = C::BUF;
+    // FFT f (0, 1) packs frames a_f = 4 qq + 2 f and a_f + 1
+    float2 u[NB][C::PER1][C::R1];
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+        const int64_t a = 4 * qq + 2 * f;
+        const bool hasa = a < d.F, hasb = a + 1 < d.F;
+        const int64_t ca = hasa ? a * d.hop : -(int64_t)4 * NF - d.n;   // absent frame: all taps outside [0, n)
+        gather_first<NF, true>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
+    }
+#pragma unroll
+    for (int f = 0; f < NB; ++f) fft_first_from_regs<NF, TPF, false>(buf + f * BS, u[f], tid);
+    __syncthreads();
+    fft_middle_multi<NF, TPF, C::R1, false, NB, BS>(buf, d.tw, tid);
+    float2 v[NB][16];
+    fft_last_multi<NF, TPF, false, NB, BS>(buf, d.tw, tid, v);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) scatter_band<NF>(buf + f * BS, buf + f * BS + d.nb, d, tid, v[f]);
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+        const float2 *zc = buf + f * BS, *zm = zc + d.nb;
+        for (int kk = tid; kk < d.nb; kk += TPF) {
+            const float2 zk = zc[kk], zn = zm[kk];
+            const float ar = 0.5f * (zk.x + zn.x), ai = 0.5f * (zk.y - zn.y);
+            const float br = 0.5f * (zk.y + zn.y), bi = 0.5f * (zn.x - zk.x);
+            best = fmaxf(best, fmaxf(ar * ar + ai * ai, br * br + bi * bi));
+        }
+    }
+    __syncthreads();
+    return best;
+}
+
+#define SST_ABSMAX_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
+
+template <int NF>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_ABSMAX_MINB)
+k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
+    using C = Cfg<NF>;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    float *red = reinterpret_cast<float *>(buf + NB * C::BUF);
+    float *red = reinterpret_cast<float *>(buf + 2 * C::BUF);
     const int tid = threadIdx.x;
-    const int64_t npairs = (d.F + 1) / 2;
-    const int64_t nquads = (npairs + 1) / 2;
+    const int64_t nquads = (d.F + 3) / 4;
     float best = 0.f;
-    for (int64_t qq = blockIdx.x; qq < nquads; qq += gridDim.x) {
-        // FFT f (0, 1) packs frames a_f = 4 qq + 2 f and a_f + 1
-        float2 u[NB][C::PER1][C::R1];
-#pragma unroll
-        for (int f = 0; f < NB; ++f) {
-            const int64_t a = 4 * qq + 2 * f;
-            const bool hasa = a < d.F, hasb = a + 1 < d.F;
-            const int64_t ca = hasa ? a * d.hop : -(int64_t)4 * NF - d.n;   // absent frame: all taps outside [0, n)
-            gather_first<NF, true>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
-        }
-#pragma unroll
-        for (int f = 0; f < NB; ++f) fft_first_from_regs<NF, TPF, false>(buf + f * BS, u[f], tid);
-        __syncthreads();
-        fft_middle_multi<NF, TPF, C::R1, false, NB, BS>(buf, d.tw, tid);
-        float2 v[NB][16];
-        fft_last_multi<NF, TPF, false, NB, BS>(buf, d.tw, tid, v);
-#pragma unroll
-        for (int f = 0; f < NB; ++f) scatter_band<NF>(buf + f * BS, buf + f * BS + d.nb, d, tid, v[f]);
-        __syncthreads();
-#pragma unroll
-        for (int f = 0; f < NB; ++f) {
-            const float2 *zc = buf + f * BS, *zm = zc + d.nb;
-            for (int kk = tid; kk < d.nb; kk += TPF) {
-                const float2 zk = zc[kk], zn = zm[kk];
-                const float ar = 0.5f * (zk.x + zn.x), ai = 0.5f * (zk.y - zn.y);
-                const float br = 0.5f * (zk.y + zn.y), bi = 0.5f * (zn.x - zk.x);
-                best = fmaxf(best, fmaxf(ar * ar + ai * ai, br * br + bi * bi));
-            }
-        }
-        __syncthreads();
-    }
+    for (int64_t qq = blockIdx.x; qq < nquads; qq += gridDim.x) best = absmax_quad<NF>(d, x, qq, buf, tid, best);
     best = block_max<C::NWARP>(best, red, tid);
     if (tid == 0) partial[blockIdx.x] = best;
 }
@@ -229,12 +236,93 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
 // ---------------------------------------------------------------------------
 enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2 };
 
+struct FwdScale {
+    float gamma2;   // threshold squared
+    float s1, s2;   // fixed-point scale 2^e = s1 s2
+    float r1, r2;   // 2^-e = r1 r2
+};
+
+__device__ __forceinline__ FwdScale fwd_scale(const SstDev &d, const SstScalars *__restrict__ sc, bool need_t) {
+    FwdScale f;
+    f.gamma2 = d.relative ? sc->gamma2 : d.gamma2_abs;
+    f.s1 = f.s2 = f.r1 = f.r2 = 1.f;
+    if (need_t) { f.s1 = sc->s1; f.s2 = sc->s2; f.r1 = sc->r1; f.r2 = sc->r2; }
+    return f;
+}
+
+// One frame m of the forward transform.  acc_re / acc_im (nbo each) must be
+// zero on entry and are zero again on return (MODE_T).
+template <int NF, int MODE>
+__device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
+                                              float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
+                                              float2 *buf, unsigned long long *acc_re, unsigned long long *acc_im,
+                                              int tid) {
+    using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    float2 v[16];
+    forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);
+    float2 *zc = buf, *zm = buf + d.nb;
+    scatter_band<NF>(zc, zm, d, tid, v);
+    __syncthreads();
+
+#pragma unroll
+    for (int i = 0; i < C::KMAX; ++i) {
+        const int kk = tid + i * TPF;
+        if (kk < d.nb) {
+            const int k = d.k_lo + kk;
+            const float2 zk = zc[kk];
+            const float2 zn = zm[kk];
+            const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            const float2 Vd = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+            const size_t o = (size_t)m * d.nb + kk;
+            if (MODE == MODE_STFT) {
+                out0[o] = V;
+                reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
+                continue;
+            }
+            const float mag2 = V.x * V.x + V.y * V.y;
+            // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36)
+            const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
+            int l = -1;
+            if (mag2 > fs.gamma2) {
+                const float f = floorf(fmaf((float)d.z, delta, 0.5f));
+                l = -2;
+                if (f > -1073741824.f && f < 1073741824.f) {
+                    const int lc = d.z * (k - d.k_lo) + (int)f;
+                    if (lc >= 0 && lc < d.nbo) l = lc;
+                }
+            }
+            if (MODE == MODE_MAP) {
+                reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
+                reinterpret_cast<int32_t *>(out1)[o] = l;
+                continue;
+            }
+            if (l >= 0) {
+                atomicAdd(&acc_re[l], (unsigned long long)__float2ll_rn((V.x * fs.s1) * fs.s2));
+                atomicAdd(&acc_im[l], (unsigned long long)__float2ll_rn((V.y * fs.s1) * fs.s2));
+            }
+        }
+    }
+    // all band reads and atomics done before the T row is read and the next
+    // frame's first pass overwrites buf
+    __syncthreads();
+    if (MODE != MODE_T) return;
+    float2 *Trow = out0 + (size_t)m * d.nbo;
+    for (int l = tid; l < d.nbo; l += TPF) {
+        const long long ar = (long long)acc_re[l], ai = (long long)acc_im[l];
+        Trow[l] = make_float2((__ll2float_rn(ar) * fs.r1) * fs.r2, (__ll2float_rn(ai) * fs.r1) * fs.r2);
+        acc_re[l] = 0ull;
+        acc_im[l] = 0ull;
+    }
+    // the zeroing above is ordered before the next frame's atomics by the
+    // __syncthreads inside the next frame's FFT
+}
+
 template <int NF, int MODE>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
 k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
           float2 *__restrict__ out0, void *__restrict__ out1) {
     using C = Cfg<NF>;
-    constexpr int TPF = C::TPF;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     // after the frame buffer (BUF float2 = BUF x 8 bytes) and 128 bytes of slack:
@@ -242,73 +330,12 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
     unsigned long long *acc_re = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
     unsigned long long *acc_im = acc_re + d.nbo;
     const int tid = threadIdx.x;
-    const float gamma2 = d.relative ? sc->gamma2 : d.gamma2_abs;
-    float s1 = 1.f, s2 = 1.f, r1 = 1.f, r2 = 1.f;
-    if (MODE == MODE_T) {
-        s1 = sc->s1; s2 = sc->s2; r1 = sc->r1; r2 = sc->r2;
-        for (int i = tid; i < 2 * d.nbo; i += TPF) acc_re[i] = 0ull;
-    }
-    // (the first __syncthreads below orders this before any atomic)
-
-    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x) {
-        float2 v[16];
-        forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);
-        float2 *zc = buf, *zm = buf + d.nb;
-        scatter_band<NF>(zc, zm, d, tid, v);
-        __syncthreads();
-
-#pragma unroll
-        for (int i = 0; i < C::KMAX; ++i) {
-            const int kk = tid + i * TPF;
-            if (kk < d.nb) {
-                const int k = d.k_lo + kk;
-                const float2 zk = zc[kk];
-                const float2 zn = zm[kk];
-                const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-                const float2 Vd = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
-                const size_t o = (size_t)m * d.nb + kk;
-                if (MODE == MODE_STFT) {
-                    out0[o] = V;
-                    reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
-                    continue;
-                }
-                const float mag2 = V.x * V.x + V.y * V.y;
-                // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36)
-                const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
-                int l = -1;
-                if (mag2 > gamma2) {
-                    const float f = floorf(fmaf((float)d.z, delta, 0.5f));
-                    l = -2;
-                    if (f > -1073741824.f && f < 1073741824.f) {
-                        const int lc = d.z * (k - d.k_lo) + (int)f;
-                        if (lc >= 0 && lc < d.nbo) l = lc;
-                    }
-                }
-                if (MODE == MODE_MAP) {
-                    reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
-                    reinterpret_cast<int32_t *>(out1)[o] = l;
-                    continue;
-                }
-                if (l >= 0) {
-                    atomicAdd(&acc_re[l], (unsigned long long)__float2ll_rn((V.x * s1) * s2));
-                    atomicAdd(&acc_im[l], (unsigned long long)__float2ll_rn((V.y * s1) * s2));
-                }
-            }
-        }
-        // all band reads and atomics done before the T row is read and the
-        // next frame's first pass overwrites buf
-        __syncthreads();
-        if (MODE != MODE_T) continue;
-        float2 *Trow = out0 + (size_t)m * d.nbo;
-        for (int l = tid; l < d.nbo; l += TPF) {
-            const long long ar = (long long)acc_re[l], ai = (long long)acc_im[l];
-            Trow[l] = make_float2((__ll2float_rn(ar) * r1) * r2, (__ll2float_rn(ai) * r1) * r2);
-            acc_re[l] = 0ull;
-            acc_im[l] = 0ull;
-        }
-        // the zeroing above is ordered before the next frame's atomics by the
-        // __syncthreads inside the next frame's FFT
-    }
+    const FwdScale fs = fwd_scale(d, sc, MODE == MODE_T);
+    if (MODE == MODE_T)
+        for (int i = tid; i < 2 * d.nbo; i += C::TPF) acc_re[i] = 0ull;
+    // (the first __syncthreads in forward_frame orders this before any atomic)
+    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
+        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc_re, acc_im, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,21 +361,21 @@ template <bool NARROW> struct InvTaps {
     __host__ __device__ static constexpr int r_of(int i) { return NARROW ? (i <= 4 ? i : i + 7) : (i < 16 ? i : 8); }
 };
 
+// One inverse tile; smem4 is the kernel's dynamic shared memory.  Ends with a
+// barrier-free write of the tile's segment (callers looping over tiles sync
+// before the next tile zeroes the segment).
 template <int NF, bool NARROW>
-__global__ void __launch_bounds__(Cfg<NF>::TPF, (512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
-k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
+__device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__restrict__ T, float *__restrict__ partial,
+                                             int64_t tile, float4 *smem4, int tid) {
     using C = Cfg<NF>;
     using TP = InvTaps<NARROW>;
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
-    extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     // staged rows: Tst[f][s][q] = w T_f[z q + s], q in [0, nq), nq = N_r + 1
     const int nq = d.k_hi - d.k_lo + 1;
     float2 *Tst = buf + C::BUF;
     float *seg = reinterpret_cast<float *>(Tst + 2 * d.z * nq);
-    const int tid = threadIdx.x;
-    const int64_t tile = blockIdx.x;
     const int64_t m0 = tile * d.B;
     const float cnorm = 1.0f / (float)NF;
     const bool live = (TPF == NS) || tid < NS;
@@ -473,6 +500,123 @@ k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
     for (int i = tid; i < d.seg_len; i += TPF) out[i] = seg[i];
 }
 
+#define SST_INV_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
+
+template <int NF, bool NARROW>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_INV_MINB)
+k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
+    extern __shared__ float4 smem4[];
+    inverse_tile<NF, NARROW>(d, T, partial, blockIdx.x, smem4, threadIdx.x);
+}
+
+__device__ __forceinline__ float recip_norm(const SstDev &d, int64_t p) {
+    if (p < d.EL) return d.rD_left[p];
+    if (p >= d.ER) return d.rD_right[p - d.ER];
+    return d.rD_per[p % d.hop];
+}
+
+// xhat[p] = (sum over the tiles whose segment covers p, in tile order) / D[p]
+__device__ __forceinline__ float finalize_value(const SstDev &d, const float *__restrict__ partial, int64_t p) {
+    const int64_t BH = (int64_t)d.B * d.hop;
+    const int64_t num = p + d.M - d.seg_len + 1;
+    const int64_t tlo = num <= 0 ? 0 : (num + BH - 1) / BH;
+    int64_t thi = (p + d.M) / BH;
+    if (thi > d.ntiles - 1) thi = d.ntiles - 1;
+    float s = 0.f;
+    for (int64_t t = tlo; t <= thi; ++t) s += partial[t * d.seg_len + (p + d.M - t * BH)];
+    return s * recip_norm(d, p);
+}
+
 __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat);
+
+// ---------------------------------------------------------------------------
+// Batched kernels: persistent CTAs walk a table of work items (BatchItem) of
+// many channels that share this NF.  Each item's SstDev is copied into
+// shared memory first; the per-unit bodies are the single-plan ones.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_chan(SstDev &sd, const BatchChan *__restrict__ ch, int c, int tid, int nthr) {
+    const int *src = reinterpret_cast<const int *>(&ch[c].d);
+    int *dst = reinterpret_cast<int *>(&sd);
+    for (int i = tid; i < (int)(sizeof(SstDev) / sizeof(int)); i += nthr) dst[i] = src[i];
+}
+
+// a channel descriptor this NF's kernels can run (guards every loop bound
+// against a corrupt table: such items are skipped)
+template <int NF> __device__ __forceinline__ bool chan_ok(const SstDev &d) {
+    return d.nf == NF && d.z >= 1 && d.z <= 16 && d.B >= 2 && d.B <= (1 << 20) && d.hop >= 1 && d.L >= 3 &&
+           d.L <= NF + 1 && d.n >= 1 && d.F >= 1 && d.nbo >= 1 && d.nb >= 1 && d.seg_len >= d.L;
+}
+
+template <int NF>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_ABSMAX_MINB)
+k_absmax_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems,
+               float *__restrict__ partial) {
+    using C = Cfg<NF>;
+    __shared__ SstDev sd;
+    __shared__ float red[32];
+    extern __shared__ float4 smem4[];
+    float2 *buf = reinterpret_cast<float2 *>(smem4);
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        load_chan(sd, ch, w.chan, tid, C::TPF);
+        __syncthreads();
+        const float *x = ch[w.chan].x;
+        float best = 0.f;
+        if (!chan_ok<NF>(sd)) {
+        } else if (sd.relative) {
+            for (int64_t qq = w.begin; qq < w.end; ++qq) best = absmax_quad<NF>(sd, x, qq, buf, tid, best);
+        } else {
+            for (int64_t p = w.begin + tid; p < w.end; p += C::TPF) best = fmaxf(best, fabsf(x[p]));
+        }
+        best = block_max<C::NWARP>(best, red, tid);
+        if (tid == 0) partial[it] = best;
+    }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
+k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems, int max_nbo) {
+    using C = Cfg<NF>;
+    __shared__ SstDev sd;
+    extern __shared__ float4 smem4[];
+    float2 *buf = reinterpret_cast<float2 *>(smem4);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * max_nbo; i += C::TPF) acc[i] = 0ull;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        __syncthreads();   // previous item done with sd
+        load_chan(sd, ch, w.chan, tid, C::TPF);
+        __syncthreads();
+        const BatchChan &c = ch[w.chan];
+        if (!chan_ok<NF>(sd) || sd.nbo > max_nbo || w.end > sd.F) continue;
+        const FwdScale fs = fwd_scale(sd, c.sc, true);
+        for (int64_t m = w.begin; m < w.end; ++m)
+            forward_frame<NF, MODE_T>(sd, c.x, fs, c.T, nullptr, m, buf, acc, acc + sd.nbo, tid);
+    }
+}
+
+template <int NF, bool NARROW>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_INV_MINB)
+k_inverse_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems) {
+    using C = Cfg<NF>;
+    __shared__ SstDev sd;
+    extern __shared__ float4 smem4[];
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        __syncthreads();   // previous tile's segment written out, sd free
+        load_chan(sd, ch, w.chan, tid, C::TPF);
+        __syncthreads();
+        if (!chan_ok<NF>(sd) || w.begin >= sd.ntiles) continue;
+        inverse_tile<NF, NARROW>(sd, ch[w.chan].T, ch[w.chan].ola, w.begin, smem4, tid);
+    }
+}
+
+// per-channel reductions of the batched pre-pass (one CTA per channel)
+__global__ void k_gamma_batch(BatchChan *__restrict__ ch, int nchan, const float *__restrict__ partial);
+// xhat of every channel (items: sample ranges)
+__global__ void k_finalize_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems);
 
 }  // namespace sst

@@ -10,7 +10,7 @@
 namespace sst {
 
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
-       KIND_COUNT = 6 };
+       KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_COUNT = 10 };
 
 struct KernelTable {
     int nf;
@@ -26,6 +26,9 @@ struct KernelTable {
                            void *out1, int grid, size_t smem, cudaStream_t st);
     // kind: KIND_INV (window L <= nf/2 + 1) or KIND_INV_WIDE (L <= nf + 1)
     cudaError_t (*inverse)(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st);
+    // batched kernels over a work-item table (kind: KIND_B_*)
+    cudaError_t (*batch)(int kind, const BatchChan *ch, const BatchItem *items, int nitems, int max_nbo, int grid,
+                         size_t smem, float *partial, cudaStream_t st);
 };
 
 const KernelTable *table_for_nf(int nf);

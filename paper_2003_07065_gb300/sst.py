@@ -32,6 +32,13 @@ class sst_params(ctypes.Structure):
                 ("z", ctypes.c_int32), ("gamma", ctypes.c_double), ("flags", ctypes.c_uint32)]
 
 
+class sst_batch_item(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("x", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("tfr", ctypes.c_void_p), ("xhat", ctypes.c_void_p)]
+
+
+SST_BATCH_GRAPH = 0x1
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -64,6 +71,19 @@ def load():
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
+                              ctypes.POINTER(_vp)], ctypes.c_int),
+        "sst_batch_workspace": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sst_batch_run": ([_vp, _vp, _vp], ctypes.c_int),
+        "sst_batch_tune": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sst_batch_knobs": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "sst_batch_destroy": ([_vp], None),
+        "sst_batch_submit": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, _vp, ctypes.c_size_t, _vp],
+                             ctypes.c_int),
+        "sst_batch_workspace_for": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "sst_sync": ([_vp], ctypes.c_int),
         "sst_launch_count": ([], ctypes.c_uint64),
         "sst_profile_enable": ([ctypes.c_int], ctypes.c_int),
@@ -177,6 +197,61 @@ def sst_max_abs_v(plan, x, n, maxv, workspace, stream=None):
 
 def sst_forward_static(plan, x, n, tfr, stream=None):
     _check(load().sst_forward_static(plan, _ptr(x), n, _ptr(tfr), _stream(stream)))
+
+
+def _items(items):
+    arr = (sst_batch_item * len(items))()
+    for i, (plan, x, n, tfr, xhat) in enumerate(items):
+        arr[i].plan, arr[i].x, arr[i].n = plan, _ptr(x), int(n)
+        arr[i].tfr, arr[i].xhat = _ptr(tfr), _ptr(xhat)
+    return arr
+
+
+def sst_batch_create(items, graph: bool = False) -> int:
+    """items: sequence of (plan handle, x, n, tfr, xhat); returns a batch handle."""
+    arr = _items(items)
+    out = _vp()
+    _check(load().sst_batch_create(arr, len(items), SST_BATCH_GRAPH if graph else 0, ctypes.byref(out)))
+    return out.value
+
+
+def sst_batch_workspace(batch) -> int:
+    b = ctypes.c_size_t()
+    _check(load().sst_batch_workspace(batch, ctypes.byref(b)))
+    return b.value
+
+
+def sst_batch_run(batch, workspace, stream=None):
+    _check(load().sst_batch_run(batch, _ptr(workspace), _stream(stream)))
+
+
+def sst_batch_tune(batch, workspace, stream=None):
+    """Returns (untuned ms, tuned ms) per batch run."""
+    u, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().sst_batch_tune(batch, _ptr(workspace), _stream(stream), ctypes.byref(u), ctypes.byref(t)))
+    return u.value, t.value
+
+
+def sst_batch_knobs(batch) -> dict:
+    a, b_, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().sst_batch_knobs(batch, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)))
+    return {"fwd_frames": a.value, "abs_quads": b_.value, "grid_mul": c.value}
+
+
+def sst_batch_destroy(batch):
+    load().sst_batch_destroy(batch)
+
+
+def sst_batch_submit(items, workspace, workspace_bytes, stream=None):
+    arr = _items(items)
+    _check(load().sst_batch_submit(arr, len(items), _ptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def sst_batch_workspace_for(items) -> int:
+    arr = _items(items)
+    b = ctypes.c_size_t()
+    _check(load().sst_batch_workspace_for(arr, len(items), ctypes.byref(b)))
+    return b.value
 
 
 def sst_sync(stream=None):

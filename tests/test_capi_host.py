@@ -88,3 +88,21 @@ def test_null_arguments(lib):
     assert L.sst_forward(None, None, 0, None, None, None) == 1
     assert L.sst_plan_query(None, None, None, None, None, None) == 1
     L.sst_plan_destroy(None)
+
+
+def test_host_calls_return_promptly(lib):
+    """Entry points that fail validation or find no device return at once
+    (a regression guard for host-side loops: runs in a child with a timeout)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2003_07065_gb300 import sst as S\n"
+            "L = S.load()\n"
+            "print(L.sst_launch_count())\n"
+            "for _ in range(3):\n"
+            "    try:\n"
+            "        S.sst_plan_create(n=1000, fs=1000.0, L=65, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)\n"
+            "    except S.SstError as e:\n"
+            "        print(e.status)\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
