@@ -118,6 +118,7 @@ struct sst_batch {
     std::vector<cudaEvent_t> ev;     // fork / join events
     cudaGraphExec_t gexec = nullptr;
     void *graph_ws = nullptr;
+    int graph_kernels = 0;           // kernels per graph replay
     Knobs knobs;
     std::string signature;
 };
@@ -349,8 +350,12 @@ sst_status run(sst_batch *b, void *ws, cudaStream_t st) {
             return cuda_fail(e, "graph instantiate");
         }
         b->graph_ws = ws;
+        b->graph_kernels = 0;
+        for (auto &g : b->groups) b->graph_kernels += 1;
+        b->graph_kernels += 2;   // per-channel thresholds and finalize
     }
     SST_CU(cudaGraphLaunch(b->gexec, st), "graph launch");
+    for (int k = 0; k < b->graph_kernels; ++k) count_launch();
     return SST_OK;
 }
 

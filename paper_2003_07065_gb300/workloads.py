@@ -69,3 +69,29 @@ PRECISION_64K = Workload("precision_64k", 65536, 25600.0, 2049, 256.0, 16, 4096,
                          1e-3, True, "chirp_fm")
 
 ALL = {w.name: w for w in (CHIRP_FM_64K, RUNUP_16M, RUNUP_256K, RUNUP_4M, PRECISION_64K)}
+
+
+def batch_channels(count: int = 256, log2_min: float = 14.0, log2_max: float = 22.0, seed: int = 4):
+    """Mixed multi-channel batch: per channel a length log-uniform in
+    [2^log2_min, 2^log2_max], hop in {8, 16, 32, 64}, Nf in {512 .. 8192},
+    L = Nf/2 + 1, sigma = (L - 1)/8, fs = 25.6 kHz, a band of 10-50 % of
+    Nyquist at a uniform start, z in {1, 2, 4}, gamma = 1e-3 max|V|, and a
+    seeded random mix of 1-4 chirp / FM components plus 0-20 dB noise.
+
+    Returns a list of (params dict, noisy float32 signal)."""
+    out = []
+    fs = 25600.0
+    for i in range(count):
+        gen = signals.rng(seed, i)
+        n = int(round(2.0 ** gen.uniform(log2_min, log2_max)))
+        hop = int(gen.choice([8, 16, 32, 64]))
+        nfft = int(gen.choice([512, 1024, 2048, 4096, 8192]))
+        L = nfft // 2 + 1
+        width = float(gen.uniform(0.1, 0.5)) * fs / 2
+        f_lo = float(gen.uniform(0.0, fs / 2 - width))
+        z = int(gen.choice([1, 2, 4]))
+        noisy, _ = signals.random_mix(n, fs, f_lo, f_lo + width, gen)
+        params = dict(n=n, fs=fs, L=L, sigma=(L - 1) / 8.0, hop=hop, nfft=nfft, f_lo=f_lo,
+                      f_hi=f_lo + width, z=z, gamma=1e-3, relative=True)
+        out.append((params, noisy.astype(np.float32)))
+    return out
