@@ -285,7 +285,7 @@ sst_status bind(sst_batch *b, void *ws, cudaStream_t st) {
 
 // Enqueue one phase: the groups of `kind` (a predicate) on forked streams.
 template <class Pred>
-sst_status enqueue_phase(sst_batch *b, cudaStream_t st, float *part, Pred pred) {
+sst_status enqueue_phase(sst_batch *b, cudaStream_t st, float *part, bool count, Pred pred) {
     std::vector<Group *> gs;
     for (auto &g : b->groups)
         if (pred(g.kind)) gs.push_back(&g);
@@ -299,7 +299,7 @@ sst_status enqueue_phase(sst_batch *b, cudaStream_t st, float *part, Pred pred) 
         cudaError_t e = g.kt->batch(g.kind, b->d_ch, g.d_items, (int)g.items.size(), g.max_nbo, g.grid, g.smem,
                                     part + g.part_off, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-        count_launch();
+        if (count) count_launch();
     }
     // join
     for (size_t i = 1; i < gs.size(); ++i) {
@@ -309,33 +309,34 @@ sst_status enqueue_phase(sst_batch *b, cudaStream_t st, float *part, Pred pred) 
     return SST_OK;
 }
 
-sst_status enqueue_all(sst_batch *b, void *ws, cudaStream_t st) {
+// count = false while capturing a graph: the replays are counted instead
+sst_status enqueue_all(sst_batch *b, void *ws, cudaStream_t st, bool count) {
     float *part = (float *)((char *)ws + b->off_part);
-    sst_status s = enqueue_phase(b, st, part, [](int k) { return k == KIND_B_ABSMAX; });
+    sst_status s = enqueue_phase(b, st, part, count, [](int k) { return k == KIND_B_ABSMAX; });
     if (s != SST_OK) return s;
     k_gamma_batch<<<(unsigned)b->ch.size(), 256, 0, st>>>(b->d_ch, (int)b->ch.size(), part);
     SST_CU(cudaGetLastError(), "batch gamma launch");
-    count_launch();
-    s = enqueue_phase(b, st, part, [](int k) { return k == KIND_B_FWD; });
+    if (count) count_launch();
+    s = enqueue_phase(b, st, part, count, [](int k) { return k == KIND_B_FWD; });
     if (s != SST_OK) return s;
-    s = enqueue_phase(b, st, part, [](int k) { return k == KIND_B_INV || k == KIND_B_INV_WIDE; });
+    s = enqueue_phase(b, st, part, count, [](int k) { return k == KIND_B_INV || k == KIND_B_INV_WIDE; });
     if (s != SST_OK) return s;
     const int grid = (int)std::min<size_t>(std::max<size_t>(b->fin.size(), 1), (size_t)b->nsm * 8);
     k_finalize_batch<<<grid, 256, 0, st>>>(b->d_ch, b->d_fin, (int)b->fin.size());
     SST_CU(cudaGetLastError(), "batch finalize launch");
-    count_launch();
+    if (count) count_launch();
     return SST_OK;
 }
 
 sst_status run(sst_batch *b, void *ws, cudaStream_t st) {
     sst_status s = bind(b, ws, st);
     if (s != SST_OK) return s;
-    if (!(b->flags & SST_BATCH_GRAPH)) return enqueue_all(b, ws, st);
+    if (!(b->flags & SST_BATCH_GRAPH)) return enqueue_all(b, ws, st, true);
     if (!b->gexec || b->graph_ws != ws) {
         drop_graph(b);
         // capture on the batch's own stream; the graph is launched on the caller's
         SST_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "graph capture begin");
-        s = enqueue_all(b, ws, b->cap);
+        s = enqueue_all(b, ws, b->cap, false);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
         if (s != SST_OK) {
