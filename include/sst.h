@@ -206,6 +206,47 @@ sst_status sst_batch_submit(const sst_batch_item *items, int32_t count, void *wo
 /* Workspace bytes sst_batch_submit needs for these items. */
 sst_status sst_batch_workspace_for(const sst_batch_item *items, int32_t count, size_t *bytes);
 
+/* ---- Streaming service (continuous batching of many live streams).
+ * Streams push chunks of samples; each sst_service_tick moves every stream's
+ * pending chunks to the device and runs, for all streams together, the
+ * frames whose window has fully arrived, the inverse tiles (16 frames) whose
+ * frames are all transformed, and the output samples no later frame touches.
+ * Per-stream state (signal tail, TFR rows and overlap-add tiles not yet
+ * consumed, cursors) stays on the device.  A stream's results do not depend
+ * on its chunking or on the other streams; after sst_stream_close and the
+ * ticks that flush it, they equal the whole-signal transform of the
+ * concatenated chunks (absolute threshold).  Streams are admitted while their
+ * device state fits the service's memory budget. */
+typedef struct sst_service *sst_service_t;
+sst_status sst_service_create(int32_t max_streams, size_t mem_budget_bytes, sst_service_t *out);
+/* Open a stream.  params->n is ignored; the threshold must be absolute
+ * (SST_EUNSUPPORTED otherwise: the whole-signal maximum is unknown while
+ * streaming).  amp_bound >= max |x| of the stream fixes the exact-sum scale;
+ * max_chunk bounds one push.  SST_EBUSY when no slot or budget is left. */
+sst_status sst_stream_open(sst_service_t svc, const sst_params *params, float amp_bound, int64_t max_chunk,
+                           int32_t *stream_id);
+/* Queue a host chunk (copied).  t_arrival: seconds on CLOCK_MONOTONIC (e.g.
+ * Python time.monotonic()), or negative for "now"; latency = completion of
+ * the tick that consumed the chunk minus t_arrival.  SST_EBUSY if more than
+ * 8 max_chunk samples are queued. */
+sst_status sst_stream_push(sst_service_t svc, int32_t stream_id, const float *host_chunk, int64_t n, double t_arrival);
+/* End of data: later ticks flush the last frames (zero padding after the end). */
+sst_status sst_stream_close(sst_service_t svc, int32_t stream_id);
+/* Process everything ready on every stream; synchronous. */
+sst_status sst_service_tick(sst_service_t svc);
+/* Take finished output: up to max_cols TFR columns (bins complex each) and
+ * up to max_samples reconstructed samples, with the index of the first of
+ * each; *finished = 1 once a closed stream has delivered everything. */
+sst_status sst_stream_poll(sst_service_t svc, int32_t stream_id, float *tfr_host, int64_t max_cols, int64_t *cols,
+                           int64_t *first_col, float *xhat_host, int64_t max_samples, int64_t *samples,
+                           int64_t *first_sample, int32_t *finished);
+/* Free a stream's slot and device state. */
+sst_status sst_stream_release(sst_service_t svc, int32_t stream_id);
+/* Latency quantiles (seconds) over the chunks consumed so far; reset != 0 clears them. */
+sst_status sst_service_latency(sst_service_t svc, double *p50, double *p99, int64_t *count, int32_t reset);
+sst_status sst_service_memory(sst_service_t svc, size_t *used_bytes, size_t *budget_bytes);
+void sst_service_destroy(sst_service_t svc);
+
 /* Block until `stream` is idle; returns SST_ECUDA with the message of any
  * pending asynchronous error. */
 sst_status sst_sync(void *stream);

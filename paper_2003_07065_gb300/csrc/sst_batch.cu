@@ -62,7 +62,8 @@ __global__ void k_finalize_batch(const BatchChan *__restrict__ ch, const BatchIt
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
         const BatchChan &c = ch[w.chan];
-        for (int64_t p = w.begin + threadIdx.x; p < w.end; p += blockDim.x) c.xhat[p] = finalize_value(c.d, c.ola, p);
+        for (int64_t p = w.begin + threadIdx.x; p < w.end; p += blockDim.x)
+            c.xhat[p - c.poff] = finalize_value(c.d, c.ola, p);
     }
 }
 
@@ -226,7 +227,7 @@ sst_status build_items(sst_batch *b) {
         for (int64_t p = 0; p < b->ch[c].d.n; p += 65536) b->fin.push_back({c, 0, p, std::min(b->ch[c].d.n, p + 65536)});
     // shapes, uploads
     for (auto &g : b->groups) {
-        cudaError_t e = g.kt->set_smem(g.kind, g.smem);
+        cudaError_t e = raise_smem(g.kt, g.kind, g.smem);
         if (e != cudaSuccess) return cuda_fail(e, "batch cudaFuncSetAttribute");
         int occ = 1;
         if (g.kt->occupancy(g.kind, g.smem, &occ) != cudaSuccess || occ < 1) occ = 1;

@@ -2,6 +2,7 @@
 // validation, workspace layout and the launch sequences of each entry point.
 #include <atomic>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <cstdarg>
 #include <cstdio>
@@ -125,6 +126,18 @@ sst_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, int>, size_t> g_smem_set;
+
+cudaError_t raise_smem(const KernelTable *kt, int kind, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    size_t &cur = g_smem_set[{kt->nf, kind}];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = kt->set_smem(kind, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 // ------------------------------------------------------------ profiling
 static const char *kPkNames[SST_PROFILE_KINDS] = {"absmax", "gamma", "forward", "stft", "map", "inverse",
@@ -372,7 +385,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {KIND_FWD_T, pl->smem_fwd_t},
         {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {pl->inv_kind, pl->smem_inv}};
     for (auto &k : kinds) {
-        ce = kt->set_smem(k.kind, k.bytes);
+        ce = raise_smem(kt, k.kind, k.bytes);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
     }
     auto grid_for = [&](int kind, size_t bytes, int64_t units) {

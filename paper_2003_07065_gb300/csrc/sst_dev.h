@@ -30,7 +30,18 @@ struct SstDev {
     int B;              // frames per inverse tile (even)
     int seg_len;        // (B - 1) hop + L
     int64_t ntiles;
+    // buffer placement (all zero for a whole-signal call); used by streams:
+    int64_t xoff;       // the x pointer holds samples from global index xoff on
+    int trow_cap;       // T row of frame m is m % trow_cap (ring), or m when 0
+    int tile_cap;       // overlap-add slot of tile t is t % tile_cap, or t when 0
 };
+
+__host__ __device__ __forceinline__ int64_t trow_of(const SstDev &d, int64_t m) {
+    return d.trow_cap ? m % d.trow_cap : m;
+}
+__host__ __device__ __forceinline__ int64_t tslot_of(const SstDev &d, int64_t t) {
+    return d.tile_cap ? t % d.tile_cap : t;
+}
 
 // Per-call scalars produced on the device before the forward kernel runs
 // (at the start of the workspace, or of the static scratch array).
@@ -55,6 +66,7 @@ struct BatchChan {
     float sum_abs_g;   // |S^g| <= max|x| sum|g| (absolute-threshold channels)
     int part0;         // first pre-pass partial of this channel
     int nparts;        // number of pre-pass partials of this channel
+    int64_t poff;      // xhat holds samples from global index poff on (streams)
 };
 
 // A unit of batched work: channel `chan`, units [begin, end) -- quads of

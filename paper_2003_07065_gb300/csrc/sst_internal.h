@@ -18,6 +18,9 @@ namespace sst {
 sst_status fail(sst_status s, const char *fmt, ...);
 sst_status cuda_fail(cudaError_t e, const char *what);
 void count_launch();
+// raise (never lower) a kernel's dynamic shared-memory limit, so plans,
+// batches and streams with different needs can share the kernels
+cudaError_t raise_smem(const KernelTable *kt, int kind, size_t bytes);
 
 #define SST_CU(call, what)                                      \
     do {                                                        \

@@ -57,13 +57,13 @@ __device__ __forceinline__ float2 frame_sample(const SstDev &d, const float *__r
     for (int j = jmin; j <= d.M; j += NF) {
         const float2 w = __ldg(&d.win[j + d.M]);
         const int64_t s1 = c1 + j;
-        const float x1 = (s1 >= 0 && s1 < d.n) ? __ldg(&x[s1]) : 0.f;
+        const float x1 = (s1 >= 0 && s1 < d.n) ? __ldg(&x[s1 - d.xoff]) : 0.f;
         if (!PAIR) {
             acc.x = fmaf(x1, w.x, acc.x);
             acc.y = fmaf(x1, w.y, acc.y);
         } else {
             const int64_t s2 = c2 + j;
-            const float x2 = (has2 && s2 >= 0 && s2 < d.n) ? __ldg(&x[s2]) : 0.f;
+            const float x2 = (has2 && s2 >= 0 && s2 < d.n) ? __ldg(&x[s2 - d.xoff]) : 0.f;
             acc.x = fmaf(x1, w.x, acc.x);
             acc.y = fmaf(x2, w.x, acc.y);
         }
@@ -83,8 +83,8 @@ __device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>:
     const bool in1 = c1 - d.M >= 0 && c1 + d.M < d.n;
     const bool in2 = !PAIR || (has2 && c2 - d.M >= 0 && c2 + d.M < d.n);
     if (in1 && in2 && d.L <= NF) {
-        const float *x1 = x + c1;
-        const float *x2 = x + (PAIR ? c2 : c1);
+        const float *x1 = x + (c1 - d.xoff);
+        const float *x2 = x + ((PAIR ? c2 : c1) - d.xoff);
         const float2 *w = d.win + d.M;
 #pragma unroll
         for (int b = 0; b < C::PER1; ++b) {
@@ -307,7 +307,7 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     // frame's first pass overwrites buf
     __syncthreads();
     if (MODE != MODE_T) return;
-    float2 *Trow = out0 + (size_t)m * d.nbo;
+    float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
     for (int l = tid; l < d.nbo; l += TPF) {
         const long long ar = (long long)acc_re[l], ai = (long long)acc_im[l];
         Trow[l] = make_float2((__ll2float_rn(ar) * fs.r1) * fs.r2, (__ll2float_rn(ai) * fs.r1) * fs.r2);
@@ -404,7 +404,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
         // stage both rows (contiguous in T), regrouped by sub-grid, with the
         // 1/2 weight of the DC and Nyquist destinations (Hermitian completion)
         for (int f = 0; f < 2; ++f) {
-            const float2 *src = T + (size_t)(a + f) * d.nbo;
+            const float2 *src = T + (size_t)trow_of(d, a + f) * d.nbo;
             const bool have = f == 0 || hasb;
             for (int q = tid; q < nq; q += TPF) {
                 const int k = d.k_lo + q;
@@ -496,7 +496,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
         }
         __syncthreads();
     }
-    float *out = partial + (size_t)tile * d.seg_len;
+    float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
     for (int i = tid; i < d.seg_len; i += TPF) out[i] = seg[i];
 }
 
@@ -523,7 +523,7 @@ __device__ __forceinline__ float finalize_value(const SstDev &d, const float *__
     int64_t thi = (p + d.M) / BH;
     if (thi > d.ntiles - 1) thi = d.ntiles - 1;
     float s = 0.f;
-    for (int64_t t = tlo; t <= thi; ++t) s += partial[t * d.seg_len + (p + d.M - t * BH)];
+    for (int64_t t = tlo; t <= thi; ++t) s += partial[tslot_of(d, t) * d.seg_len + (p + d.M - t * BH)];
     return s * recip_norm(d, p);
 }
 

@@ -84,6 +84,21 @@ def load():
                              ctypes.c_int),
         "sst_batch_workspace_for": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sst_service_create": ([ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(_vp)], ctypes.c_int),
+        "sst_stream_open": ([_vp, ctypes.POINTER(sst_params), ctypes.c_float, _i64,
+                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "sst_stream_push": ([_vp, ctypes.c_int32, _vp, _i64, ctypes.c_double], ctypes.c_int),
+        "sst_stream_close": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sst_service_tick": ([_vp], ctypes.c_int),
+        "sst_stream_poll": ([_vp, ctypes.c_int32, _vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp,
+                             _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32)],
+                            ctypes.c_int),
+        "sst_stream_release": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sst_service_latency": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(_i64), ctypes.c_int32], ctypes.c_int),
+        "sst_service_memory": ([_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+                               ctypes.c_int),
+        "sst_service_destroy": ([_vp], None),
         "sst_sync": ([_vp], ctypes.c_int),
         "sst_launch_count": ([], ctypes.c_uint64),
         "sst_profile_enable": ([ctypes.c_int], ctypes.c_int),
@@ -124,11 +139,7 @@ def _stream(stream) -> int | None:
 
 
 # ------------------------------------------------------------------ C names
-def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
-                    z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
-                    g=None, dg=None) -> int:
-    """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows."""
-    lib = load()
+def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg):
     p = sst_params()
     p.n, p.fs, p.L = int(n), float(fs), int(L)
     p.sigma = float(sigma) if sigma is not None else 0.0
@@ -144,6 +155,15 @@ def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float,
     p.f_lo, p.f_hi, p.z = float(f_lo), float(f_hi), int(z)
     p.gamma = float(gamma)
     p.flags = SST_GAMMA_RELATIVE if relative else 0
+    return p, keep
+
+
+def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
+                    z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
+                    g=None, dg=None) -> int:
+    """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows."""
+    lib = load()
+    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg)
     out = _vp()
     _check(lib.sst_plan_create(ctypes.byref(p), ctypes.byref(out)))
     del keep
@@ -252,6 +272,72 @@ def sst_batch_workspace_for(items) -> int:
     b = ctypes.c_size_t()
     _check(load().sst_batch_workspace_for(arr, len(items), ctypes.byref(b)))
     return b.value
+
+
+def sst_service_create(max_streams: int, mem_budget: int) -> int:
+    out = _vp()
+    _check(load().sst_service_create(int(max_streams), int(mem_budget), ctypes.byref(out)))
+    return out.value
+
+
+def sst_stream_open(svc, amp_bound: float, max_chunk: int, fs: float, L: int, hop: int, nfft: int,
+                    f_lo: float, f_hi: float, z: int = 1, gamma: float = 0.0, sigma: float | None = None,
+                    g=None, dg=None) -> int:
+    """Open a stream (absolute threshold gamma); returns its id."""
+    p, keep = _params(0, fs, L, hop, nfft, f_lo, f_hi, z, gamma, False, sigma, g, dg)
+    sid = ctypes.c_int32()
+    _check(load().sst_stream_open(svc, ctypes.byref(p), float(amp_bound), int(max_chunk), ctypes.byref(sid)))
+    del keep
+    return sid.value
+
+
+def sst_stream_push(svc, sid: int, chunk, t_arrival: float = -1.0):
+    import numpy as np
+    a = np.ascontiguousarray(chunk, dtype=np.float32)
+    _check(load().sst_stream_push(svc, int(sid), a.ctypes.data, len(a), float(t_arrival)))
+
+
+def sst_stream_close(svc, sid: int):
+    _check(load().sst_stream_close(svc, int(sid)))
+
+
+def sst_service_tick(svc):
+    _check(load().sst_service_tick(svc))
+
+
+def sst_stream_poll(svc, sid: int, bins: int, max_cols: int = 4096, max_samples: int = 1 << 17):
+    """Returns (tfr [cols, bins] complex64, first_col, xhat float32, first_sample, finished)."""
+    import numpy as np
+    t = np.empty((max_cols, bins, 2), dtype=np.float32)
+    x = np.empty(max_samples, dtype=np.float32)
+    cols, fc, ns, fs_, fin = _i64(), _i64(), _i64(), _i64(), ctypes.c_int32()
+    _check(load().sst_stream_poll(svc, int(sid), t.ctypes.data, max_cols, ctypes.byref(cols), ctypes.byref(fc),
+                                  x.ctypes.data, max_samples, ctypes.byref(ns), ctypes.byref(fs_),
+                                  ctypes.byref(fin)))
+    tc = t[:cols.value]
+    return (tc[..., 0] + 1j * tc[..., 1]).astype(np.complex64), fc.value, x[:ns.value].copy(), fs_.value, \
+        bool(fin.value)
+
+
+def sst_stream_release(svc, sid: int):
+    _check(load().sst_stream_release(svc, int(sid)))
+
+
+def sst_service_latency(svc, reset: bool = False):
+    """Returns (p50 s, p99 s, chunks)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), _i64()
+    _check(load().sst_service_latency(svc, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), 1 if reset else 0))
+    return a.value, b.value, c.value
+
+
+def sst_service_memory(svc):
+    u, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().sst_service_memory(svc, ctypes.byref(u), ctypes.byref(b)))
+    return u.value, b.value
+
+
+def sst_service_destroy(svc):
+    load().sst_service_destroy(svc)
 
 
 def sst_sync(stream=None):
