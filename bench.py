@@ -246,6 +246,123 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ streaming workload
+def run_stream(args):
+    """64 sensor streams at 25.6 kHz pushing 8192-sample chunks with Poisson
+    arrivals (2 chunks/s per stream; bursts of 1 s at 5x the rate starting as
+    a 0.1/s Poisson process), served in real time for --seconds: p50/p99
+    latency (tick completion minus scheduled arrival).  Then an overload phase
+    (every stream's queue kept full) gives the sustained samples/s."""
+    import torch
+    from paper_2003_07065_gb300 import build, sst, signals
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    sst.load()
+    nstreams, fs, chunk = 64, 25600.0, 8192
+    P = dict(fs=fs, L=1025, sigma=128.0, hop=16, nfft=2048, f_lo=0.0, f_hi=8000.0, z=2)
+    dur = args.seconds
+    # arrival schedules
+    sched = []
+    for i in range(nstreams):
+        gen = signals.rng(5, i)
+        bursts = []
+        t = 0.0
+        while t < dur:
+            t += gen.exponential(1 / 0.1)
+            bursts.append((t, t + 1.0))
+        arr, t = [], 0.0
+        while t < dur:
+            rate = 2.0 * (5.0 if any(a <= t < b for a, b in bursts) else 1.0)
+            t += gen.exponential(1 / rate)
+            if t < dur:
+                arr.append(t)
+        sched.append(arr)
+    need = max(len(a) for a in sched) * chunk + 64 * chunk
+    sigs, gammas = [], []
+    for i in range(nstreams):
+        x, _ = signals.chirp_fm_mix(need, fs, 10.0, seed=(5, 1000 + i))
+        sigs.append(x.astype(np.float32))
+    # per-stream absolute threshold: 1e-3 of the stream's whole-signal max |V| (product path)
+    for i in range(nstreams):
+        pl = sst.Plan(n=len(sigs[i]), gamma=1e-3, relative=True, **P)
+        gammas.append(1e-3 * float(pl.max_abs_v(torch.from_numpy(sigs[i]).cuda()).item()))
+        pl.close()
+    nb = P["z"] * int(math.floor(P["f_hi"] * P["nfft"] / fs + 0.5)) + 1
+    svc = sst.sst_service_create(nstreams, 64 << 30)
+    ids = [sst.sst_stream_open(svc, 8.0, chunk, gamma=gammas[i], **P) for i in range(nstreams)]
+    l0 = sst.sst_launch_count()
+    # real-time phase
+    events = sorted((t, i) for i, a in enumerate(sched) for t in a)
+    pos = [0] * nstreams
+    t0 = time.monotonic()
+    k = 0
+    pushed = dropped = ticks = 0
+    while True:
+        now = time.monotonic() - t0
+        if now >= dur and k >= len(events):
+            break
+        while k < len(events) and events[k][0] <= now:
+            ta, i = events[k]
+            try:
+                sst.sst_stream_push(svc, ids[i], sigs[i][pos[i]:pos[i] + chunk], t0 + ta)
+                pos[i] += chunk
+                pushed += chunk
+            except sst.SstError:
+                dropped += 1
+            k += 1
+        sst.sst_service_tick(svc)
+        ticks += 1
+        for i in range(nstreams):
+            while True:
+                t, _, x, _, _ = sst.sst_stream_poll(svc, ids[i], nb)
+                if not len(t) and not len(x):
+                    break
+        if k < len(events):
+            wait = events[k][0] - (time.monotonic() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.002))
+    wall = time.monotonic() - t0
+    p50, p99, nlat = sst.sst_service_latency(svc, reset=True)
+    # overload phase: keep every queue full for ~3 s
+    t1 = time.monotonic()
+    processed = 0
+    while time.monotonic() - t1 < 3.0:
+        for i in range(nstreams):
+            for _ in range(4):
+                if pos[i] + chunk > len(sigs[i]):
+                    pos[i] = 0
+                try:
+                    sst.sst_stream_push(svc, ids[i], sigs[i][pos[i]:pos[i] + chunk])
+                    pos[i] += chunk
+                    processed += chunk
+                except sst.SstError:
+                    break
+        sst.sst_service_tick(svc)
+        for i in range(nstreams):
+            while True:
+                t, _, x, _, _ = sst.sst_stream_poll(svc, ids[i], nb)
+                if not len(t) and not len(x):
+                    break
+    sustained = processed / (time.monotonic() - t1)
+    o50, o99, _ = sst.sst_service_latency(svc, reset=True)
+    launches = sst.sst_launch_count() - l0
+    sst.sst_service_destroy(svc)
+    line = {
+        "metric": "p50/p99 stream latency; sustained input samples/s", "value": sustained, "unit": "samples/s",
+        "n_gpus": 1, "steps": ticks, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "stream64", "streams": nstreams, "chunk": chunk, "fs": fs, "hop": 16, "nfft": 2048,
+                   "L": 1025, "band_hz": [0.0, 8000.0], "z": 2, "arrivals": "Poisson 2/s, 1 s bursts x5 at 0.1/s",
+                   "seconds": dur},
+        "latency_s": {"p50": p50, "p99": p99, "chunks": nlat, "offered_samples_per_s": pushed / wall,
+                      "dropped_chunks": dropped, "ticks": ticks},
+        "overload_latency_s": {"p50": o50, "p99": o99},
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -253,11 +370,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="runup_16m", choices=sorted(W.ALL) + ["batch256"])
+    ap.add_argument("--workload", default="runup_16m", choices=sorted(W.ALL) + ["batch256", "stream64"])
+    ap.add_argument("--seconds", type=float, default=12.0, help="stream64: simulated real-time seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch256":
         return run_batch(args)
+    if args.workload == "stream64":
+        return run_stream(args)
     w = W.ALL[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
