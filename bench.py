@@ -129,6 +129,26 @@ def measured_peaks() -> dict:
     return {}
 
 
+def measured_traffic_per_frame(kernel: str):
+    """DRAM bytes per frame of `kernel` from the committed ncu capture
+    (profiles/dram_traffic_runup.json), or None when the kernel sources have
+    changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic_runup.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2003_07065_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("kernel_source_sha256"):
+        return None
+    return rec["dram_bytes_per_frame"].get(kernel)
+
+
 def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
     """FP32 ALU peak: 128 FP32 lanes per SM, one FMA (2 FLOPs) per lane per
     clock."""
@@ -487,8 +507,10 @@ def main():
         achieved = flops / (per_launch_ms / 1e3) / 1e12
         sm_max = peaks.get("sm_max_mhz") or 2070.0
         peak = fp32_peak_tflops(num_sms, sm_max)
+        tpf = measured_traffic_per_frame(dom)
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": (tpf * units if tpf is not None else None),
+                "traffic_note": "ncu dram__bytes_read+write of one runup_4m launch scaled by frames",
                 "peak_note": f"FP32 FMA peak {num_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max clock)",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
                 "hbm_gbs_achieved": by[dom] * units / (per_launch_ms / 1e3) / 1e9,
