@@ -39,12 +39,8 @@ const KernelTable *table_for_nf(int nf) {
 }
 
 // ------------------------------------------------------------ small kernels
-// Reduce the pre-pass partials.  Relative plans (from_x = 0): the partials are
-// max |S^g|^2 per CTA; gamma^2 = frac^2 max, maxv = sqrt(max).  Absolute plans
-// (from_x = 1): the partials are max |x| per CTA and |S^g| <= max|x| sum|g|.
-// Either way the bound B on |S^g| (0.1% margin for the forward kernel's own
-// rounding) gives the fixed-point scale 2^e, e = 61 - ceil(log2 B) -
-// ceil(log2 nb): a frame's at most nb terms then sum below 2^62 in int64.
+// Reduce the pre-pass partials (max |S^g|^2 per CTA for relative plans, max
+// |x| per CTA for absolute ones) into the call's scalars (scalars_from_max).
 __global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
                         int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out) {
     __shared__ float red[32];
@@ -57,27 +53,8 @@ __global__ void k_gamma(const float *__restrict__ partial, int count, float frac
     if (threadIdx.x == 0) {
         float r = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
-        float bound;
-        if (!from_x) {
-            const float mv = sqrtf(r);
-            sc->gamma2 = frac2 * r;
-            sc->maxv = mv;
-            if (maxv_out) *maxv_out = mv;
-            bound = mv * 1.001f;
-        } else {
-            bound = r * bound_mul;
-        }
-        int e = 0;
-        if (bound > 0.f && bound < 3.0e38f) {
-            int ex;
-            frexpf(bound, &ex);  // bound < 2^ex
-            e = 61 - ex - log2_nb;
-        }
-        const int e1 = e / 2, e2 = e - e / 2;
-        sc->s1 = ldexpf(1.f, e1);
-        sc->s2 = ldexpf(1.f, e2);
-        sc->r1 = ldexpf(1.f, -e1);
-        sc->r2 = ldexpf(1.f, -e2);
+        *sc = scalars_from_max(r, frac2, from_x, bound_mul, log2_nb);
+        if (maxv_out && !from_x) *maxv_out = sc->maxv;
     }
 }
 
@@ -267,6 +244,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     std::vector<float2> win(L);
     std::vector<float> gf(L);
     for (int i = 0; i < L; ++i) { win[i] = make_float2((float)g[i], (float)(dg[i] * dsc)); gf[i] = (float)g[i]; }
+    pl->g64 = g;
+    pl->dgs64.resize(L);
+    for (int i = 0; i < L; ++i) pl->dgs64[i] = dg[i] * dsc;
     // Stockham twiddles, per radix-16 pass of span Ns (Ns = R1, 16 R1, ..., nf/16): rows
     // m = 1, 2, 4, 8 of exp(-2 pi i m k / (16 Ns)), k in [0, Ns), from entry 4 (Ns - R1) / 15
     int lg2 = 0;

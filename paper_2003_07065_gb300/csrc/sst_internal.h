@@ -81,4 +81,5 @@ struct sst_plan {
     int inv_kind = sst::KIND_INV;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
     size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
+    std::vector<double> g64, dgs64;   // FP64 window g and s g' (basis of the tensor form)
 };

@@ -215,6 +215,38 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
 
 // Reduce the pre-pass partial maxima into the call's scalars (see k_gamma in
 // sst_capi.cu): threshold, max |S^g| and the fixed-point scale of the T sums.
+// The call's scalars from the pre-pass maximum r.  Relative plans (from_x =
+// 0): r = max |S^g|^2, gamma^2 = frac^2 r, maxv = sqrt(r).  Absolute plans
+// (from_x = 1): r = max |x| and |S^g| <= max|x| sum|g|.  Either way the bound
+// B on |S^g| (0.1% margin for the forward kernel's own rounding) gives the
+// fixed-point scale 2^e, e = 61 - ceil(log2 B) - ceil(log2 nb): a frame's at
+// most nb terms then sum below 2^62 in int64.
+__device__ __forceinline__ SstScalars scalars_from_max(float r, float frac2, int from_x, float bound_mul,
+                                                       int log2_nb) {
+    SstScalars sc = {};
+    float bound;
+    if (!from_x) {
+        const float mv = sqrtf(r);
+        sc.gamma2 = frac2 * r;
+        sc.maxv = mv;
+        bound = mv * 1.001f;
+    } else {
+        bound = r * bound_mul;
+    }
+    int e = 0;
+    if (bound > 0.f && bound < 3.0e38f) {
+        int ex;
+        frexpf(bound, &ex);  // bound < 2^ex
+        e = 61 - ex - log2_nb;
+    }
+    const int e1 = e / 2, e2 = e - e / 2;
+    sc.s1 = ldexpf(1.f, e1);
+    sc.s2 = ldexpf(1.f, e2);
+    sc.r1 = ldexpf(1.f, -e1);
+    sc.r2 = ldexpf(1.f, -e2);
+    return sc;
+}
+
 __global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
                         int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out);
 

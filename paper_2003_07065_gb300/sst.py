@@ -71,6 +71,16 @@ def load():
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_tc_plan_create": ([_vp, ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
+        "sst_tc_plan_destroy": ([_vp], None),
+        "sst_tc_plan_query": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64),
+                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "sst_tc_plan_set_cluster": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sst_tc_forward": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_tc_stft": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_tc_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_tc_contract": ([_vp, _vp, _i64, _vp], ctypes.c_int),
+        "sst_tc_check": ([_vp, _vp], ctypes.c_int),
         "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
                               ctypes.POINTER(_vp)], ctypes.c_int),
         "sst_batch_workspace": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -217,6 +227,50 @@ def sst_max_abs_v(plan, x, n, maxv, workspace, stream=None):
 
 def sst_forward_static(plan, x, n, tfr, stream=None):
     _check(load().sst_forward_static(plan, _ptr(x), n, _ptr(tfr), _stream(stream)))
+
+
+SST_FORM_BF16, SST_FORM_BF16X3, SST_FORM_TF32 = 0, 1, 2
+FORMS = {"bf16": SST_FORM_BF16, "bf16x3": SST_FORM_BF16X3, "tf32": SST_FORM_TF32}
+
+
+def sst_tc_plan_create(plan, form: int) -> int:
+    h = _vp()
+    _check(load().sst_tc_plan_create(plan, form, ctypes.byref(h)))
+    return h.value
+
+
+def sst_tc_plan_destroy(tc) -> None:
+    load().sst_tc_plan_destroy(tc)
+
+
+def sst_tc_plan_query(tc) -> dict:
+    hv, fl, cl = ctypes.c_int32(), _i64(), ctypes.c_int32()
+    _check(load().sst_tc_plan_query(tc, ctypes.byref(hv), ctypes.byref(fl), ctypes.byref(cl)))
+    return {"hankel_view": bool(hv.value), "gemm_flops": fl.value, "cluster": cl.value}
+
+
+def sst_tc_plan_set_cluster(tc, cluster: int) -> None:
+    _check(load().sst_tc_plan_set_cluster(tc, cluster))
+
+
+def sst_tc_forward(tc, x, n, tfr, stream=None):
+    _check(load().sst_tc_forward(tc, _ptr(x), n, _ptr(tfr), _stream(stream)))
+
+
+def sst_tc_stft(tc, x, n, V, Vd, stream=None):
+    _check(load().sst_tc_stft(tc, _ptr(x), n, _ptr(V), _ptr(Vd), _stream(stream)))
+
+
+def sst_tc_reassign_map(tc, x, n, omega, dest, stream=None):
+    _check(load().sst_tc_reassign_map(tc, _ptr(x), n, _ptr(omega), _ptr(dest), _stream(stream)))
+
+
+def sst_tc_contract(tc, x, n, stream=None):
+    _check(load().sst_tc_contract(tc, _ptr(x), n, _stream(stream)))
+
+
+def sst_tc_check(tc, stream=None):
+    _check(load().sst_tc_check(tc, _stream(stream)))
 
 
 def _items(items):
@@ -435,9 +489,43 @@ class Plan:
         return out
 
     def close(self):
+        for tc in getattr(self, "_tc", {}).values():
+            sst_tc_plan_destroy(tc)
+        self._tc = {}
         if self.handle:
             sst_plan_destroy(self.handle)
             self.handle = 0
+
+    # tensor-core band form ("bf16", "bf16x3", "tf32"); the tensor plan is
+    # created on first use and owned by this object
+    def _tc_handle(self, form: str) -> int:
+        if not hasattr(self, "_tc"):
+            self._tc = {}
+        if form not in self._tc:
+            self._tc[form] = sst_tc_plan_create(self.handle, FORMS[form])
+        return self._tc[form]
+
+    def tc_forward(self, x, form: str, tfr=None):
+        tfr = self.new_tfr() if tfr is None else tfr
+        sst_tc_forward(self._tc_handle(form), x, self.n, tfr)
+        sst_tc_check(self._tc_handle(form))
+        return tfr
+
+    def tc_stft(self, x, form: str):
+        import torch
+        V = torch.empty((self.frames, self.nb, 2), dtype=torch.float32, device=self.device)
+        Vd = torch.empty_like(V)
+        sst_tc_stft(self._tc_handle(form), x, self.n, V, Vd)
+        sst_tc_check(self._tc_handle(form))
+        return V, Vd
+
+    def tc_reassign_map(self, x, form: str):
+        import torch
+        om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
+        de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
+        sst_tc_reassign_map(self._tc_handle(form), x, self.n, om, de)
+        sst_tc_check(self._tc_handle(form))
+        return om, de
 
     def __del__(self):
         try:
