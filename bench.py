@@ -33,6 +33,8 @@ from paper_2003_07065_gb300 import workloads as W  # noqa: E402
 METRIC = "input samples/s through SST fwd+inverse"
 UNIT = "samples/s"
 L2_BYTES = 129 * 1024 * 1024
+FALLBACK_BF16_TFLOPS = 1900.0      # used only when MEASURED_PEAKS.json is absent
+TF32_OVER_BF16 = 1.1 / 2.25        # nominal dense TF32 / BF16 tensor rate
 
 
 def flops_per_frame(w) -> dict:
@@ -266,6 +268,108 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ tensor-core band form
+TC_FORMS = ("fft", "bf16", "bf16x3", "tf32")
+
+
+def run_tensor(args):
+    """Precision workload (Nf 4096, L 2049, hop 16, 1025 in-band bins): one
+    step = forward (FFT form, or the tcgen05 contraction in one of its three
+    operand forms) + the shared direct inverse.  Reports every form's time and
+    the reconstruction SNR against the clean signal; the headline is the BF16
+    tensor form.  The roofline is the contraction's, against the measured
+    dense BF16 tensor peak (TF32 at the nominal TF32 / BF16 ratio)."""
+    import torch
+    from paper_2003_07065_gb300 import build, sst
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    sst.load()
+    w = W.PRECISION_64K
+    noisy, clean = w.signal()
+    x = torch.from_numpy(noisy.astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    tfr = plan.new_tfr()
+    xhat = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    bf16_peak = peaks.get("bf16_tflops") or FALLBACK_BF16_TFLOPS
+    forms = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = sst.sst_launch_count()
+    for form in TC_FORMS:
+        info = {}
+        if form == "fft":
+            def fwd():
+                sst.sst_forward(plan.handle, x, w.n, tfr, plan.workspace, stream)
+        else:
+            h = plan._tc_handle(form)
+            cl, _ = sst.sst_tc_plan_tune(h, x, w.n, stream)
+            q = sst.sst_tc_plan_query(h)
+            info.update(cluster=cl, hankel_view=q["hankel_view"], gemm_flops=q["gemm_flops"])
+
+            def fwd(h=h):
+                sst.sst_tc_forward(h, x, w.n, tfr, stream)
+
+        def step():
+            fwd()
+            sst.sst_inverse(plan.handle, tfr, w.n, xhat, plan.workspace, stream)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        sst.sst_profile_enable(True)
+        sst.sst_profile_collect()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        sst.sst_profile_enable(False)
+        prof = sst.sst_profile_collect()
+        if form != "fft":
+            sst.sst_tc_check(plan._tc_handle(form))
+        t_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        xh = xhat.cpu().numpy().astype(np.float64)
+        err = clean - xh
+        info.update(ms_per_step=t_ms, samples_per_s=w.n / (t_ms / 1e3),
+                    snr_db=float(10 * np.log10(np.sum(clean ** 2) / np.sum(err ** 2))),
+                    kernels={k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                             for k, v in prof.items()})
+        if form != "fft":
+            gemm_ms = prof["stft"][0] / args.steps      # the contraction is timed under this kind
+            peak = bf16_peak * (TF32_OVER_BF16 if form == "tf32" else 1.0)
+            info["contraction"] = {"ms": gemm_ms, "tflops": info["gemm_flops"] / gemm_ms / 1e9,
+                                   "peak_tflops": peak, "frac": info["gemm_flops"] / gemm_ms / 1e9 / peak}
+        forms[form] = info
+    launches = sst.sst_launch_count() - l0
+    clocks = sampler.stop()
+    head = forms["bf16"]
+    line = {
+        "metric": METRIC, "value": head["samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "fs": w.fs, "nfft": w.nfft, "hop": w.hop, "L": w.L,
+                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "bins": plan.nb,
+                   "frames": plan.frames, "form": "bf16 tcgen05 contraction + FP32 inverse",
+                   "l2": "flushed before each timed step"},
+        "vs_fft_form": head["samples_per_s"] / forms["fft"]["samples_per_s"],
+        "snr_gap_db": head["snr_db"] - forms["fft"]["snr_db"],
+        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm", "achieved": head["contraction"]["tflops"],
+                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": head["contraction"]["frac"], "traffic": None,
+                     "peak_note": "measured dense BF16 burst (MEASURED_PEAKS.json)"},
+        "forms": forms, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 # ------------------------------------------------------------------ streaming workload
 def run_stream(args):
     """64 sensor streams at 25.6 kHz pushing 8192-sample chunks with Poisson
@@ -390,7 +494,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="runup_16m", choices=sorted(W.ALL) + ["batch256", "stream64"])
+    ap.add_argument("--workload", default="runup_16m",
+                    choices=sorted(W.ALL) + ["batch256", "stream64", "precision64k_tc"])
     ap.add_argument("--seconds", type=float, default=12.0, help="stream64: simulated real-time seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -398,6 +503,8 @@ def main():
         return run_batch(args)
     if args.workload == "stream64":
         return run_stream(args)
+    if args.workload == "precision64k_tc":
+        return run_tensor(args)
     w = W.ALL[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

@@ -196,6 +196,12 @@ sst_status sst_tc_plan_query(sst_tc_plan_t tc, int32_t *hankel_view, int64_t *ge
  * cluster loads 1/cluster of the basis tile and multicasts it to the others.
  * Results do not depend on it.  SST_EUNSUPPORTED if no such cluster fits. */
 sst_status sst_tc_plan_set_cluster(sst_tc_plan_t tc, int32_t cluster);
+/* Times the contraction on x_dev (n floats) with each cluster size that fits
+ * (best of three after one untimed run, CUDA events on the stream), keeps the
+ * fastest and returns it with its time in ms (either pointer may be NULL).
+ * Synchronises the stream.  Errors as sst_tc_forward and sst_tc_check. */
+sst_status sst_tc_plan_tune(sst_tc_plan_t tc, const float *x_dev, int64_t n, void *stream, int32_t *cluster,
+                            float *ms);
 /* As sst_forward / sst_stft / sst_reassign_map, through the contraction.
  * Layouts as there.  Enqueued on the stream without synchronising; the
  * contraction's waits are bounded, and one that gives up (about a second)

@@ -34,27 +34,7 @@ __global__ void k_gamma_batch(BatchChan *__restrict__ ch, int nchan, const float
     if (threadIdx.x == 0) {
         float r = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
-        SstScalars *sc = b.sc;
-        float bound;
-        if (b.d.relative) {
-            const float mv = sqrtf(r);
-            sc->gamma2 = b.frac2 * r;
-            sc->maxv = mv;
-            bound = mv * 1.001f;
-        } else {
-            bound = r * b.sum_abs_g;
-        }
-        int e = 0;
-        if (bound > 0.f && bound < 3.0e38f) {
-            int ex;
-            frexpf(bound, &ex);
-            e = 61 - ex - b.d.log2_nb;
-        }
-        const int e1 = e / 2, e2 = e - e / 2;
-        sc->s1 = ldexpf(1.f, e1);
-        sc->s2 = ldexpf(1.f, e2);
-        sc->r1 = ldexpf(1.f, -e1);
-        sc->r2 = ldexpf(1.f, -e2);
+        *b.sc = scalars_from_max(r, b.frac2, b.d.relative ? 0 : 1, b.sum_abs_g, b.d.log2_nb);
     }
 }
 
@@ -190,7 +170,7 @@ sst_status build_items(sst_batch *b) {
                 if (r < v.size()) { g.items.push_back(v[r]); any = true; }
             if (!any) break;
         }
-        g.smem = g.kt->smem_frame + 16 * (size_t)g.max_nbo;
+        g.smem = g.kt->smem_frame + tacc_bytes(g.max_nbo);
         b->groups.push_back(std::move(g));
     }
     // inverse groups, by (nf, window class)

@@ -43,6 +43,18 @@ __host__ __device__ __forceinline__ int64_t tslot_of(const SstDev &d, int64_t t)
     return d.tile_cap ? t % d.tile_cap : t;
 }
 
+// Exact T sums.  A source's fixed-point value v = round(S^g 2^e) is kept
+// below 2^SST_T_BITS / nb in magnitude (e from a bound on |S^g|), so a fine
+// bin's sum of at most nb sources stays below 2^SST_T_BITS.  The sums are
+// accumulated in shared memory as four arrays of 32-bit words (re lo, re hi,
+// im lo, im hi), each tacc_stride(nbo) words long: v = hi 2^16 + lo with
+// 0 <= lo < 2^16, so the lo sums of up to 2^16 sources stay below 2^32 and
+// the hi sums below 2^31 -- exact, hence independent of the order of the
+// (native 32-bit) atomic additions.
+#define SST_T_BITS 45
+__host__ __device__ __forceinline__ int tacc_stride(int nbo) { return (nbo + 3) & ~3; }
+__host__ __device__ __forceinline__ size_t tacc_bytes(int nbo) { return 16 * (size_t)tacc_stride(nbo); }
+
 // Per-call scalars produced on the device before the forward kernel runs
 // (at the start of the workspace, or of the static scratch array).
 struct SstScalars {

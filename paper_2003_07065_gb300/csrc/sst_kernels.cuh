@@ -219,8 +219,8 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
 // 0): r = max |S^g|^2, gamma^2 = frac^2 r, maxv = sqrt(r).  Absolute plans
 // (from_x = 1): r = max |x| and |S^g| <= max|x| sum|g|.  Either way the bound
 // B on |S^g| (0.1% margin for the forward kernel's own rounding) gives the
-// fixed-point scale 2^e, e = 61 - ceil(log2 B) - ceil(log2 nb): a frame's at
-// most nb terms then sum below 2^62 in int64.
+// fixed-point scale 2^e, e = SST_T_BITS - ceil(log2 B) - ceil(log2 nb): a
+// frame's at most nb terms then sum below 2^SST_T_BITS.
 __device__ __forceinline__ SstScalars scalars_from_max(float r, float frac2, int from_x, float bound_mul,
                                                        int log2_nb) {
     SstScalars sc = {};
@@ -237,7 +237,7 @@ __device__ __forceinline__ SstScalars scalars_from_max(float r, float frac2, int
     if (bound > 0.f && bound < 3.0e38f) {
         int ex;
         frexpf(bound, &ex);  // bound < 2^ex
-        e = 61 - ex - log2_nb;
+        e = SST_T_BITS - ex - log2_nb;
     }
     const int e1 = e / 2, e2 = e - e / 2;
     sc.s1 = ldexpf(1.f, e1);
@@ -282,13 +282,53 @@ __device__ __forceinline__ FwdScale fwd_scale(const SstDev &d, const SstScalars 
     return f;
 }
 
-// One frame m of the forward transform.  acc_re / acc_im (nbo each) must be
+// Adds a source (V scaled by 2^e) to fine bin l of the T accumulators.
+__device__ __forceinline__ void tacc_add(uint32_t *__restrict__ acc, int stride, int l, float2 V, const FwdScale &fs) {
+    const long long a = __float2ll_rn((V.x * fs.s1) * fs.s2);
+    const long long b = __float2ll_rn((V.y * fs.s1) * fs.s2);
+    atomicAdd(&acc[l], (uint32_t)(a & 0xffff));
+    atomicAdd(&acc[stride + l], (uint32_t)(int32_t)(a >> 16));
+    atomicAdd(&acc[2 * stride + l], (uint32_t)(b & 0xffff));
+    atomicAdd(&acc[3 * stride + l], (uint32_t)(int32_t)(b >> 16));
+}
+
+__device__ __forceinline__ float tacc_value(uint32_t lo, uint32_t hi, const FwdScale &fs) {
+    return (__ll2float_rn((long long)(int32_t)hi * 65536LL + (long long)lo) * fs.r1) * fs.r2;
+}
+
+// Reads fine bins 4 q .. 4 q + 3 (those below nbo) into Trow and clears them.
+__device__ __forceinline__ void tacc_take4(uint32_t *__restrict__ acc, int stride, int q, int nbo,
+                                           float2 *__restrict__ Trow, const FwdScale &fs) {
+    uint4 *a4 = reinterpret_cast<uint4 *>(acc);
+    const int s4 = stride >> 2;
+    const uint4 rl = a4[q], rh = a4[s4 + q], il = a4[2 * s4 + q], ih = a4[3 * s4 + q];
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    a4[q] = z;
+    a4[s4 + q] = z;
+    a4[2 * s4 + q] = z;
+    a4[3 * s4 + q] = z;
+    const float2 t0 = make_float2(tacc_value(rl.x, rh.x, fs), tacc_value(il.x, ih.x, fs));
+    const float2 t1 = make_float2(tacc_value(rl.y, rh.y, fs), tacc_value(il.y, ih.y, fs));
+    const float2 t2 = make_float2(tacc_value(rl.z, rh.z, fs), tacc_value(il.z, ih.z, fs));
+    const float2 t3 = make_float2(tacc_value(rl.w, rh.w, fs), tacc_value(il.w, ih.w, fs));
+    const int l = 4 * q;
+    if (l + 3 < nbo && (reinterpret_cast<uintptr_t>(Trow + l) & 15) == 0) {
+        reinterpret_cast<float4 *>(Trow + l)[0] = make_float4(t0.x, t0.y, t1.x, t1.y);
+        reinterpret_cast<float4 *>(Trow + l)[1] = make_float4(t2.x, t2.y, t3.x, t3.y);
+    } else {
+        Trow[l] = t0;
+        if (l + 1 < nbo) Trow[l + 1] = t1;
+        if (l + 2 < nbo) Trow[l + 2] = t2;
+        if (l + 3 < nbo) Trow[l + 3] = t3;
+    }
+}
+
+// One frame m of the forward transform.  The T accumulators (tacc_stride(nbo) words x 4) must be
 // zero on entry and are zero again on return (MODE_T).
 template <int NF, int MODE>
 __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
                                               float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
-                                              float2 *buf, unsigned long long *acc_re, unsigned long long *acc_im,
-                                              int tid) {
+                                              float2 *buf, uint32_t *acc, int tid) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     float2 v[16];
@@ -329,10 +369,7 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
                 reinterpret_cast<int32_t *>(out1)[o] = l;
                 continue;
             }
-            if (l >= 0) {
-                atomicAdd(&acc_re[l], (unsigned long long)__float2ll_rn((V.x * fs.s1) * fs.s2));
-                atomicAdd(&acc_im[l], (unsigned long long)__float2ll_rn((V.y * fs.s1) * fs.s2));
-            }
+            if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
         }
     }
     // all band reads and atomics done before the T row is read and the next
@@ -340,12 +377,7 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     __syncthreads();
     if (MODE != MODE_T) return;
     float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
-    for (int l = tid; l < d.nbo; l += TPF) {
-        const long long ar = (long long)acc_re[l], ai = (long long)acc_im[l];
-        Trow[l] = make_float2((__ll2float_rn(ar) * fs.r1) * fs.r2, (__ll2float_rn(ai) * fs.r1) * fs.r2);
-        acc_re[l] = 0ull;
-        acc_im[l] = 0ull;
-    }
+    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, tacc_stride(d.nbo), q, d.nbo, Trow, fs);
     // the zeroing above is ordered before the next frame's atomics by the
     // __syncthreads inside the next frame's FFT
 }
@@ -358,16 +390,15 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     // after the frame buffer (BUF float2 = BUF x 8 bytes) and 128 bytes of slack:
-    // the T accumulators, real parts then imaginary parts
-    unsigned long long *acc_re = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
-    unsigned long long *acc_im = acc_re + d.nbo;
+    // the T accumulators
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
     const int tid = threadIdx.x;
     const FwdScale fs = fwd_scale(d, sc, MODE == MODE_T);
     if (MODE == MODE_T)
-        for (int i = tid; i < 2 * d.nbo; i += C::TPF) acc_re[i] = 0ull;
+        for (int i = tid; i < 4 * tacc_stride(d.nbo); i += C::TPF) acc[i] = 0u;
     // (the first __syncthreads in forward_frame orders this before any atomic)
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
-        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc_re, acc_im, tid);
+        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -613,9 +644,9 @@ k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
     __shared__ SstDev sd;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem4) + C::BUF + 16;
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * max_nbo; i += C::TPF) acc[i] = 0ull;
+    for (int i = tid; i < 4 * tacc_stride(max_nbo); i += C::TPF) acc[i] = 0u;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
         __syncthreads();   // previous item done with sd
@@ -625,7 +656,7 @@ k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
         if (!chan_ok<NF>(sd) || sd.nbo > max_nbo || w.end > sd.F) continue;
         const FwdScale fs = fwd_scale(sd, c.sc, true);
         for (int64_t m = w.begin; m < w.end; ++m)
-            forward_frame<NF, MODE_T>(sd, c.x, fs, c.T, nullptr, m, buf, acc, acc + sd.nbo, tid);
+            forward_frame<NF, MODE_T>(sd, c.x, fs, c.T, nullptr, m, buf, acc, tid);
     }
 }
 

@@ -247,7 +247,7 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
     if (bound > 0.f && bound < 3.0e38f) {
         int ex;
         std::frexp(bound, &ex);
-        e = 61 - ex - d.log2_nb;
+        e = SST_T_BITS - ex - d.log2_nb;
     }
     const int e1 = e / 2, e2 = e - e / 2;
     sc.s1 = std::ldexp(1.f, e1);
@@ -261,7 +261,7 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
         return cuda_fail(ce, "stream scalars");
     }
     // kernel attributes for this stream's shapes
-    const size_t smem_f = plan->kt->smem_frame + 16 * (size_t)d.nbo;
+    const size_t smem_f = plan->kt->smem_frame + tacc_bytes(d.nbo);
     const size_t smem_i = plan->kt->smem_frame + 16 * (size_t)d.z * (size_t)(d.k_hi - d.k_lo + 1) + 4 * (size_t)d.seg_len;
     const int ik = d.L <= d.nf / 2 + 1 ? KIND_B_INV : KIND_B_INV_WIDE;
     if (raise_smem(plan->kt, KIND_B_FWD, smem_f) != cudaSuccess || raise_smem(plan->kt, ik, smem_i) != cudaSuccess) {
@@ -429,7 +429,7 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
         for (int64_t t = S.t_next; t < work[i].t_ready; ++t) inv[nf * 16 + ik].push_back({(int)i, 0, t, t + 1});
         for (int64_t p = S.p_next; p < work[i].p_ready; p += 65536)
             fin.push_back({(int)i, 0, p, std::min<int64_t>(work[i].p_ready, p + 65536)});
-        smem_f[nf] = std::max(smem_f[nf], S.plan->kt->smem_frame + 16 * (size_t)c.d.nbo);
+        smem_f[nf] = std::max(smem_f[nf], S.plan->kt->smem_frame + tacc_bytes(c.d.nbo));
         maxnbo[nf] = std::max(maxnbo[nf], c.d.nbo);
         smem_i[nf * 16 + ik] = std::max(smem_i[nf * 16 + ik], S.plan->kt->smem_frame +
                                         16 * (size_t)c.d.z * (size_t)(c.d.k_hi - c.d.k_lo + 1) + 4 * (size_t)c.d.seg_len);

@@ -383,18 +383,35 @@ __global__ void k_tc_hankel(const T *__restrict__ xp, int hop, int64_t rows, int
     }
 }
 
+// 1-D bulk copy global -> shared, completion counted on an mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
 // per frame: the FFT form's epilogue on the contraction's S^g, S^g' (MODE_T,
-// MODE_STFT, MODE_MAP as in k_forward).  A thread loads up to KM bins of a
-// frame before it uses any, so KM loads are in flight per thread.  With
-// maxbits (relative thresholds) every CTA derives the call's scalars from the
-// contraction's max |S^g|^2 itself; otherwise they come from sc.
-template <int MODE, int KM>
-__global__ void __launch_bounds__(256, 8)
+// MODE_STFT, MODE_MAP as in k_forward).  The CTA's frames m = blockIdx.x +
+// i gridDim.x stream through two shared-memory row buffers filled by bulk
+// copies, so the next frame's row arrives while this one is reassigned and
+// written out.  With maxbits (relative thresholds) every CTA derives the
+// call's scalars from the contraction's max |S^g|^2 itself; otherwise they
+// come from sc.  Waits are bounded; on expiry the CTA records it in *err,
+// drains its copies and stops.
+template <int MODE>
+__global__ void __launch_bounds__(256)
 k_tc_band(SstDev d, const float *__restrict__ C, int ldc, const SstScalars *__restrict__ sc,
-          const unsigned *__restrict__ maxbits, float frac2, float2 *__restrict__ out0, void *__restrict__ out1) {
-    extern __shared__ unsigned long long acc[];   // re then im, nbo rounded up to even each (16-byte pairs)
-    const int nbo2 = (d.nbo + 1) & ~1;
-    unsigned long long *acc_re = acc, *acc_im = acc + nbo2;
+          const unsigned *__restrict__ maxbits, float frac2, float2 *__restrict__ out0, void *__restrict__ out1,
+          int *__restrict__ err) {
+    extern __shared__ uint4 smem_band[];
+    const int stride = tacc_stride(d.nbo);
+    const uint32_t rowbytes = 16u * (uint32_t)d.nb;
+    const int tacc_words = MODE == MODE_T ? 4 * stride : 0;
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem_band);
+    float4 *rows = reinterpret_cast<float4 *>(acc + tacc_words);          // 2 x nb float4
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rows + 2 * d.nb);         // 2 mbarriers
+    volatile int *stop = reinterpret_cast<volatile int *>(bar + 2);
     const int tid = threadIdx.x;
     FwdScale fs;
     if (maxbits) {
@@ -404,76 +421,82 @@ k_tc_band(SstDev d, const float *__restrict__ C, int ldc, const SstScalars *__re
     } else {
         fs = fwd_scale(d, sc, MODE == MODE_T);
     }
-    if (MODE == MODE_T)
-        for (int i = tid; i < 2 * nbo2; i += blockDim.x) acc[i] = 0ull;
-    __syncthreads();
-    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x) {
-        const float *row = C + (size_t)m * ldc;
-        for (int base = 0; base < d.nb; base += KM * 256) {
-            float4 c[KM];
-#pragma unroll
-            for (int i = 0; i < KM; ++i) {
-                const int kk = base + tid + i * 256;
-                c[i] = (kk < d.nb) ? __ldg(reinterpret_cast<const float4 *>(row) + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int i = 0; i < KM; ++i) {
-                const int kk = base + tid + i * 256;
-                if (kk >= d.nb) continue;
-                const int k = d.k_lo + kk;
-                const float2 V = make_float2(c[i].x, c[i].y), Vd = make_float2(c[i].z, c[i].w);
-                const size_t o = (size_t)m * d.nb + kk;
-                if (MODE == MODE_STFT) {
-                    out0[o] = V;
-                    reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
-                    continue;
-                }
-                const float mag2 = V.x * V.x + V.y * V.y;
-                // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13)
-                const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
-                int l = -1;
-                if (mag2 > fs.gamma2) {
-                    const float f = floorf(fmaf((float)d.z, delta, 0.5f));
-                    l = -2;
-                    if (f > -1073741824.f && f < 1073741824.f) {
-                        const int lc = d.z * (k - d.k_lo) + (int)f;
-                        if (lc >= 0 && lc < d.nbo) l = lc;
-                    }
-                }
-                if (MODE == MODE_MAP) {
-                    reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
-                    reinterpret_cast<int32_t *>(out1)[o] = l;
-                    continue;
-                }
-                if (l >= 0) {
-                    atomicAdd(&acc_re[l], (unsigned long long)__float2ll_rn((V.x * fs.s1) * fs.s2));
-                    atomicAdd(&acc_im[l], (unsigned long long)__float2ll_rn((V.y * fs.s1) * fs.s2));
-                }
-            }
-        }
-        if (MODE != MODE_T) continue;
-        __syncthreads();
-        // read back and clear two fine bins per thread (16-byte accesses)
-        float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
-        const bool row16 = (reinterpret_cast<uintptr_t>(Trow) & 15) == 0;
-        for (int l2 = tid; 2 * l2 < d.nbo; l2 += blockDim.x) {
-            const ulonglong2 ar = reinterpret_cast<ulonglong2 *>(acc_re)[l2];
-            const ulonglong2 ai = reinterpret_cast<ulonglong2 *>(acc_im)[l2];
-            reinterpret_cast<ulonglong2 *>(acc_re)[l2] = make_ulonglong2(0ull, 0ull);
-            reinterpret_cast<ulonglong2 *>(acc_im)[l2] = make_ulonglong2(0ull, 0ull);
-            const float2 t0 = make_float2((__ll2float_rn((long long)ar.x) * fs.r1) * fs.r2,
-                                          (__ll2float_rn((long long)ai.x) * fs.r1) * fs.r2);
-            const float2 t1 = make_float2((__ll2float_rn((long long)ar.y) * fs.r1) * fs.r2,
-                                          (__ll2float_rn((long long)ai.y) * fs.r1) * fs.r2);
-            if (row16 && 2 * l2 + 1 < d.nbo) {
-                reinterpret_cast<float4 *>(Trow)[l2] = make_float4(t0.x, t0.y, t1.x, t1.y);
-            } else {
-                Trow[2 * l2] = t0;
-                if (2 * l2 + 1 < d.nbo) Trow[2 * l2 + 1] = t1;
-            }
-        }
-        __syncthreads();
+    const int64_t mine = (d.F - blockIdx.x + gridDim.x - 1) / gridDim.x;   // frames of this CTA
+    for (int i = tid; i < tacc_words; i += blockDim.x) acc[i] = 0u;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    if (tid == 0)
+        for (int j = 0; j < 2 && j < mine; ++j) {
+            mbar_expect_tx(&bar[j], rowbytes);
+            bulk_g2s(rows + j * d.nb, C + (size_t)(blockIdx.x + (int64_t)j * gridDim.x) * ldc, rowbytes, &bar[j]);
+        }
+    int64_t i = 0;
+    for (; i < mine; ++i) {
+        const int b = (int)(i & 1);
+        const int64_t m = blockIdx.x + i * gridDim.x;
+        if (tid == 0 && !mbar_wait(&bar[b], (uint32_t)((i >> 1) & 1))) {
+            atomicOr(err, 64);
+            *stop = 1;
+        }
+        __syncthreads();
+        if (*stop) break;
+        const float4 *row = rows + b * d.nb;
+        for (int kk = tid; kk < d.nb; kk += blockDim.x) {
+            const float4 c = row[kk];
+            const int k = d.k_lo + kk;
+            const float2 V = make_float2(c.x, c.y), Vd = make_float2(c.z, c.w);
+            const size_t o = (size_t)m * d.nb + kk;
+            if (MODE == MODE_STFT) {
+                out0[o] = V;
+                reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
+                continue;
+            }
+            const float mag2 = V.x * V.x + V.y * V.y;
+            // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13)
+            const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
+            int l = -1;
+            if (mag2 > fs.gamma2) {
+                const float f = floorf(fmaf((float)d.z, delta, 0.5f));
+                l = -2;
+                if (f > -1073741824.f && f < 1073741824.f) {
+                    const int lc = d.z * (k - d.k_lo) + (int)f;
+                    if (lc >= 0 && lc < d.nbo) l = lc;
+                }
+            }
+            if (MODE == MODE_MAP) {
+                reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
+                reinterpret_cast<int32_t *>(out1)[o] = l;
+                continue;
+            }
+            if (l >= 0) tacc_add(acc, stride, l, V, fs);
+        }
+        __syncthreads();   // row buffer b read, accumulators complete
+        if (tid == 0 && i + 2 < mine) {
+            mbar_expect_tx(&bar[b], rowbytes);
+            bulk_g2s(rows + b * d.nb, C + (size_t)(m + 2 * (int64_t)gridDim.x) * ldc, rowbytes, &bar[b]);
+        }
+        if (MODE == MODE_T) {
+            float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
+            for (int q = tid; 4 * q < d.nbo; q += blockDim.x) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
+            __syncthreads();
+        }
+    }
+    // after an early stop: copies issued for frames i, i + 1 may still be in flight
+    if (tid == 0 && i < mine) {
+        for (int64_t j = i; j < mine && j < i + 2; ++j)
+            if (!mbar_wait(&bar[j & 1], (uint32_t)((j >> 1) & 1))) atomicOr(err, 128);
+    }
+}
+
+// dynamic shared memory of k_tc_band: accumulators, two row buffers, barriers
+template <int MODE>
+size_t tc_band_smem(const SstDev &d) {
+    return (MODE == MODE_T ? tacc_bytes(d.nbo) : 0) + 32 * (size_t)d.nb + 32;
 }
 
 }  // namespace tc
@@ -701,20 +724,20 @@ SST_API sst_status sst_tc_plan_create(sst_plan_t base, int32_t form, sst_tc_plan
         t->grid[ci] = std::max(clusters, 0) * cl;
     }
     t->cl = 1;
-    // the T-mode epilogue's accumulators; the limit is only ever raised, so
-    // plans with different band widths can share the kernels
-    const size_t band_smem = 16 * (size_t)((d.nbo + 1) & ~1);
+    // the epilogue's accumulators and row buffers; the limit is only ever
+    // raised, so plans with different band widths can share the kernels
     {
         static std::mutex mu;
-        static size_t band_max = 48 * 1024;
+        static size_t band_max[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+        const size_t need[3] = {tc_band_smem<MODE_T>(d), tc_band_smem<MODE_STFT>(d), tc_band_smem<MODE_MAP>(d)};
+        const void *fns[3] = {(const void *)k_tc_band<MODE_T>, (const void *)k_tc_band<MODE_STFT>,
+                              (const void *)k_tc_band<MODE_MAP>};
         std::lock_guard<std::mutex> lk(mu);
-        if (e == cudaSuccess && band_smem > band_max) {
-            for (auto fnp : {(const void *)k_tc_band<MODE_T, 1>, (const void *)k_tc_band<MODE_T, 2>,
-                             (const void *)k_tc_band<MODE_T, 4>})
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(fnp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem);
-            if (e == cudaSuccess) band_max = band_smem;
-        }
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            if (need[i] > band_max[i]) {
+                e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[i]);
+                if (e == cudaSuccess) band_max[i] = need[i];
+            }
     }
     if (e != cudaSuccess) {
         cudaFree(t->dmem);
@@ -739,6 +762,8 @@ SST_API sst_status sst_tc_plan_query(sst_tc_plan_t t, int32_t *hankel_view, int6
         *gemm_flops = 2LL * t->base->d.F * (int64_t)t->ncols * t->base->d.L * (t->form == SST_FORM_BF16X3 ? 3 : 1);
     return SST_OK;
 }
+
+SST_API sst_status sst_tc_check(sst_tc_plan_t t, void *stream);
 
 // the contraction: signal prep (and explicit Hankel copy when needed), GEMM, error check
 static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) {
@@ -785,6 +810,60 @@ static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) 
     return SST_OK;
 }
 
+SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t n, void *stream, int32_t *cluster,
+                                    float *ms_out) {
+    if (!t) return fail(SST_EINVAL, "plan is NULL");
+    if (!x_dev) return fail(SST_EINVAL, "input pointer is NULL");
+    if (n != t->base->d.n) return fail(SST_EINVAL, "n = %lld differs from the plan's n", (long long)n);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    SST_CU(cudaEventCreate(&a), "event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(SST_ECUDA, "event");
+    }
+    const int keep = t->cl;
+    int best = 0;
+    float best_ms = 0.f;
+    sst_status s = SST_OK;
+    for (int ci = 0; ci < 3 && s == SST_OK; ++ci) {
+        if (t->grid[ci] <= 0) continue;
+        t->cl = 1 << ci;
+        float ms = 0.f;
+        // one untimed run, then the best of three
+        for (int r = 0; r < 4 && s == SST_OK; ++r) {
+            if (cudaEventRecord(a, st) != cudaSuccess) { s = fail(SST_ECUDA, "event record"); break; }
+            s = tc_contract(t, x_dev, st);
+            if (s != SST_OK) break;
+            if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+                s = fail(SST_ECUDA, "event timing");
+                break;
+            }
+            float e = 0.f;
+            cudaEventElapsedTime(&e, a, b);
+            if (r == 1 || (r > 1 && e < ms)) ms = e;
+        }
+        if (s == SST_OK && (best == 0 || ms < best_ms)) {
+            best = 1 << ci;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != SST_OK) {
+        t->cl = keep;
+        return s;
+    }
+    if ((s = sst_tc_check(t, stream)) != SST_OK) {
+        t->cl = keep;
+        return s;
+    }
+    t->cl = best ? best : keep;
+    if (cluster) *cluster = t->cl;
+    if (ms_out) *ms_out = best_ms;
+    return SST_OK;
+}
+
 SST_API sst_status sst_tc_plan_set_cluster(sst_tc_plan_t t, int32_t cluster) {
     if (!t) return fail(SST_EINVAL, "plan is NULL");
     if (cluster != 1 && cluster != 2 && cluster != 4) return fail(SST_EINVAL, "cluster must be 1, 2 or 4");
@@ -826,25 +905,18 @@ static sst_status tc_scalars(sst_tc_plan_t t, const float *x, cudaStream_t st) {
     return SST_OK;
 }
 
-template <int MODE, int KM>
-static cudaError_t tc_band_launch(sst_tc_plan_t t, int grid, void *o0, void *o1, cudaStream_t st) {
-    const SstDev &d = t->base->d;
-    const size_t smem = MODE == MODE_T ? 16 * (size_t)((d.nbo + 1) & ~1) : 0;
-    const bool rel = d.relative && MODE != MODE_STFT;
-    k_tc_band<MODE, KM><<<grid, 256, smem, st>>>(d, t->C, t->npad, t->sc, rel ? (const unsigned *)t->partial : nullptr,
-                                                 t->base->gamma_frac2, (float2 *)o0, o1);
-    return cudaGetLastError();
-}
-
 template <int MODE>
 static sst_status tc_band(sst_tc_plan_t t, void *o0, void *o1, cudaStream_t st) {
     const SstDev &d = t->base->d;
-    const int grid = (int)std::min<int64_t>(d.F, (int64_t)t->base->num_sms * 8);
-    const int per = (d.nb + 255) / 256;
+    const size_t smem = tc_band_smem<MODE>(d);
+    const int per_sm = std::max(1, std::min(8, (int)(200 * 1024 / smem)));
+    const int grid = (int)std::min<int64_t>(d.F, (int64_t)t->base->num_sms * per_sm);
+    const bool rel = d.relative && MODE != MODE_STFT;
     SST_LAUNCHED_K(MODE == MODE_T ? PK_FORWARD : (MODE == MODE_STFT ? PK_STFT : PK_MAP), st,
-                   (per <= 1   ? tc_band_launch<MODE, 1>(t, grid, o0, o1, st)
-                    : per <= 2 ? tc_band_launch<MODE, 2>(t, grid, o0, o1, st)
-                               : tc_band_launch<MODE, 4>(t, grid, o0, o1, st)),
+                   (k_tc_band<MODE><<<grid, 256, smem, st>>>(d, t->C, t->npad, t->sc,
+                                                           rel ? (const unsigned *)t->partial : nullptr,
+                                                           t->base->gamma_frac2, (float2 *)o0, o1, t->err),
+                    cudaGetLastError()),
                    "tensor-form epilogue");
     return SST_OK;
 }

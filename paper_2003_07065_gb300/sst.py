@@ -76,6 +76,8 @@ def load():
         "sst_tc_plan_query": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64),
                                ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sst_tc_plan_set_cluster": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sst_tc_plan_tune": ([_vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)],
+                             ctypes.c_int),
         "sst_tc_forward": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
         "sst_tc_stft": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_tc_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
@@ -251,6 +253,13 @@ def sst_tc_plan_query(tc) -> dict:
 
 def sst_tc_plan_set_cluster(tc, cluster: int) -> None:
     _check(load().sst_tc_plan_set_cluster(tc, cluster))
+
+
+def sst_tc_plan_tune(tc, x, n, stream=None) -> tuple:
+    """(chosen cluster size, its contraction time in ms)."""
+    cl, ms = ctypes.c_int32(), ctypes.c_float()
+    _check(load().sst_tc_plan_tune(tc, _ptr(x), n, _stream(stream), ctypes.byref(cl), ctypes.byref(ms)))
+    return cl.value, ms.value
 
 
 def sst_tc_forward(tc, x, n, tfr, stream=None):
