@@ -272,33 +272,16 @@ def run_batch(args):
 TC_FORMS = ("fft", "bf16", "bf16x3", "tf32")
 
 
-def run_tensor(args):
-    """Precision workload (Nf 4096, L 2049, hop 16, 1025 in-band bins): one
-    step = forward (FFT form, or the tcgen05 contraction in one of its three
-    operand forms) + the shared direct inverse.  Reports every form's time and
-    the reconstruction SNR against the clean signal; the headline is the BF16
-    tensor form.  The roofline is the contraction's, against the measured
-    dense BF16 tensor peak (TF32 at the nominal TF32 / BF16 ratio)."""
+def tensor_forms(args, w, params, x, clean, stream, flush, bf16_peak):
+    """Per form: fwd+inv step time (L2 flushed before each step), SNR of the
+    reconstruction against the clean signal, per-kernel times and, for the
+    tensor forms, the contraction's tensor-pipe fraction."""
     import torch
-    from paper_2003_07065_gb300 import build, sst
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
-    sst.load()
-    w = W.PRECISION_64K
-    noisy, clean = w.signal()
-    x = torch.from_numpy(noisy.astype(np.float32)).cuda()
-    plan = sst.Plan(**w.params())
+    from paper_2003_07065_gb300 import sst
+    plan = sst.Plan(**params)
     tfr = plan.new_tfr()
     xhat = torch.empty(w.n, dtype=torch.float32, device="cuda")
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    peaks = measured_peaks()
-    bf16_peak = peaks.get("bf16_tflops") or FALLBACK_BF16_TFLOPS
     forms = {}
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(0.3)
-    l0 = sst.sst_launch_count()
     for form in TC_FORMS:
         info = {}
         if form == "fft":
@@ -347,6 +330,39 @@ def run_tensor(args):
             info["contraction"] = {"ms": gemm_ms, "tflops": info["gemm_flops"] / gemm_ms / 1e9,
                                    "peak_tflops": peak, "frac": info["gemm_flops"] / gemm_ms / 1e9 / peak}
         forms[form] = info
+    bins = plan.nb
+    plan.close()
+    return forms, bins
+
+
+def run_tensor(args):
+    """Precision workload (Nf 4096, L 2049, hop 16; the 0-6.4 kHz band at
+    25.6 kHz = 1025 bins): one step = forward (the FFT form, or the tcgen05
+    contraction in one of its three operand forms) + the shared direct inverse.
+    Every form's time and reconstruction SNR (against the clean signal) is
+    reported; the headline is the BF16 tensor form.  The same is timed on the
+    literal 512-bin shape (k = 0..511).  The roofline is the contraction's,
+    against the measured dense BF16 tensor peak (TF32 at the nominal TF32 /
+    BF16 ratio)."""
+    import dataclasses
+    import torch
+    from paper_2003_07065_gb300 import build, sst
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    sst.load()
+    w = W.PRECISION_64K
+    noisy, clean = w.signal()
+    x = torch.from_numpy(noisy.astype(np.float32)).cuda()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    bf16_peak = measured_peaks().get("bf16_tflops") or FALLBACK_BF16_TFLOPS
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = sst.sst_launch_count()
+    forms, bins = tensor_forms(args, w, w.params(), x, clean, stream, flush, bf16_peak)
+    w512 = dataclasses.replace(w, f_hi=511 * w.fs / w.nfft)
+    forms512, bins512 = tensor_forms(args, w512, w512.params(), x, clean, stream, flush, bf16_peak)
     launches = sst.sst_launch_count() - l0
     clocks = sampler.stop()
     head = forms["bf16"]
@@ -355,18 +371,18 @@ def run_tensor(args):
         "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "fs": w.fs, "nfft": w.nfft, "hop": w.hop, "L": w.L,
-                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "bins": plan.nb,
-                   "frames": plan.frames, "form": "bf16 tcgen05 contraction + FP32 inverse",
-                   "l2": "flushed before each timed step"},
+                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "bins": bins,
+                   "form": "bf16 tcgen05 contraction + FP32 inverse", "l2": "flushed before each timed step"},
         "vs_fft_form": head["samples_per_s"] / forms["fft"]["samples_per_s"],
         "snr_gap_db": head["snr_db"] - forms["fft"]["snr_db"],
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm", "achieved": head["contraction"]["tflops"],
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": head["contraction"]["frac"], "traffic": None,
                      "peak_note": "measured dense BF16 burst (MEASURED_PEAKS.json)"},
-        "forms": forms, "gpu_launches": launches, "clocks": clocks,
+        "forms": forms,
+        "literal_512_bins": {"band_hz": [w512.f_lo, w512.f_hi], "bins": bins512, "forms": forms512},
+        "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line))
-    plan.close()
     return 0
 
 
