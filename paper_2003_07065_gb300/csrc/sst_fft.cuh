@@ -38,6 +38,15 @@ template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
 __host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 
+// Padded index of element i0 + r STRIDE given p0 = padded(i0).  When STRIDE is
+// a multiple of 16 the pad count grows by exactly STRIDE / 16 per step, so
+// the address is p0 plus a compile-time constant (an immediate offset on the
+// shared-memory access, no per-element index arithmetic).
+template <int STRIDE> __device__ __forceinline__ int padded_at(int i0, int p0, int r) {
+    if constexpr (STRIDE % 16 == 0) return p0 + r * (STRIDE + STRIDE / 16);
+    else return padded(i0 + r * STRIDE);
+}
+
 // sqrt(1/2), cos(pi/8), sin(pi/8)
 #define SST_R2 0.70710678118654752440f
 #define SST_C8 0.92387953251128675613f
@@ -187,10 +196,11 @@ __device__ __forceinline__ void stockham16_multi(float2 *buf, const float2 *__re
     const bool live = (TPF == NBF) || tid < NBF;
     float2 v[NB][16];
     if (live) {
+        const int p0 = padded(tid);
 #pragma unroll
         for (int f = 0; f < NB; ++f)
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded(tid + r * NBF)];
+            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded_at<NBF>(tid, p0, r)];
     }
     __syncthreads();
     if (live) {
@@ -198,13 +208,14 @@ __device__ __forceinline__ void stockham16_multi(float2 *buf, const float2 *__re
         float2 w[16];
         twiddles16<INV>(w, tw + tw_offset<NF, NS>(), NS, k);
         const int base = (tid - k) * 16 + k;
+        const int pb = padded(base);
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[f][r] = cmul(v[f][r], w[r]);
             dft16<INV>(v[f]);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) buf[f * BS + padded(base + r * NS)] = v[f][r];
+            for (int r = 0; r < 16; ++r) buf[f * BS + padded_at<NS>(base, pb, r)] = v[f][r];
         }
     }
     __syncthreads();
@@ -224,10 +235,11 @@ __device__ __forceinline__ void fft_last_multi(const float2 *buf, const float2 *
                                                float2 (&v)[NB][16]) {
     constexpr int NS = NF / 16;
     if (TPF == NS || tid < NS) {
+        const int p0 = padded(tid);
 #pragma unroll
         for (int f = 0; f < NB; ++f)
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded(tid + r * NS)];
+            for (int r = 0; r < 16; ++r) v[f][r] = buf[f * BS + padded_at<NS>(tid, p0, r)];
         float2 w[16];
         twiddles16<INV>(w, tw + tw_offset<NF, NS>(), NS, tid);
 #pragma unroll
@@ -251,8 +263,9 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
     for (int b = 0; b < PER; ++b) {
         const int j = tid + b * TPF;
         if (PER * TPF == NBF || j < NBF) {
+            const int p0 = padded(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = buf[padded(j + r * NBF)];
+            for (int r = 0; r < R; ++r) v[b][r] = buf[padded_at<NBF>(j, p0, r)];
         }
     }
     __syncthreads();
@@ -264,8 +277,16 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
             if constexpr (NS > 1) twiddle16<INV>(v[b], tw + tw_offset<NF, NS>(), NS, k);
             dft_r<R, INV>(v[b]);
             const int base = (j - k) * R + k;
+            if constexpr (NS == 1) {
+                // span 1: the R outputs j R .. j R + R - 1 share one pad block (R divides 16)
+                const int pb = padded(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[padded(base + r * NS)] = v[b][r];
+                for (int r = 0; r < R; ++r) buf[pb + r] = v[b][r];
+            } else {
+                const int pb = padded(base);
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[padded_at<NS>(base, pb, r)] = v[b][r];
+            }
         }
     }
     __syncthreads();
@@ -303,8 +324,10 @@ __device__ __forceinline__ void fft_first_from_regs(float2 *buf, float2 (*v)[Fft
         const int j = tid + b * TPF;
         if (PER * TPF == NBF || j < NBF) {
             dft_r<R1, INV>(v[b]);
+            // outputs j R1 .. j R1 + R1 - 1 share one pad block (R1 divides 16)
+            const int pb = padded(j * R1);
 #pragma unroll
-            for (int r = 0; r < R1; ++r) buf[padded(j * R1 + r)] = v[b][r];
+            for (int r = 0; r < R1; ++r) buf[pb + r] = v[b][r];
         }
     }
 }
@@ -318,8 +341,9 @@ __device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2
     constexpr int NS = NF / 16;
     const int j = tid;
     if (TPF == NS || j < NS) {
+        const int p0 = padded(j);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = buf[padded(j + r * NS)];
+        for (int r = 0; r < 16; ++r) v[r] = buf[padded_at<NS>(j, p0, r)];
         twiddle16<INV>(v, tw + tw_offset<NF, NS>(), NS, j);
         dft16<INV>(v);
     }
