@@ -495,23 +495,33 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             const float2 *Tb = Tst + (d.z + s) * nq, *Tbm = Tst + (d.z + sb) * nq;
             // first pass with the spectrum built in registers:
             // Y_s[k] = (1/NF) (X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl]))
+            // Input k = j + r NF/R1 reads q = k - k_lo and, for the image,
+            // qm = ((NF - k - dl) mod NF) - k_lo = (NF - dl - j - k_lo) - r NF/R1,
+            // except at k = 0 with dl = 0 (qm = -k_lo).  The band is a small part
+            // of the spectrum, so most r hold nothing for a whole warp: those
+            // iterations are skipped on a warp vote.
+            constexpr int STEP = NF / C::R1;
             float2 u[C::PER1][C::R1];
 #pragma unroll
             for (int bb = 0; bb < C::PER1; ++bb) {
                 const int j = tid + bb * TPF;
+                const bool jok = C::PER1 * TPF == NF / C::R1 || j < NF / C::R1;
+                const int q0 = j - d.k_lo;
+                const int qm0 = NF - dl - j - d.k_lo;
 #pragma unroll
                 for (int r = 0; r < C::R1; ++r) {
-                    const int k = j + r * (NF / C::R1);
                     float2 y = make_float2(0.f, 0.f);
-                    if (C::PER1 * TPF == NF / C::R1 || j < NF / C::R1) {
-                        const int q = k - d.k_lo;
-                        if ((unsigned)q < (unsigned)nqs) {
+                    const int q = q0 + r * STEP;
+                    const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
+                    const bool hd = jok && (unsigned)q < (unsigned)nqs;
+                    const bool hm = jok && (unsigned)qm < (unsigned)nqb;
+                    if (__any_sync(0xffffffffu, hd || hm)) {
+                        if (hd) {
                             const float2 xa = Ta[q], xb = Tb[q];
                             y.x += xa.x - xb.y;
                             y.y += xa.y + xb.x;
                         }
-                        const int qm = ((NF - k - dl) & (NF - 1)) - d.k_lo;
-                        if ((unsigned)qm < (unsigned)nqb) {
+                        if (hm) {
                             const float2 xa = Tam[qm], xb = Tbm[qm];
                             // conj(xa) + i conj(xb)
                             y.x += xa.x + xb.y;
