@@ -55,6 +55,14 @@ typedef enum {
 
 /* flags */
 #define SST_GAMMA_RELATIVE 0x1u  /* gamma is a fraction of max|V| over all frames and in-band bins */
+/* Relative plans only: find max|V| in a separate full pass before the forward
+ * transform (as the batch API does), instead of the default one-pass
+ * threshold, which keeps every source clearly above the threshold, sets aside
+ * those whose fate depends on the exact max|V| and settles them once the
+ * forward pass has found it.  Both give the same kept set up to the rounding
+ * of max|V| (the FP32 STFT of two different FFT packings); batch results are
+ * bit-identical to single-plan results of plans with this flag. */
+#define SST_TWO_PASS 0x2u
 
 typedef struct sst_plan *sst_plan_t;
 
@@ -141,6 +149,15 @@ sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, floa
  * threshold), written as one float to maxv_dev. */
 sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev,
                          void *workspace_dev, void *stream);
+
+/* The last sst_forward / sst_forward_inverse of a relative plan with the
+ * one-pass threshold (the default): how many sources waited for the exact
+ * threshold, how many fine bins they fell in, and whether a record buffer
+ * overflowed so that the two-pass kernels redid the forward (then 1).  Reads
+ * the control words the call left in `workspace` (synchronises the device).
+ * Zeros for other plans. */
+sst_status sst_threshold_stats(sst_plan_t plan, const void *workspace, int64_t *waiting, int64_t *bins,
+                               int32_t *fell_back);
 
 /* Forward SST (as sst_forward) that allocates nothing and takes no
  * workspace.  The paper has no counterpart: this exists for callers that

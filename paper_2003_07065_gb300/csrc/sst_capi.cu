@@ -42,8 +42,10 @@ const KernelTable *table_for_nf(int nf) {
 // Reduce the pre-pass partials (max |S^g|^2 per CTA for relative plans, max
 // |x| per CTA for absolute ones) into the call's scalars (scalars_from_max).
 __global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
-                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out) {
+                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out,
+                        const unsigned *__restrict__ gate) {
     __shared__ float red[32];
+    if (gate && *gate == 0u) return;
     float v = 0.f;
     for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmaxf(v, partial[i]);
 #pragma unroll
@@ -71,6 +73,112 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
         float r = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
         partial[blockIdx.x] = r;
+    }
+}
+
+// ---- one-pass relative threshold (run_forward_spec)
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// max over frames of A_m = sum_j |x[m H + j - M]| |g_j|, which bounds |S^g| in
+// every bin of frame m; folded into ctl[4] (float bits).  A CTA takes tiles
+// of tf frames, staging the tile's |x| segment ((tf - 1) H + L floats) in
+// shared memory; a warp sums one frame at a time.
+__global__ void k_frame_absmax(SstDev d, const float *__restrict__ x, int tf, unsigned *__restrict__ ctl) {
+    extern __shared__ float seg[];
+    __shared__ float red[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t tiles = (d.F + tf - 1) / tf;
+    const int len = (tf - 1) * d.hop + d.L;
+    float best = 0.f;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t m0 = t * tf;
+        const int64_t s0 = m0 * d.hop - d.M;
+        __syncthreads();
+        for (int i = tid; i < len; i += blockDim.x) {
+            const int64_t p = s0 + i;
+            seg[i] = (p >= 0 && p < d.n) ? fabsf(x[p]) : 0.f;
+        }
+        __syncthreads();
+        for (int f = warp; f < tf && m0 + f < d.F; f += nw) {
+            const float *w = seg + f * d.hop;
+            float a = 0.f;
+            for (int j = lane; j < d.L; j += 32) a = fmaf(w[j], fabsf(__ldg(&d.g[j])), a);
+            best = fmaxf(best, warp_sum(a));
+        }
+    }
+    best = warp_max(best);
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+        float r = 0.f;
+        for (int w = 0; w < nw; ++w) r = fmaxf(r, red[w]);
+        if (r > 0.f) atomicMax(&ctl[4], __float_as_uint(r));
+    }
+}
+
+// The one-pass scalars: g_lb2 from the sampled pre-pass maximum (a lower bound
+// of max |S^g|^2, 0.1% margin against the two FFT packings' rounding), g_ub2
+// and the fixed-point scale from max_m A_m (an upper bound, 0.1% margin).
+__global__ void k_spec_scalars(const float *__restrict__ partial, int count, const unsigned *__restrict__ ctl,
+                               float frac2, int log2_nb, SstScalars *__restrict__ sc) {
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmaxf(v, partial[i]);
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+        const float amax = __uint_as_float(ctl[4]);
+        SstScalars s = scalars_from_max(amax, frac2, 1, 1.001f, log2_nb);
+        const float ub = amax * 1.001f;
+        s.gamma2 = 0.f;
+        s.maxv = 0.f;
+        s.g_lb2 = frac2 * r * 0.999f;
+        s.g_ub2 = frac2 * ub * ub;
+        *sc = s;
+    }
+}
+
+// Settle the waiting sources against the exact gamma^2 = frac^2 max |S^g|^2
+// (the same arithmetic as k_gamma): a kept one adds its fixed-point value to
+// its bin record (exact integer atomics, so the order does not matter).
+__global__ void k_spec_fix_src(SpecBuf sb, const SstScalars *__restrict__ sc, float frac2) {
+    if (sb.ctl[3]) return;
+    const float gamma2 = frac2 * __uint_as_float(sb.ctl[0]);
+    const unsigned n = min(sb.ctl[1], (unsigned)sb.cap_src);
+    const float s1 = sc->s1, s2 = sc->s2;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SpecSrc r = sb.src[i];
+        if (r.bin < 0 || !(r.mag2 > gamma2)) continue;
+        const long long a = __float2ll_rn((r.vr * s1) * s2);
+        const long long b = __float2ll_rn((r.vi * s1) * s2);
+        uint32_t *w = sb.bin[r.bin].w;
+        atomicAdd(&w[0], (uint32_t)(a & 0xffff));
+        atomicAdd(&w[1], (uint32_t)(int32_t)(a >> 16));
+        atomicAdd(&w[2], (uint32_t)(b & 0xffff));
+        atomicAdd(&w[3], (uint32_t)(int32_t)(b >> 16));
+    }
+}
+
+// Rewrite the T entries of the bins that received waiting sources.
+__global__ void k_spec_fix_bin(SpecBuf sb, const SstScalars *__restrict__ sc, SstDev d, float2 *__restrict__ T) {
+    if (sb.ctl[3]) return;
+    const unsigned n = min(sb.ctl[2], (unsigned)sb.cap_bin);
+    FwdScale fs;
+    fs.r1 = sc->r1;
+    fs.r2 = sc->r2;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SpecBin r = sb.bin[i];
+        if (r.l < 0) continue;   // an unused chunk tail
+        T[(size_t)trow_of(d, r.m) * d.nbo + r.l] = make_float2(tacc_value(r.w[0], r.w[1], fs),
+                                                               tacc_value(r.w[2], r.w[3], fs));
     }
 }
 
@@ -151,7 +259,7 @@ static sst_status validate(const sst_params *p) {
     if (!(p->gamma >= 0.0) || !std::isfinite(p->gamma)) return fail(SST_EINVAL, "gamma must be finite and >= 0");
     if ((p->g == nullptr) != (p->dg == nullptr)) return fail(SST_EINVAL, "give both g and dg, or neither");
     if (!p->g && !(p->sigma > 0.0)) return fail(SST_EINVAL, "sigma must be > 0 when g is not given");
-    if (p->flags & ~SST_GAMMA_RELATIVE) return fail(SST_EINVAL, "unknown flags 0x%x", p->flags);
+    if (p->flags & ~(SST_GAMMA_RELATIVE | SST_TWO_PASS)) return fail(SST_EINVAL, "unknown flags 0x%x", p->flags);
     return SST_OK;
 }
 
@@ -379,10 +487,31 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->grid_fwd = grid_for(KIND_FWD_T, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
 
+    // ---- one-pass relative threshold (default for relative plans)
+    pl->smem_fwd_spec = pl->smem_fwd_t +
+                        (spec_in_frame(nb, nbo, (int)((kt->smem_frame - 128) / sizeof(float2))) ? 0 : spec_smem_bytes(nbo));
+    pl->spec = d.relative && !(p.flags & SST_TWO_PASS) && pl->smem_fwd_spec <= smax;
+    if (pl->spec) {
+        ce = raise_smem(kt, KIND_FWD_SPEC, pl->smem_fwd_spec);
+        if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
+        pl->grid_fwd_spec = grid_for(KIND_FWD_SPEC, pl->smem_fwd_spec, F);
+        // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
+        pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop + 1));
+        // records: 1/64 of the sources, plus the chunk tails each CTA may leave unused
+        pl->spec_cap = (int)std::min<int64_t>(std::max<int64_t>(4096, F * (int64_t)nb / 64) +
+                                                  (int64_t)SPEC_CHUNK * pl->grid_fwd_spec,
+                                              (int64_t)1 << 28);
+    }
+
     // ---- workspace: [scalars 256 B][absmax partials][overlap-add partials]
+    //      then, for the one-pass threshold, [control 256 B][source records][bin records]
     pl->ws_off_partial = 256;
     pl->ws_off_ola = align256(pl->ws_off_partial + sizeof(float) * pl->grid_absmax);
     pl->ws_bytes = align256(pl->ws_off_ola + sizeof(float) * (size_t)d.ntiles * d.seg_len);
+    if (pl->spec) {
+        pl->ws_off_spec = pl->ws_bytes;
+        pl->ws_bytes = align256(pl->ws_off_spec + 256 + (sizeof(SpecSrc) + sizeof(SpecBin)) * (size_t)pl->spec_cap);
+    }
     *out = pl;
     return SST_OK;
 }
@@ -450,12 +579,12 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
     if (profile) {
         SST_LAUNCHED_K(PK_GAMMA, st,
                        (k_gamma<<<1, 256, 0, st>>>(partial, count, pl->gamma_frac2, pl->d.relative ? 0 : 1,
-                                                   pl->sum_abs_g, pl->d.log2_nb, sc, maxv_out),
+                                                   pl->sum_abs_g, pl->d.log2_nb, sc, maxv_out, nullptr),
                         cudaGetLastError()),
                        "gamma launch");
     } else {
         k_gamma<<<1, 256, 0, st>>>(partial, count, pl->gamma_frac2, pl->d.relative ? 0 : 1, pl->sum_abs_g,
-                                   pl->d.log2_nb, sc, maxv_out);
+                                   pl->d.log2_nb, sc, maxv_out, nullptr);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "gamma launch");
         count_launch();
@@ -463,7 +592,78 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
     return SST_OK;
 }
 
+static SpecBuf ws_spec(sst_plan_t pl, void *ws) {
+    SpecBuf b;
+    char *base = (char *)ws + pl->ws_off_spec;
+    b.ctl = (unsigned *)base;
+    b.src = (SpecSrc *)(base + 256);
+    b.bin = (SpecBin *)(base + 256 + sizeof(SpecSrc) * (size_t)pl->spec_cap);
+    b.cap_src = b.cap_bin = pl->spec_cap;
+    return b;
+}
+
+// Relative threshold in one forward pass.  The FFT pre-pass over every frame
+// (about a third of the forward's cost) is replaced by two cheap bounds:
+// g_lb from the pre-pass on every 16th group of four frames (below the true
+// gamma), g_ub from max_m A_m (above it).  The forward keeps sources above
+// g_ub at once, drops those at or below g_lb, and records the rest with the
+// exact partial sums of their bins; it also finds the exact max |S^g|.  Two
+// small kernels then keep the recorded sources above the exact gamma and
+// rewrite their bins.  Same kept set and the same exact sums as the two-pass
+// path (up to the rounding of max |S^g|).  If a record buffer overflows, the
+// two-pass kernels, launched behind a device-side gate, redo the forward.
+static constexpr int kSpecStride = 16;
+static sst_status run_forward_spec(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
+    const SstDev &d = pl->d;
+    SstScalars *sc = ws_scalars(pl, ws);
+    float *partial = ws_partial(pl, ws);
+    const SpecBuf sb = ws_spec(pl, ws);
+    SST_CU(cudaMemsetAsync(sb.ctl, 0, 64, st), "control reset");
+    {
+        const int64_t tiles = (d.F + pl->spec_tf - 1) / pl->spec_tf;
+        const int grid = (int)std::min<int64_t>(tiles, (int64_t)pl->num_sms * 8);
+        const size_t smem = sizeof(float) * ((size_t)(pl->spec_tf - 1) * d.hop + d.L);
+        SST_LAUNCHED_K(PK_ABSMAX, st,
+                       (k_frame_absmax<<<grid, 256, smem, st>>>(d, x, pl->spec_tf, sb.ctl), cudaGetLastError()),
+                       "frame bound launch");
+    }
+    SstDev ds = d;
+    ds.sample_stride = kSpecStride;
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(ds, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+                   "sampled pre-pass launch");
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   (k_spec_scalars<<<1, 256, 0, st>>>(partial, pl->grid_absmax, sb.ctl, pl->gamma_frac2, d.log2_nb,
+                                                      sc),
+                    cudaGetLastError()),
+                   "one-pass scalars launch");
+    SstDev df = d;
+    df.spec = sb;
+    SST_LAUNCHED_K(PK_FORWARD, st,
+                   pl->kt->forward(df, KIND_FWD_SPEC, x, sc, tfr, nullptr, pl->grid_fwd_spec, pl->smem_fwd_spec, st),
+                   "one-pass forward launch");
+    const int gfix = pl->num_sms * 4;
+    SST_LAUNCHED_K(PK_OTHER, st, (k_spec_fix_src<<<gfix, 256, 0, st>>>(sb, sc, pl->gamma_frac2), cudaGetLastError()),
+                   "threshold settle launch");
+    SST_LAUNCHED_K(PK_OTHER, st, (k_spec_fix_bin<<<gfix, 256, 0, st>>>(sb, sc, d, (float2 *)tfr), cudaGetLastError()),
+                   "bin rewrite launch");
+    // the two-pass path, run only if a record buffer overflowed
+    SstDev dg = d;
+    dg.gate = sb.ctl + 3;
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(dg, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+                   "absmax launch");
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   (k_gamma<<<1, 256, 0, st>>>(partial, pl->grid_absmax, pl->gamma_frac2, 0, 1.f, d.log2_nb, sc,
+                                               nullptr, sb.ctl + 3),
+                    cudaGetLastError()),
+                   "gamma launch");
+    SST_LAUNCHED_K(PK_FORWARD, st,
+                   pl->kt->forward(dg, KIND_FWD_T, x, sc, tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   "forward launch");
+    return SST_OK;
+}
+
 static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
+    if (pl->spec) return run_forward_spec(pl, x, tfr, ws, st);
     sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
     if (s != SST_OK) return s;
     SST_LAUNCHED_K(PK_FORWARD, st,
@@ -563,7 +763,7 @@ SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n,
                    "absmax launch");
     SST_LAUNCHED_K(PK_GAMMA, st,
                    (k_gamma<<<1, 256, 0, st>>>(ws_partial(plan, ws), plan->grid_absmax, plan->gamma_frac2, 0, 1.f,
-                                               plan->d.log2_nb, ws_scalars(plan, ws), maxv_dev),
+                                               plan->d.log2_nb, ws_scalars(plan, ws), maxv_dev, nullptr),
                     cudaGetLastError()),
                    "gamma launch");
     return SST_OK;
@@ -617,6 +817,22 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
            "forward launch");
     count_launch();
+    return SST_OK;
+}
+
+SST_API sst_status sst_threshold_stats(sst_plan_t plan, const void *ws, int64_t *waiting, int64_t *bins,
+                                       int32_t *fell_back) {
+    if (!plan || !ws) return fail(SST_EINVAL, "plan or workspace is NULL");
+    if (waiting) *waiting = 0;
+    if (bins) *bins = 0;
+    if (fell_back) *fell_back = 0;
+    if (!plan->spec) return SST_OK;
+    unsigned ctl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    SST_CU(cudaDeviceSynchronize(), "device synchronise");
+    SST_CU(cudaMemcpy(ctl, (const char *)ws + plan->ws_off_spec, sizeof ctl, cudaMemcpyDeviceToHost), "control read");
+    if (waiting) *waiting = ctl[5];
+    if (bins) *bins = ctl[6];
+    if (fell_back) *fell_back = ctl[3] ? 1 : 0;
     return SST_OK;
 }
 

@@ -5,11 +5,34 @@
 
 namespace sst {
 
+// Records of the one-pass relative threshold (run_forward_spec in
+// sst_capi.cu): sources whose keep/drop decision waits for the call's exact
+// max |S^g|, and the fine bins they land in with the exact sums of the
+// sources already kept there.
+struct SpecSrc {
+    int32_t bin;      // index of its SpecBin, or -1 when that record did not fit
+    float vr, vi;     // S^g
+    float mag2;       // |S^g|^2 as the forward kernel computed it
+};
+struct SpecBin {
+    int64_t m;        // frame
+    int32_t l;        // fine bin
+    uint32_t w[4];    // exact sums (re lo, re hi, im lo, im hi), see tacc_*
+    int32_t pad;
+};
+struct SpecBuf {
+    unsigned *ctl;    // [0] max |S^g|^2 (float bits), [1] source records taken, [2] bin records taken,
+                      // [3] overflow, [4] max_m A_m (float bits), [5] waiting sources, [6] their bins
+    SpecSrc *src;
+    SpecBin *bin;
+    int cap_src, cap_bin;
+};
+
 struct SstDev {
     // tables (device pointers owned by the plan)
     const float2 *win;  // (g[j], g'[j]) for j = -M..M, L entries
     const float *g;     // g[j], L entries
-    const float2 *tw;   // Stockham twiddles per pass, [Ns - R1 + (r - 1) Ns + k] = W_{16 Ns}^{r k}
+    const float2 *tw;   // Stockham twiddles per pass, [4 (Ns - R1) / 15 + i Ns + k] = W_{16 Ns}^{2^i k}, i = 0..3
     // inverse sub-grid twiddle exp(+2 pi i s n / (z nf)) for the last-pass output slot
     // q = j + r nf/16 (n = q, or q - nf when wrapped) = twb[s nf/16 + j] * twc[(2 s + wrapped) 16 + r]
     const float2 *twb;  // [s nf/16 + j] = exp(2 pi i s j / (z nf))
@@ -34,6 +57,10 @@ struct SstDev {
     int64_t xoff;       // the x pointer holds samples from global index xoff on
     int trow_cap;       // T row of frame m is m % trow_cap (ring), or m when 0
     int tile_cap;       // overlap-add slot of tile t is t % tile_cap, or t when 0
+    // one-pass relative threshold (zero / null otherwise)
+    const unsigned *gate;  // when set, the pre-pass and forward kernels run only if *gate != 0
+    int sample_stride;     // pre-pass: every sample_stride-th group of four frames (0 or 1: all)
+    SpecBuf spec;          // forward MODE_SPEC records
 };
 
 __host__ __device__ __forceinline__ int64_t trow_of(const SstDev &d, int64_t m) {
@@ -62,7 +89,9 @@ struct SstScalars {
     float maxv;     // max |S^g| over frames and band bins (relative plans)
     float s1, s2;   // fixed-point scale 2^e = s1 s2 for the exact T sums
     float r1, r2;   // its inverse 2^-e = r1 r2
-    float pad[2];
+    // one-pass relative threshold: sources above g_ub2 are kept at once, those
+    // in (g_lb2, g_ub2] wait for the exact gamma, those at or below g_lb2 are dropped
+    float g_lb2, g_ub2;
 };
 
 // One channel of a batch (sst_batch_*): its plan's device view (with the

@@ -19,6 +19,7 @@ const void *kernel_of(int kind) {
         case KIND_FWD_T: return (const void *)k_forward<NF, MODE_T>;
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
+        case KIND_FWD_SPEC: return (const void *)k_forward<NF, MODE_SPEC>;
         case KIND_INV: return (const void *)k_inverse<NF, true>;
         case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
         case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
@@ -57,6 +58,9 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
             break;
         case KIND_FWD_MAP:
             k_forward<NF, MODE_MAP><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+            break;
+        case KIND_FWD_SPEC:
+            k_forward<NF, MODE_SPEC><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         default: return cudaErrorInvalidValue;
     }

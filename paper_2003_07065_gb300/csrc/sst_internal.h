@@ -81,5 +81,9 @@ struct sst_plan {
     int inv_kind = sst::KIND_INV;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
     size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
+    // one-pass relative threshold
+    bool spec = false;
+    size_t smem_fwd_spec = 0, ws_off_spec = 0;
+    int grid_fwd_spec = 0, spec_tf = 1, spec_cap = 0;
     std::vector<double> g64, dgs64;   // FP64 window g and s g' (basis of the tensor form)
 };

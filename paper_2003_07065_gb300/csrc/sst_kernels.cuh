@@ -206,9 +206,12 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     float *red = reinterpret_cast<float *>(buf + 2 * C::BUF);
     const int tid = threadIdx.x;
+    if (d.gate && *d.gate == 0u) return;
     const int64_t nquads = (d.F + 3) / 4;
+    const int64_t step = d.sample_stride > 1 ? d.sample_stride : 1;
     float best = 0.f;
-    for (int64_t qq = blockIdx.x; qq < nquads; qq += gridDim.x) best = absmax_quad<NF>(d, x, qq, buf, tid, best);
+    for (int64_t qq = blockIdx.x * step; qq < nquads; qq += gridDim.x * step)
+        best = absmax_quad<NF>(d, x, qq, buf, tid, best);
     best = block_max<C::NWARP>(best, red, tid);
     if (tid == 0) partial[blockIdx.x] = best;
 }
@@ -248,7 +251,8 @@ __device__ __forceinline__ SstScalars scalars_from_max(float r, float frac2, int
 }
 
 __global__ void k_gamma(const float *__restrict__ partial, int count, float frac2, int from_x, float bound_mul,
-                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out);
+                        int log2_nb, SstScalars *__restrict__ sc, float *__restrict__ maxv_out,
+                        const unsigned *__restrict__ gate);
 
 // Pre-pass of absolute-threshold plans: max |x| per CTA (bounds |S^g| by max|x| sum|g|).
 __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict__ partial);
@@ -266,18 +270,132 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
 // above 2^-39 of the bound); shared-memory 64-bit integer adds are order
 // independent, so the rounded result does not depend on thread scheduling.
 // ---------------------------------------------------------------------------
-enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2 };
+enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2, MODE_SPEC = 3 };
+
+// MODE_SPEC: per-frame shared-memory list of the sources that wait for the
+// exact threshold (beyond it the call falls back to the two-pass path)
+constexpr int SPEC_MCAP = 256;
+struct SpecFrame {
+    int nmarg;                 // sources listed for this frame
+    int pad[3];
+    float4 item[SPEC_MCAP];    // (l as int bits, S^g re, S^g im, |S^g|^2)
+    int binidx[SPEC_MCAP];     // the bin record of each listed source
+};
+// Records are taken from the global arrays in chunks of SPEC_CHUNK per CTA
+// (one global atomic per chunk, not per frame); unused chunk tails are
+// marked invalid (source bin -1, bin l -1).
+constexpr unsigned SPEC_CHUNK = 256;
+struct SpecCursor {
+    unsigned src_cur, src_end, bin_cur, bin_end;
+};
+__device__ __forceinline__ void spec_drop_src(const SpecBuf &b, unsigned from, unsigned to) {
+    for (unsigned i = from; i < to && i < (unsigned)b.cap_src; ++i) b.src[i].bin = -1;
+}
+__device__ __forceinline__ void spec_drop_bin(const SpecBuf &b, unsigned from, unsigned to) {
+    for (unsigned i = from; i < to && i < (unsigned)b.cap_bin; ++i) b.bin[i].l = -1;
+}
+// k records from a chunk cursor (lane 0's registers); returns the first index
+__device__ __forceinline__ unsigned spec_take(const SpecBuf &b, unsigned &cur, unsigned &end, unsigned k,
+                                              unsigned *counter, bool src) {
+    if (cur + k > end) {
+        if (src) spec_drop_src(b, cur, end);
+        else spec_drop_bin(b, cur, end);
+        const unsigned take = max(SPEC_CHUNK, k);
+        cur = atomicAdd(counter, take);
+        end = cur + take;
+    }
+    const unsigned r = cur;
+    cur += k;
+    return r;
+}
+// Warp 0, after the frame's sources are listed: one bin record per distinct
+// fine bin (with the exact sums of the sources already kept there, read
+// before the accumulators are cleared), then one source record per listed
+// source pointing at its bin's record.
+__device__ __forceinline__ void spec_records(const SstDev &d, SpecFrame *sf, const uint32_t *acc, int64_t m,
+                                             int lane, SpecCursor *cur) {
+    const int n = min(sf->nmarg, SPEC_MCAP);
+    const int stride = tacc_stride(d.nbo);
+    if (lane == 0 && sf->nmarg > SPEC_MCAP) d.spec.ctl[3] = 1u;
+    for (int c = 0; c < n; c += 32) {
+        const int i = c + lane;
+        const int l = i < n ? __float_as_int(sf->item[i].x) : -1;
+        int first = i;   // the earliest listed source with the same bin
+        if (i < n)
+            for (int j = 0; j < i; ++j)
+                if (__float_as_int(sf->item[j].x) == l) { first = j; break; }
+        const bool lead = i < n && first == i;
+        const unsigned lm = __ballot_sync(0xffffffffu, lead);
+        unsigned base = 0;
+        if (lane == 0 && lm) {
+            base = spec_take(d.spec, cur->bin_cur, cur->bin_end, (unsigned)__popc(lm), &d.spec.ctl[2], false);
+            atomicAdd(&d.spec.ctl[6], (unsigned)__popc(lm));   // statistics (no wait)
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lead) {
+            const unsigned b = base + (unsigned)__popc(lm & ((1u << lane) - 1u));
+            if (b < (unsigned)d.spec.cap_bin) {
+                SpecBin r;
+                r.m = m;
+                r.l = l;
+                r.w[0] = acc[l];
+                r.w[1] = acc[stride + l];
+                r.w[2] = acc[2 * stride + l];
+                r.w[3] = acc[3 * stride + l];
+                r.pad = 0;
+                d.spec.bin[b] = r;
+                sf->binidx[i] = (int)b;
+            } else {
+                d.spec.ctl[3] = 1u;
+                sf->binidx[i] = -1;
+            }
+        }
+        __syncwarp();
+        if (i < n && !lead) sf->binidx[i] = sf->binidx[first];
+        __syncwarp();
+    }
+    unsigned sbase = 0;
+    if (lane == 0 && n) {
+        sbase = spec_take(d.spec, cur->src_cur, cur->src_end, (unsigned)n, &d.spec.ctl[1], true);
+        atomicAdd(&d.spec.ctl[5], (unsigned)n);
+    }
+    sbase = __shfl_sync(0xffffffffu, sbase, 0);
+    for (int i = lane; i < n; i += 32) {
+        const unsigned g = sbase + (unsigned)i;
+        if (g < (unsigned)d.spec.cap_src) {
+            const float4 it = sf->item[i];
+            SpecSrc r;
+            r.bin = sf->binidx[i];
+            r.vr = it.y;
+            r.vi = it.z;
+            r.mag2 = it.w;
+            d.spec.src[g] = r;
+        } else {
+            d.spec.ctl[3] = 1u;
+        }
+    }
+}
+// bytes of MODE_SPEC shared state
+__host__ __device__ __forceinline__ size_t spec_smem_bytes(int nbo) {
+    return sizeof(SpecFrame);
+}
+// whether it fits in a frame buffer of buf float2 after the 2 nb band values
+__host__ __device__ __forceinline__ bool spec_in_frame(int nb, int nbo, int buf) {
+    return ((16 * (size_t)nb + 15) & ~(size_t)15) + spec_smem_bytes(nbo) <= 8 * (size_t)buf;
+}
 
 struct FwdScale {
-    float gamma2;   // threshold squared
+    float gamma2;   // threshold squared (MODE_SPEC: the lower one, g_lb2)
     float s1, s2;   // fixed-point scale 2^e = s1 s2
     float r1, r2;   // 2^-e = r1 r2
+    float g_ub2;    // MODE_SPEC: above this a source is kept without waiting
 };
 
 __device__ __forceinline__ FwdScale fwd_scale(const SstDev &d, const SstScalars *__restrict__ sc, bool need_t) {
     FwdScale f;
     f.gamma2 = d.relative ? sc->gamma2 : d.gamma2_abs;
     f.s1 = f.s2 = f.r1 = f.r2 = 1.f;
+    f.g_ub2 = 0.f;
     if (need_t) { f.s1 = sc->s1; f.s2 = sc->s2; f.r1 = sc->r1; f.r2 = sc->r2; }
     return f;
 }
@@ -324,17 +442,21 @@ __device__ __forceinline__ void tacc_take4(uint32_t *__restrict__ acc, int strid
 }
 
 // One frame m of the forward transform.  The T accumulators (tacc_stride(nbo) words x 4) must be
-// zero on entry and are zero again on return (MODE_T).
+// zero on entry and are zero again on return (MODE_T, MODE_SPEC).  MODE_SPEC
+// also needs sf (set up here for every frame) and the CTA's record cursor,
+// and folds max |S^g|^2 into *vmax.
 template <int NF, int MODE>
 __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
                                               float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
-                                              float2 *buf, uint32_t *acc, int tid) {
+                                              float2 *buf, uint32_t *acc, int tid, SpecFrame *sf = nullptr,
+                                              float *vmax = nullptr, SpecCursor *cur = nullptr) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     float2 v[16];
     forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);
     float2 *zc = buf, *zm = buf + d.nb;
     scatter_band<NF>(zc, zm, d, tid, v);
+    if (MODE == MODE_SPEC && tid == 0) sf->nmarg = 0;   // (sf may live in the frame buffer)
     __syncthreads();
 
 #pragma unroll
@@ -369,15 +491,29 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
                 reinterpret_cast<int32_t *>(out1)[o] = l;
                 continue;
             }
+            if (MODE == MODE_SPEC) {
+                *vmax = fmaxf(*vmax, mag2);
+                if (l >= 0 && !(mag2 > fs.g_ub2)) {
+                    // kept only if |S^g| exceeds the exact threshold: list it, flag its bin
+                    const int i = atomicAdd(&sf->nmarg, 1);
+                    if (i < SPEC_MCAP) sf->item[i] = make_float4(__int_as_float(l), V.x, V.y, mag2);
+                    continue;
+                }
+            }
             if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
         }
     }
     // all band reads and atomics done before the T row is read and the next
     // frame's first pass overwrites buf
     __syncthreads();
-    if (MODE != MODE_T) return;
+    if (MODE != MODE_T && MODE != MODE_SPEC) return;
     float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
-    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, tacc_stride(d.nbo), q, d.nbo, Trow, fs);
+    const int stride = tacc_stride(d.nbo);
+    if (MODE == MODE_SPEC && sf->nmarg > 0) {   // (block-uniform)
+        if (tid < 32) spec_records(d, sf, acc, m, tid, cur);
+        __syncthreads();   // records read the sums before they are cleared, and sf before the next FFT
+    }
+    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
     // the zeroing above is ordered before the next frame's atomics by the
     // __syncthreads inside the next frame's FFT
 }
@@ -393,12 +529,35 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
     // the T accumulators
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
     const int tid = threadIdx.x;
-    const FwdScale fs = fwd_scale(d, sc, MODE == MODE_T);
-    if (MODE == MODE_T)
-        for (int i = tid; i < 4 * tacc_stride(d.nbo); i += C::TPF) acc[i] = 0u;
+    if (d.gate && *d.gate == 0u) return;
+    FwdScale fs = fwd_scale(d, sc, MODE == MODE_T || MODE == MODE_SPEC);
+    if (MODE == MODE_SPEC) {
+        fs.gamma2 = sc->g_lb2;
+        fs.g_ub2 = sc->g_ub2;
+    }
+    const int stride = tacc_stride(d.nbo);
+    // MODE_SPEC state: in the frame buffer after the band values when it fits
+    // there (no extra shared memory, so no loss of occupancy), else after the
+    // accumulators
+    const size_t band_bytes = (16 * (size_t)d.nb + 15) & ~(size_t)15;
+    SpecFrame *sf = (spec_in_frame(d.nb, d.nbo, C::BUF))
+                        ? reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(buf) + band_bytes)
+                        : reinterpret_cast<SpecFrame *>(acc + 4 * stride);
+    if (MODE == MODE_T || MODE == MODE_SPEC)
+        for (int i = tid; i < 4 * stride; i += C::TPF) acc[i] = 0u;
+    float vmax = 0.f;
+    SpecCursor cur = {0u, 0u, 0u, 0u};
     // (the first __syncthreads in forward_frame orders this before any atomic)
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
-        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc, tid);
+        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc, tid, sf, &vmax, &cur);
+    if (MODE == MODE_SPEC) {
+        vmax = warp_max(vmax);
+        if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
+        if (tid == 0) {
+            spec_drop_src(d.spec, cur.src_cur, cur.src_end);
+            spec_drop_bin(d.spec, cur.bin_cur, cur.bin_end);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -898,7 +898,7 @@ static sst_status tc_scalars(sst_tc_plan_t t, const float *x, cudaStream_t st) {
                        "absx launch");
         SST_LAUNCHED_K(PK_GAMMA, st,
                        (k_gamma<<<1, 256, 0, st>>>(t->partial + 1, grid, t->base->gamma_frac2, 1, t->base->sum_abs_g,
-                                                   d.log2_nb, t->sc, nullptr),
+                                                   d.log2_nb, t->sc, nullptr, nullptr),
                         cudaGetLastError()),
                        "gamma launch");
     }

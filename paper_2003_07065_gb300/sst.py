@@ -14,6 +14,7 @@ import os
 from . import build as _build
 
 SST_GAMMA_RELATIVE = 0x1
+SST_TWO_PASS = 0x2
 STATUS = {0: "SST_OK", 1: "SST_EINVAL", 2: "SST_ENOMEM", 3: "SST_ECUDA", 4: "SST_EBUSY",
           5: "SST_ETIMEOUT", 6: "SST_EUNSUPPORTED", 7: "SST_EINTERNAL"}
 
@@ -71,6 +72,8 @@ def load():
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_threshold_stats": ([_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                 ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sst_tc_plan_create": ([_vp, ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
         "sst_tc_plan_destroy": ([_vp], None),
         "sst_tc_plan_query": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64),
@@ -151,7 +154,7 @@ def _stream(stream) -> int | None:
 
 
 # ------------------------------------------------------------------ C names
-def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg):
+def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass=False):
     p = sst_params()
     p.n, p.fs, p.L = int(n), float(fs), int(L)
     p.sigma = float(sigma) if sigma is not None else 0.0
@@ -166,16 +169,17 @@ def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg):
     p.hop, p.nfft = int(hop), int(nfft)
     p.f_lo, p.f_hi, p.z = float(f_lo), float(f_hi), int(z)
     p.gamma = float(gamma)
-    p.flags = SST_GAMMA_RELATIVE if relative else 0
+    p.flags = (SST_GAMMA_RELATIVE if relative else 0) | (SST_TWO_PASS if two_pass else 0)
     return p, keep
 
 
 def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
                     z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
-                    g=None, dg=None) -> int:
-    """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows."""
+                    g=None, dg=None, two_pass: bool = False) -> int:
+    """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows;
+    two_pass: SST_TWO_PASS (separate max|V| pre-pass for relative thresholds)."""
     lib = load()
-    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg)
+    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass)
     out = _vp()
     _check(lib.sst_plan_create(ctypes.byref(p), ctypes.byref(out)))
     del keep
@@ -280,6 +284,12 @@ def sst_tc_contract(tc, x, n, stream=None):
 
 def sst_tc_check(tc, stream=None):
     _check(load().sst_tc_check(tc, _stream(stream)))
+
+
+def sst_threshold_stats(plan, workspace) -> dict:
+    w, b, f = _i64(), _i64(), ctypes.c_int32()
+    _check(load().sst_threshold_stats(plan, _ptr(workspace), ctypes.byref(w), ctypes.byref(b), ctypes.byref(f)))
+    return {"waiting": w.value, "bins": b.value, "fell_back": bool(f.value)}
 
 
 def _items(items):

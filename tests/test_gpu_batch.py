@@ -1,9 +1,10 @@
 """Batched execution (many channels, uneven lengths, mixed hop / Nf / band /
 z / window class / threshold kind) through sst_batch_*: every channel's TFR
 and reconstruction must be bit-identical to the single-plan call on the same
-input (same arithmetic, deterministic sums), with and without the captured
-CUDA graph and after autotuning; two channels are also checked against the
-FP64 oracle."""
+input (same arithmetic, deterministic sums; relative thresholds from the
+separate max|V| pre-pass, i.e. plans made with SST_TWO_PASS), with and
+without the captured CUDA graph and after autotuning; two channels are also
+checked against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -50,7 +51,7 @@ def signal(p, seed):
 def setup(S):
     plans, xs, refs = [], [], []
     for i, p in enumerate(CHANNELS):
-        pl = S.Plan(**p)
+        pl = S.Plan(**p, two_pass=True)     # the batch's relative thresholds are two-pass
         x = torch.from_numpy(signal(p, i)).cuda()
         t, xh = pl.forward_inverse(x)
         plans.append(pl)
