@@ -209,9 +209,12 @@ void sst_tc_plan_destroy(sst_tc_plan_t tc);
  * multiply-adds x 2 of one contraction (all products of the form); cluster =
  * the CTAs that share each basis tile (sst_tc_plan_set_cluster). */
 sst_status sst_tc_plan_query(sst_tc_plan_t tc, int32_t *hankel_view, int64_t *gemm_flops, int32_t *cluster);
-/* CTAs per thread-block cluster in the contraction (1, 2 or 4): each CTA of a
- * cluster loads 1/cluster of the basis tile and multicasts it to the others.
- * Results do not depend on it.  SST_EUNSUPPORTED if no such cluster fits. */
+/* How the contraction's CTAs share operands.  1, 2 or 4: CTAs per cluster;
+ * each loads 1/cluster of the basis tile and multicasts it to the others
+ * (M = 128 products per SM).  0: CTA pairs issuing one M = 256 product across
+ * both SMs (tcgen05 cta_group::2), each SM loading its own rows and half of
+ * the basis tile.  Results agree to the accumulation's rounding.
+ * SST_EUNSUPPORTED if no such cluster fits. */
 sst_status sst_tc_plan_set_cluster(sst_tc_plan_t tc, int32_t cluster);
 /* Times the contraction on x_dev (n floats) with each cluster size that fits
  * (best of three after one untimed run, CUDA events on the stream), keeps the

@@ -134,6 +134,60 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// ---- CTA pairs (tcgen05 cta_group::2): one MMA of M = 256 rows across two SMs
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// load into this CTA's shared memory, completion counted on a barrier that
+// may live in the peer CTA (cluster address)
+__device__ __forceinline__ void tma_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cluster, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)map), "r"(bar_cluster), "r"(c0), "r"(c1)
+        : "memory");
+}
+template <bool TF32>
+__device__ __forceinline__ void mma_pair(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+// arrive on the barrier at this offset in both CTAs of the pair once the pair's products issued so far complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_acq_cluster(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *b, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_acq_cluster(b, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                  : "memory");
@@ -352,6 +406,194 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUte
     }
 }
 
+// Pair form of the contraction: a cluster of two CTAs computes 256 x 256
+// output tiles with one tcgen05.mma of M = 256 (cta_group::2) issued by the
+// even CTA; each CTA loads its own 128 rows of A and its 128 rows of the basis
+// tile (half of the N = 256 columns), so a stage is 32 KB per SM and six
+// stages fit.  Loads of both CTAs complete on the even CTA's barrier; the
+// products' completion is signalled to both CTAs (stage free, accumulator
+// ready); each CTA reads back its own 128 rows from its tensor memory and
+// tells the even CTA when the buffer is free.  Waits are bounded as in
+// k_tc_gemm.
+constexpr int P_STAGES = 6;
+constexpr int P_STAGE = A_TILE + B_TILE / 2;   // 32 KB per CTA
+constexpr size_t SMEM_PAIR = 1024 + (size_t)P_STAGES * P_STAGE + 256;
+
+template <bool TF32>
+__global__ void __launch_bounds__(THREADS, 1)
+k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+               const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, float *__restrict__ C,
+               int rows, int ldc, int vcols, int mtiles, int ntiles, int ktiles, int passes,
+               unsigned *__restrict__ maxbits, int *__restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + P_STAGES * P_STAGE);
+    uint64_t *empty = full + P_STAGES;
+    uint64_t *tfull = empty + P_STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *issued_s = (volatile int *)(tmem_slot + 1);
+    volatile int *consumed_s = issued_s + 1;
+    volatile int *failed_s = issued_s + 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rank = (int)cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = blockIdx.x >> 1, clusters = gridDim.x >> 1;
+    const int mpairs = mtiles >> 1;
+    const int tiles = mpairs * ntiles;
+    const int per_tile = ktiles * passes;
+    constexpr int KEL = TF32 ? 32 : 64;
+    constexpr uint32_t ID = (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) |
+                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+
+    if (tid == 0) {
+        for (int i = 0; i < P_STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);   // four read-back warps in each CTA of the pair
+        }
+        mbar_init(drain, 1);
+        *issued_s = 0;
+        *consumed_s = 0;
+        *failed_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(2 * TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();
+    fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer (both CTAs): own A rows and own half of the basis tile, counted on the even CTA's barrier
+        int it = 0;
+        bool ok = true;
+        for (int t = cid; t < tiles && ok; t += clusters) {
+            const int m0 = ((t % mpairs) * 2 + rank) * BM, n0 = (t / mpairs) * BN + rank * (BN / 2);
+            for (int j = 0; j < per_tile; ++j, ++it) {
+                const int s = it % P_STAGES;
+                if (it >= P_STAGES && !mbar_wait_cluster(&empty[s], ((it / P_STAGES) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    *failed_s = 1;
+                    ok = false;
+                    break;
+                }
+                const int pass = j / ktiles, kt = j % ktiles;
+                const CUtensorMap *ma = (pass == 2) ? &tmA1 : &tmA0;
+                const CUtensorMap *mb = (pass == 1) ? &tmB1 : &tmB0;
+                uint8_t *sa = smem + s * P_STAGE, *sb = sa + A_TILE;
+                if (leader) mbar_expect_tx(&full[s], 2 * P_STAGE);
+                const uint32_t fb = mapa(su32(&full[s]), 0);
+                tma_2d_pair(sa, ma, fb, kt * KEL, m0);
+                tma_2d_pair(sb, mb, fb, kt * KEL, n0);
+            }
+        }
+        *issued_s = it;
+    } else if (warp == 1 && lane == 0 && leader) {
+        // MMA issuer (even CTA)
+        int it = 0, lt = 0;
+        bool ok = true;
+        for (int t = cid; t < tiles && ok; t += clusters, ++lt) {
+            const int b = lt & 1;
+            if (lt >= 2 && !mbar_wait_cluster(&tempty[b], ((lt >> 1) & 1) ^ 1)) {
+                atomicOr(err, 2);
+                *failed_s = 1;
+                break;
+            }
+            fence_after();
+            const uint32_t dt = tbase + (uint32_t)(b * TMEM_COLS);
+            for (int j = 0; j < per_tile; ++j, ++it) {
+                const int s = it % P_STAGES;
+                if (!mbar_wait_cluster(&full[s], (it / P_STAGES) & 1)) {
+                    atomicOr(err, 4);
+                    *failed_s = 1;
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t sa = su32(smem + s * P_STAGE), sb = sa + A_TILE;
+#pragma unroll
+                for (int k = 0; k < KB / 32; ++k)
+                    mma_pair<TF32>(dt, sdesc(sa + 32 * k), sdesc(sb + 32 * k), ID, (j > 0 || k > 0) ? 1u : 0u);
+                mma_commit_pair(&empty[s]);
+            }
+            if (ok) mma_commit_pair(&tfull[b]);
+        }
+        *consumed_s = it;
+        __threadfence_block();
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(drain))
+                     : "memory");
+        if (!mbar_wait(drain, 0)) atomicOr(err, 8);
+    } else if (warp >= 2) {
+        // read-back (both CTAs): this CTA's 128 rows of the pair's tile
+        const int q = warp & 3;
+        float vmax = 0.f;
+        int lt = 0;
+        const uint32_t te0 = mapa(su32(&tempty[0]), 0), te1 = mapa(su32(&tempty[1]), 0);
+        for (int t = cid; t < tiles; t += clusters, ++lt) {
+            const int b = lt & 1;
+            int go = 0;
+            if (lane == 0) {
+                const bool okw = mbar_wait_cluster(&tfull[b], (lt >> 1) & 1);
+                if (!okw) atomicOr(err, 16);
+                go = (okw && *failed_s == 0) ? 1 : 0;
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
+            fence_after();
+            const int m0 = ((t % mpairs) * 2 + rank) * BM, n0 = (t / mpairs) * BN;
+            const int row = m0 + 32 * q + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tbase + (uint32_t)(b * TMEM_COLS) + ((uint32_t)(32 * q) << 16) + 32 * c, v);
+                if (row < rows) {
+                    float *dst = C + (size_t)row * ldc + n0 + 32 * c;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) st_v8(dst + 8 * i, &v[8 * i]);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (n0 + 32 * c + 4 * i < vcols) vmax = fmaxf(vmax, v[4 * i] * v[4 * i] + v[4 * i + 1] * v[4 * i + 1]);
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(b ? te1 : te0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0 && vmax > 0.f) atomicMax(maxbits, __float_as_uint(vmax));
+    }
+    fence_before();
+    __syncthreads();
+    // on an error, wait (bounded) for this CTA's loads issued but never consumed
+    // (the even CTA's barrier counts both CTAs' loads; only it can wait on them)
+    if (tid == 0 && leader && *issued_s > *consumed_s) {
+        for (int it = *consumed_s; it < *issued_s; ++it)
+            if (!mbar_wait(&full[it % P_STAGES], (it / P_STAGES) & 1)) {
+                atomicOr(err, 32);
+                break;
+            }
+    }
+    __syncthreads();
+    cluster_sync();   // no CTA leaves while its peer may still write to it or read its tensor memory
+    fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(2 * TMEM_COLS) : "memory");
+    }
+}
+
 // zero-padded signal for the Hankel rows: xp[q] = x[q - M] (0 outside [0, n)),
 // as BF16 hi and lo parts or as TF32 (rounded to nearest)
 __global__ void k_tc_prep_x(const float *__restrict__ x, int64_t n, int M, int64_t len, int tf32,
@@ -525,8 +767,8 @@ struct sst_tc_plan {
     SstScalars *sc = nullptr;
     CUtensorMap tA0, tA1;
     CUtensorMap tB[3][2];                    // basis (hi, lo) with a box of BN / CL rows, CL = 1, 2, 4
-    int cl = 1;                              // CTAs per cluster sharing the basis tile
-    int grid[3] = {0, 0, 0};                 // persistent grid per cluster size
+    int cl = 1;                              // CTAs per cluster sharing the basis tile; 0: CTA pairs
+    int grid[4] = {0, 0, 0, 0};              // persistent grid per variant (cluster 1, 2, 4, pair)
 };
 
 namespace {
@@ -534,20 +776,25 @@ namespace {
 typedef void (*GemmFn)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, float *, int, int,
                        int, int, int, int, int, unsigned *, int *);
 
+// cl: 1, 2, 4 (k_tc_gemm with that multicast cluster) or 0 (k_tc_gemm_pair)
 GemmFn gemm_fn(bool tf32, int cl) {
+    if (cl == 0) return tf32 ? k_tc_gemm_pair<true> : k_tc_gemm_pair<false>;
     if (tf32) return cl == 4 ? k_tc_gemm<true, 4> : cl == 2 ? k_tc_gemm<true, 2> : k_tc_gemm<true, 1>;
     return cl == 4 ? k_tc_gemm<false, 4> : cl == 2 ? k_tc_gemm<false, 2> : k_tc_gemm<false, 1>;
 }
+int variant_index(int cl) { return cl == 0 ? 3 : cl == 4 ? 2 : cl == 2 ? 1 : 0; }
+int variant_cl(int vi) { return vi == 3 ? 0 : 1 << vi; }
+int variant_ctas(int cl) { return cl == 0 ? 2 : cl; }    // CTAs per cluster
 
 cudaLaunchConfig_t gemm_config(int grid, int cl, cudaStream_t st, cudaLaunchAttribute *at) {
     cudaLaunchConfig_t cfg = {};
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.x = variant_ctas(cl);
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM;
+    cfg.dynamicSmemBytes = cl == 0 ? SMEM_PAIR : SMEM;
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -705,23 +952,26 @@ SST_API sst_status sst_tc_plan_create(sst_plan_t base, int32_t form, sst_tc_plan
         }
     }
     e = cudaSuccess;
-    for (int cl = 1; cl <= 4 && e == cudaSuccess; cl *= 2)
-        e = cudaFuncSetAttribute(gemm_fn(tf32, cl), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-    // persistent grids: one CTA per SM, whole clusters only, no more CTAs than tiles
+    for (int vi = 0; vi < 4 && e == cudaSuccess; ++vi) {
+        const int cl = variant_cl(vi);
+        e = cudaFuncSetAttribute(gemm_fn(tf32, cl), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(cl == 0 ? SMEM_PAIR : SMEM));
+    }
+    // persistent grids: one CTA per SM, whole clusters only, no more clusters than tiles
     const int mtiles = (int)(t->fpad / BM), ntiles = t->npad / BN;
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
-        const int cl = 1 << ci;
-        int clusters = base->num_sms / cl;
-        if (cl > 1) {
+    for (int vi = 0; vi < 4 && e == cudaSuccess; ++vi) {
+        const int cl = variant_cl(vi), ctas = variant_ctas(cl);
+        int clusters = base->num_sms / ctas;
+        if (ctas > 1) {
             cudaLaunchAttribute at[1];
-            cudaLaunchConfig_t cfg = gemm_config(cl * clusters, cl, nullptr, at);
+            cudaLaunchConfig_t cfg = gemm_config(ctas * clusters, cl, nullptr, at);
             int active = 0;
             e = cudaOccupancyMaxActiveClusters(&active, gemm_fn(tf32, cl), &cfg);
             if (e != cudaSuccess) break;
             clusters = std::min(clusters, active);
         }
-        clusters = std::min(clusters, (mtiles / cl) * ntiles);
-        t->grid[ci] = std::max(clusters, 0) * cl;
+        clusters = std::min(clusters, (mtiles / ctas) * ntiles);
+        t->grid[vi] = std::max(clusters, 0) * ctas;
     }
     t->cl = 1;
     // the epilogue's accumulators and row buffers; the limit is only ever
@@ -799,11 +1049,12 @@ static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) 
     const int ktiles = t->kpad / (KB / (tf32 ? 4 : 2));
     const int passes = t->form == SST_FORM_BF16X3 ? 3 : 1;
     const int mtiles = (int)(t->fpad / BM), ntiles = t->npad / BN;
-    const int ci = t->cl == 4 ? 2 : t->cl == 2 ? 1 : 0;
+    const int vi = variant_index(t->cl);
+    const int bi = t->cl == 0 ? 1 : (t->cl == 4 ? 2 : t->cl == 2 ? 1 : 0);   // basis box: BN / (CTAs sharing it)
     cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg = gemm_config(t->grid[ci], t->cl, st, at);
+    cudaLaunchConfig_t cfg = gemm_config(t->grid[vi], t->cl, st, at);
     SST_LAUNCHED_K(PK_STFT, st,
-                   cudaLaunchKernelEx(&cfg, gemm_fn(tf32, t->cl), t->tA0, t->tA1, t->tB[ci][0], t->tB[ci][1], t->C,
+                   cudaLaunchKernelEx(&cfg, gemm_fn(tf32, t->cl), t->tA0, t->tA1, t->tB[bi][0], t->tB[bi][1], t->C,
                                       (int)d.F, t->npad, t->ncols, mtiles, ntiles, ktiles, passes,
                                       (unsigned *)t->partial, t->err),
                    "tensor contraction");
@@ -823,12 +1074,12 @@ SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t
         return fail(SST_ECUDA, "event");
     }
     const int keep = t->cl;
-    int best = 0;
+    int best = -1;
     float best_ms = 0.f;
     sst_status s = SST_OK;
-    for (int ci = 0; ci < 3 && s == SST_OK; ++ci) {
-        if (t->grid[ci] <= 0) continue;
-        t->cl = 1 << ci;
+    for (int vi = 0; vi < 4 && s == SST_OK; ++vi) {
+        if (t->grid[vi] <= 0) continue;
+        t->cl = variant_cl(vi);
         float ms = 0.f;
         // one untimed run, then the best of three
         for (int r = 0; r < 4 && s == SST_OK; ++r) {
@@ -843,8 +1094,8 @@ SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t
             cudaEventElapsedTime(&e, a, b);
             if (r == 1 || (r > 1 && e < ms)) ms = e;
         }
-        if (s == SST_OK && (best == 0 || ms < best_ms)) {
-            best = 1 << ci;
+        if (s == SST_OK && (best < 0 || ms < best_ms)) {
+            best = t->cl;
             best_ms = ms;
         }
     }
@@ -858,7 +1109,7 @@ SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t
         t->cl = keep;
         return s;
     }
-    t->cl = best ? best : keep;
+    t->cl = best >= 0 ? best : keep;
     if (cluster) *cluster = t->cl;
     if (ms_out) *ms_out = best_ms;
     return SST_OK;
@@ -866,9 +1117,10 @@ SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t
 
 SST_API sst_status sst_tc_plan_set_cluster(sst_tc_plan_t t, int32_t cluster) {
     if (!t) return fail(SST_EINVAL, "plan is NULL");
-    if (cluster != 1 && cluster != 2 && cluster != 4) return fail(SST_EINVAL, "cluster must be 1, 2 or 4");
-    const int ci = cluster == 4 ? 2 : cluster == 2 ? 1 : 0;
-    if (t->grid[ci] <= 0) return fail(SST_EUNSUPPORTED, "no cluster of %d CTAs fits this device", cluster);
+    if (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4)
+        return fail(SST_EINVAL, "cluster must be 1, 2, 4 (multicast) or 0 (CTA pairs)");
+    if (t->grid[variant_index(cluster)] <= 0)
+        return fail(SST_EUNSUPPORTED, "no cluster of this kind (%d) fits this device", cluster);
     t->cl = cluster;
     return SST_OK;
 }

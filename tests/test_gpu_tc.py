@@ -252,3 +252,37 @@ def test_cluster_sizes_identical(sst, form):
     for cl, V, Vd, T in outs[1:]:
         assert torch.equal(V, outs[0][1]) and torch.equal(Vd, outs[0][2]) and torch.equal(T, outs[0][3]), cl
     plan.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pair_variant(sst, form):
+    """The CTA-pair contraction (tcgen05 cta_group::2, M = 256 across two SMs)
+    meets the same derived bounds against the oracle on the precision
+    workload."""
+    w = W.PRECISION_64K
+    noisy, clean = w.signal()
+    x32 = noisy.astype(np.float32)
+    params = w.params()
+    r = oracle_of(params, x32)
+    plan = sst.Plan(**params)
+    h = plan._tc_handle(form)
+    try:
+        sst.sst_tc_plan_set_cluster(h, 0)
+    except sst.SstError as e:
+        assert e.status == 6
+        pytest.skip("no CTA pair fits")
+    x = torch.from_numpy(x32).cuda()
+    V, Vd = plan.tc_stft(x, form)
+    om, dest = plan.tc_reassign_map(x, form)
+    tfr = plan.tc_forward(x, form)
+    xhat = plan.inverse(tfr)
+    sst.sst_tc_plan_set_cluster(h, 1)
+    V1, _ = plan.tc_stft(x, form)
+    torch.cuda.synchronize()
+    g = dict(V=as_complex(V.cpu().numpy()), Vd=as_complex(Vd.cpu().numpy()), omega=om.cpu().numpy(),
+             dest=dest.cpu().numpy().astype(np.int64), T=as_complex(tfr.cpu().numpy()),
+             xhat=xhat.cpu().numpy().astype(np.float64))
+    st = check_form(g, r, params, x32.astype(np.float64), form, clean)
+    st["same_as_cluster1"] = bool(torch.equal(V, V1))
+    print("pair", form, {k: (f"{v:.3e}" if isinstance(v, float) else v) for k, v in st.items()})
+    plan.close()
