@@ -141,9 +141,10 @@ def measured_traffic_per_frame(kernel: str):
         return None
     with open(p) as f:
         rec = json.load(f)
+    # the files that define the FFT-path kernels (device code, launch shapes)
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2003_07065_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in rec.get("kernel_sources", []):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     if h.hexdigest() != rec.get("kernel_source_sha256"):
@@ -158,12 +159,28 @@ def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
 
 
 # ------------------------------------------------------------------ reference arm
-def oracle_sample_rate(w, budget_s: float = 15.0):
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() in ("model name", "cpu model", "hardware"):
+                    return v.strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample_rate(w, budget_s: float = 15.0, n_max: int = 1 << 15):
     """Run the FP64 oracle on a bounded prefix of the workload's signal (the
     whole path: STFTs, IF, reassignment, inverse) and return samples/s."""
     import oracle as O
     noisy, _ = w.signal()
-    n_sample = min(w.n, 1 << 15)
+    n_sample = min(w.n, n_max)
     x = noisy[:n_sample].astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     reps = 0
@@ -174,7 +191,7 @@ def oracle_sample_rate(w, budget_s: float = 15.0):
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= 64:
             break
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = O.get_threads()
     return reps * n_sample / el, threads, f"{reps} x first {n_sample} samples of {w.name}", el
 
 
@@ -184,6 +201,7 @@ def run_reference(args, w):
         return 0
     import oracle as O
     O.build()
+    O.set_threads(0)
     vals = []
     for _ in range(args.warmup):
         oracle_sample_rate(w, budget_s=0.0)
@@ -197,7 +215,8 @@ def run_reference(args, w):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "nfft": w.nfft, "hop": w.hop, "L": w.L, "z": w.z,
                    "band_hz": [w.f_lo, w.f_hi]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -629,24 +648,34 @@ def main():
         flops = fl[dom] * units
         achieved = flops / (per_launch_ms / 1e3) / 1e12
         sm_max = peaks.get("sm_max_mhz") or 2070.0
-        peak = fp32_peak_tflops(num_sms, sm_max)
+        nominal = fp32_peak_tflops(num_sms, sm_max)
+        peak = sst.sst_fp32_peak(stream)
         tpf = measured_traffic_per_frame(dom)
+        step_flops = sum(fl[k] for k in ("forward", "inverse")) * units
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tpf * units if tpf is not None else None),
                 "traffic_note": "ncu dram__bytes_read+write of one runup_4m launch scaled by frames",
-                "peak_note": f"FP32 FMA peak {num_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max clock)",
+                "peak_note": ("FP32 FMA throughput measured in this run (sst_fp32_peak: independent fmaf "
+                              f"chains); nominal {nominal:.1f} = {num_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"),
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
                 "hbm_gbs_achieved": by[dom] * units / (per_launch_ms / 1e3) / 1e9,
-                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+                "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                "fused_step": {"algorithmic_flops": step_flops, "achieved": step_flops / (t_ms / args.steps / 1e3) / 1e12,
+                               "frac": step_flops / (t_ms / args.steps / 1e3) / 1e12 / peak}}
 
     kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        v, threads, sample, el = oracle_sample_rate(w, budget_s=12.0)
+        O.set_threads(0)
+        v, threads, sample, el = oracle_sample_rate(w, budget_s=10.0)
+        O.set_threads(1)
+        v1, _, sample1, el1 = oracle_sample_rate(w, budget_s=5.0, n_max=1 << 13)
+        O.set_threads(0)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
-               "seconds": el}
+               "seconds": el, "cpu_model": cpu_model(),
+               "single_thread": {"value": v1, "sample": sample1, "seconds": el1}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,

@@ -150,6 +150,12 @@ sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, floa
 sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev,
                          void *workspace_dev, void *stream);
 
+/* FP32 fused multiply-add throughput of the current device in TFLOP/s (2
+ * FLOP per FMA), measured with eight independent fmaf chains per thread at
+ * full occupancy: the denominator of an FP32 roofline.  Allocates 256 bytes,
+ * launches three ~1 ms kernels on the stream and synchronises. */
+sst_status sst_fp32_peak(double *tflops, void *stream);
+
 /* The last sst_forward / sst_forward_inverse of a relative plan with the
  * one-pass threshold (the default): how many sources waited for the exact
  * threshold, how many fine bins they fell in, and whether a record buffer

@@ -71,6 +71,10 @@ def _load():
     for name in ("oro_hf_max_rule1", "oro_hf_max_rule2"):
         getattr(lib, name).argtypes = [ctypes.c_double] * 3
         getattr(lib, name).restype = ctypes.c_double
+    lib.oro_set_threads.argtypes = [_int]
+    lib.oro_set_threads.restype = None
+    lib.oro_get_threads.argtypes = []
+    lib.oro_get_threads.restype = _int
     lib.oro_delta_f.argtypes = [ctypes.c_double, _int, _int]
     lib.oro_delta_f.restype = ctypes.c_double
     _lib = lib
@@ -92,6 +96,19 @@ def _cx(a: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- primitives
+def set_threads(n: int) -> int:
+    """OpenMP threads for the oracle's frame loops (0: all cores); returns the
+    count now in effect.  Timing only: the results do not depend on it."""
+    lib = _load()
+    lib.oro_set_threads(int(n))
+    return int(lib.oro_get_threads())
+
+
+def get_threads() -> int:
+    """OpenMP threads the oracle's frame loops use."""
+    return int(_load().oro_get_threads())
+
+
 def window(L: int, sigma: float):
     """Gaussian g (Sec. 2.1) and g' (Sec. 2.2) on j = -M..M, sigma in samples."""
     lib = _load()

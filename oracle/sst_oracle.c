@@ -356,6 +356,16 @@ int oro_colsum(const double *T, int64_t nm, int k_lo, int nbo, int nfft, int z, 
 /*   Eq. 46  Delta f < sqrt(2) sigma_f, i.e. Hf < sqrt(2) sigma_f N / fs     */
 /*   Eq. 12 / 28  Delta f = fs / Nf, subdivided Delta f* = fs / (z Nf)        */
 /* ------------------------------------------------------------------------ */
+/* Threads the OpenMP loops above may use (timing only; results do not depend on it). */
+#ifdef _OPENMP
+#include <omp.h>
+void oro_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+int oro_get_threads(void) { return omp_get_max_threads(); }
+#else
+void oro_set_threads(int n) { (void)n; }
+int oro_get_threads(void) { return 1; }
+#endif
+
 double oro_sigma_f(double sigma_s) { return 1.0 / (2.0 * ORO_PI * sigma_s); }
 double oro_hf_max_rule1(double n, double sigma_s, double fs) { return 3.0 * n / (4.0 * ORO_PI * sigma_s * fs); }
 double oro_hf_max_rule2(double n, double sigma_s, double fs) { return sqrt(2.0) * oro_sigma_f(sigma_s) * n / fs; }

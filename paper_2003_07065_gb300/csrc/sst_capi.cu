@@ -836,6 +836,55 @@ SST_API sst_status sst_threshold_stats(sst_plan_t plan, const void *ws, int64_t 
     return SST_OK;
 }
 
+// FP32 FMA throughput probe: eight independent fmaf chains per thread, full
+// occupancy; the result is kept live by a store that never happens.
+__global__ void __launch_bounds__(256) k_ffma_chains(float *__restrict__ out, int iters, float seed) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + (float)(threadIdx.x + j);
+    const float m = 0.99999994f, c = 1.0e-7f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], m, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += a[j];
+    if (t == 12345.678f) out[0] = t;
+}
+
+SST_API sst_status sst_fp32_peak(double *tflops, void *stream) {
+    if (!tflops) return fail(SST_EINVAL, "output pointer is NULL");
+    int dev = 0, sms = 0;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    SST_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attributes");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *out = nullptr;
+    SST_CU(cudaMalloc(&out, 256), "probe buffer");
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int blocks = sms * 8, iters = 16384;
+    float ms = 0.f;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {   // the last of three launches is timed
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) {
+            k_ffma_chains<<<blocks, 256, 0, st>>>(out, iters, 1.0f + r);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        count_launch();
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "FP32 probe");
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+    return SST_OK;
+}
+
 SST_API sst_status sst_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");

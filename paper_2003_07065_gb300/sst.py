@@ -72,6 +72,7 @@ def load():
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_fp32_peak": ([ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
         "sst_threshold_stats": ([_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sst_tc_plan_create": ([_vp, ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
@@ -284,6 +285,13 @@ def sst_tc_contract(tc, x, n, stream=None):
 
 def sst_tc_check(tc, stream=None):
     _check(load().sst_tc_check(tc, _stream(stream)))
+
+
+def sst_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().sst_fp32_peak(ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def sst_threshold_stats(plan, workspace) -> dict:
