@@ -305,6 +305,12 @@ sst_status sst_service_create(int32_t max_streams, size_t mem_budget_bytes, sst_
  * max_chunk bounds one push.  SST_EBUSY when no slot or budget is left. */
 sst_status sst_stream_open(sst_service_t svc, const sst_params *params, float amp_bound, int64_t max_chunk,
                            int32_t *stream_id);
+/* params->flags bit for sst_stream_open: deliver only the reconstruction;
+ * the TFR columns stay on the device (ring) and are not copied to the host
+ * (sst_stream_poll then returns no columns).  For services whose clients
+ * want x-hat only: a TFR column is (zN_r + 1) complex values per hop, i.e.
+ * 8 (zN_r + 1) / H bytes of host traffic per input sample. */
+#define SST_STREAM_XHAT_ONLY 0x100u
 /* Queue a host chunk (copied).  t_arrival: seconds on CLOCK_MONOTONIC (e.g.
  * Python time.monotonic()), or negative for "now"; latency = completion of
  * the tick that consumed the chunk minus t_arrival.  SST_EBUSY if more than

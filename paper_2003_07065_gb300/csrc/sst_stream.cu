@@ -41,6 +41,7 @@ struct Stream {
     std::vector<double> g;           // FP64 window, for the edge normalisers at close
     float amp_bound = 0.f;
     int64_t max_chunk = 0;
+    bool xhat_only = false;          // TFR columns are not copied to the host
     // device state (one allocation)
     void *dmem = nullptr;
     size_t dev_bytes = 0;
@@ -180,6 +181,8 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
     // the plan supplies the tables; its own length only sizes its edge tables
     sst_params p = *params;
     p.n = 4 * (int64_t)p.L;
+    const bool xhat_only = (p.flags & SST_STREAM_XHAT_ONLY) != 0;
+    p.flags &= ~SST_STREAM_XHAT_ONLY;
     sst_plan_t plan = nullptr;
     sst_status st = sst_plan_create(&p, &plan);
     if (st != SST_OK) return st;
@@ -188,6 +191,7 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
     S.base = plan->d;
     S.amp_bound = amp_bound;
     S.max_chunk = max_chunk;
+    S.xhat_only = xhat_only;
     SstDev &d = S.base;
     const int M = d.M, H = d.hop;
     // sizes: signal tail + a burst of pending data, twice over so compaction never overlaps
@@ -493,7 +497,7 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
     size_t out_bytes = 0;
     for (auto &w : work) {
         Stream &S = sv->s[w.id];
-        out_bytes += a256(sizeof(float2) * (size_t)(w.m_ready - S.m_next) * S.base.nbo) +
+        out_bytes += (S.xhat_only ? 0 : a256(sizeof(float2) * (size_t)(w.m_ready - S.m_next) * S.base.nbo)) +
                      a256(sizeof(float) * (size_t)(w.p_ready - S.p_next));
     }
     SST_CU(cudaStreamSynchronize(st), "tick");
@@ -505,7 +509,7 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
         Stream &S = sv->s[work[i].id];
         const int nbo = S.base.nbo;
         const size_t o_t = o;
-        for (int64_t m = S.m_next; m < work[i].m_ready;) {
+        for (int64_t m = S.m_next; m < work[i].m_ready && !S.xhat_only;) {
             const int64_t r = m % S.trow_cap;
             const int64_t cnt = std::min<int64_t>(work[i].m_ready - m, S.trow_cap - r);
             SST_CU(cudaMemcpyAsync(sv->pin + o, S.T + (size_t)r * nbo, sizeof(float2) * (size_t)cnt * nbo,
@@ -528,7 +532,7 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
         const int nbo = S.base.nbo;
         const int64_t rows = work[i].m_ready - S.m_next;
         const float *tp = (const float *)(sv->pin + where[i].first);
-        S.tfr_host.insert(S.tfr_host.end(), tp, tp + 2 * (size_t)rows * nbo);
+        if (!S.xhat_only) S.tfr_host.insert(S.tfr_host.end(), tp, tp + 2 * (size_t)rows * nbo);
         const float *xp = (const float *)(sv->pin + where[i].second);
         S.x_host.insert(S.x_host.end(), xp, xp + (work[i].p_ready - S.p_next));
         for (double ta : work[i].arrivals) sv->lat.push_back(t_done - ta);

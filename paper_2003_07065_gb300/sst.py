@@ -15,6 +15,7 @@ from . import build as _build
 
 SST_GAMMA_RELATIVE = 0x1
 SST_TWO_PASS = 0x2
+SST_STREAM_XHAT_ONLY = 0x100
 STATUS = {0: "SST_OK", 1: "SST_EINVAL", 2: "SST_ENOMEM", 3: "SST_ECUDA", 4: "SST_EBUSY",
           5: "SST_ETIMEOUT", 6: "SST_EUNSUPPORTED", 7: "SST_EINTERNAL"}
 
@@ -363,9 +364,12 @@ def sst_service_create(max_streams: int, mem_budget: int) -> int:
 
 def sst_stream_open(svc, amp_bound: float, max_chunk: int, fs: float, L: int, hop: int, nfft: int,
                     f_lo: float, f_hi: float, z: int = 1, gamma: float = 0.0, sigma: float | None = None,
-                    g=None, dg=None) -> int:
-    """Open a stream (absolute threshold gamma); returns its id."""
+                    g=None, dg=None, xhat_only: bool = False) -> int:
+    """Open a stream (absolute threshold gamma); returns its id.  xhat_only:
+    SST_STREAM_XHAT_ONLY (TFR columns stay on the device)."""
     p, keep = _params(0, fs, L, hop, nfft, f_lo, f_hi, z, gamma, False, sigma, g, dg)
+    if xhat_only:
+        p.flags |= SST_STREAM_XHAT_ONLY
     sid = ctypes.c_int32()
     _check(load().sst_stream_open(svc, ctypes.byref(p), float(amp_bound), int(max_chunk), ctypes.byref(sid)))
     del keep
@@ -386,18 +390,23 @@ def sst_service_tick(svc):
     _check(load().sst_service_tick(svc))
 
 
+_poll_bufs = {}
+
+
 def sst_stream_poll(svc, sid: int, bins: int, max_cols: int = 4096, max_samples: int = 1 << 17):
-    """Returns (tfr [cols, bins] complex64, first_col, xhat float32, first_sample, finished)."""
+    """Returns (tfr [cols, bins] complex64, first_col, xhat float32, first_sample, finished).
+    The host staging buffers are reused across calls (one pair per shape)."""
     import numpy as np
-    t = np.empty((max_cols, bins, 2), dtype=np.float32)
-    x = np.empty(max_samples, dtype=np.float32)
+    key = (bins, max_cols, max_samples)
+    if key not in _poll_bufs:
+        _poll_bufs[key] = (np.empty((max_cols, bins, 2), dtype=np.float32), np.empty(max_samples, dtype=np.float32))
+    t, x = _poll_bufs[key]
     cols, fc, ns, fs_, fin = _i64(), _i64(), _i64(), _i64(), ctypes.c_int32()
     _check(load().sst_stream_poll(svc, int(sid), t.ctypes.data, max_cols, ctypes.byref(cols), ctypes.byref(fc),
                                   x.ctypes.data, max_samples, ctypes.byref(ns), ctypes.byref(fs_),
                                   ctypes.byref(fin)))
-    tc = t[:cols.value]
-    return (tc[..., 0] + 1j * tc[..., 1]).astype(np.complex64), fc.value, x[:ns.value].copy(), fs_.value, \
-        bool(fin.value)
+    tc = t[:cols.value].view(np.complex64)[..., 0].copy()
+    return tc, fc.value, x[:ns.value].copy(), fs_.value, bool(fin.value)
 
 
 def sst_stream_release(svc, sid: int):
