@@ -55,12 +55,12 @@ def drain(S, svc, sid, nb, acc):
             return fin
 
 
-def run_streams(S, signals, seed, budget=8 << 30):
+def run_streams(S, signals, seed, budget=8 << 30, xhat_only=False):
     """Push each signal in random chunks, interleaving streams and ticks."""
     gen = np.random.default_rng(seed)
     svc = S.sst_service_create(16, budget)
     nb = bins_of(S)
-    ids = [S.sst_stream_open(svc, 8.0, MAXC, **P) for _ in signals]
+    ids = [S.sst_stream_open(svc, 8.0, MAXC, xhat_only=xhat_only, **P) for _ in signals]
     pos = [0] * len(signals)
     acc = [([], []) for _ in signals]
     while any(p < len(x) for p, x in zip(pos, signals)):
@@ -83,7 +83,7 @@ def run_streams(S, signals, seed, budget=8 << 30):
         if all(done):
             break
     assert all(done)
-    out = [(np.concatenate(a[0]), np.concatenate(a[1])) for a in acc]
+    out = [(np.concatenate(a[0]) if a[0] else None, np.concatenate(a[1])) for a in acc]
     S.sst_service_destroy(svc)
     return out
 
@@ -95,6 +95,16 @@ def test_stream_alone_equals_mix(sst):
         alone = run_streams(sst, [x], seed=100 + i)[0]
         assert np.array_equal(alone[0], mixed[i][0]), f"stream {i}: TFR differs alone vs mix"
         assert np.array_equal(alone[1], mixed[i][1]), f"stream {i}: reconstruction differs alone vs mix"
+
+
+def test_stream_xhat_only(sst):
+    """Reconstruction-only streams deliver no TFR columns and the same x-hat."""
+    signals = [sig(n, i) for i, n in enumerate((30000, 12345))]
+    full = run_streams(sst, signals, seed=9)
+    xo = run_streams(sst, signals, seed=9, xhat_only=True)
+    for (t, x), (t2, x2) in zip(full, xo):
+        assert t is not None and t2 is None
+        assert np.array_equal(x, x2)
 
 
 def test_stream_equals_whole_signal(sst):
