@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sst_async.cuh"
 #include "sst_dev.h"
 #include "sst_fft.cuh"
 
@@ -594,13 +595,23 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    // staged rows: Tst[f][s][q] = w T_f[z q + s], q in [0, nq), nq = N_r + 1
+    // staged rows.  Synchronous staging: Tst[f][s][q] = w T_f[z q + s], q in
+    // [0, nq), nq = N_r + 1 (regrouped by sub-grid, DC / Nyquist weight
+    // applied).  Asynchronous staging (rows of the tile contiguous and 16-byte
+    // aligned): the pair's two rows as they are in T, raw[f nbo + l], one bulk
+    // copy per pair, the next pair's copy issued as soon as the current pair's
+    // last spectrum is built, so it lands while that sub-grid's FFT runs.
     const int nq = d.k_hi - d.k_lo + 1;
     float2 *Tst = buf + C::BUF;
     float *seg = reinterpret_cast<float *>(Tst + 2 * d.z * nq);
+    // (the frame buffer's 128 bytes of slack are at the end of the allocation)
+    uint64_t *rbar = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(seg + d.seg_len) + 15) & ~(uintptr_t)15);
     const int64_t m0 = tile * d.B;
     const float cnorm = 1.0f / (float)NF;
     const bool live = (TPF == NS) || tid < NS;
+    const uint32_t pair_bytes = 16u * (uint32_t)d.nbo;
+    const float2 *tile_rows = T + (size_t)m0 * d.nbo;
+    bool async = d.trow_cap == 0 && m0 + d.B <= d.F && (reinterpret_cast<uintptr_t>(tile_rows) & 15) == 0;
 
     // per-thread taps of the last pass: n_i = q or q - NF, window g[n_i + M]
     int tap[TP::NACC];
@@ -618,14 +629,35 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     }
 
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
+    if (async && tid == 0) {
+        mbar_init(rbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (async && tid == 0) {
+        mbar_expect_tx(rbar, pair_bytes);
+        bulk_g2s(Tst, tile_rows, pair_bytes, rbar);
+    }
 
     for (int pr = 0; pr < d.B / 2; ++pr) {
         const int64_t a = m0 + 2 * pr, b = a + 1;
         if (a >= d.F) break;
         const bool hasb = b < d.F;
-        // stage both rows (contiguous in T), regrouped by sub-grid, with the
-        // 1/2 weight of the DC and Nyquist destinations (Hermitian completion)
-        for (int f = 0; f < 2; ++f) {
+        if (async) {
+            // this pair's rows: bounded wait; if it ever expired, wait once more
+            // (so no copy is left in flight) and stage the rest synchronously
+            int ok = 1;
+            if (tid == 0) {
+                ok = mbar_wait(rbar, (uint32_t)(pr & 1)) ? 1 : 0;
+                if (!ok) mbar_wait(rbar, (uint32_t)(pr & 1));
+            }
+            ok = __syncthreads_and(ok);
+            if (!ok) async = false;
+        }
+        // synchronous staging: both rows (contiguous in T), regrouped by
+        // sub-grid, with the 1/2 weight of the DC and Nyquist destinations
+        // (Hermitian completion)
+        for (int f = 0; f < 2 && !async; ++f) {
             const float2 *src = T + (size_t)trow_of(d, a + f) * d.nbo;
             const bool have = f == 0 || hasb;
             for (int q = tid; q < nq; q += TPF) {
@@ -650,8 +682,11 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             const int dl = (s == 0) ? 0 : 1;
             const int nqs = (s == 0) ? nq : nq - 1;     // sub-grid s holds q in [0, nqs)
             const int nqb = (sb == 0) ? nq : nq - 1;
-            const float2 *Ta = Tst + s * nq, *Tam = Tst + sb * nq;
-            const float2 *Tb = Tst + (d.z + s) * nq, *Tbm = Tst + (d.z + sb) * nq;
+            // element q of sub-grid s of row f: staged Tst[(f z + s) nq + q], raw Tst[f nbo + z q + s]
+            const int qstride = async ? d.z : 1;
+            const float2 *Ta = Tst + (async ? s : s * nq), *Tam = Tst + (async ? sb : sb * nq);
+            const float2 *Tb = Tst + (async ? d.nbo + s : (d.z + s) * nq);
+            const float2 *Tbm = Tst + (async ? d.nbo + sb : (d.z + sb) * nq);
             // first pass with the spectrum built in registers:
             // Y_s[k] = (1/NF) (X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl]))
             // Input k = j + r NF/R1 reads q = k - k_lo and, for the image,
@@ -676,12 +711,20 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                     const bool hm = jok && (unsigned)qm < (unsigned)nqb;
                     if (__any_sync(0xffffffffu, hd || hm)) {
                         if (hd) {
-                            const float2 xa = Ta[q], xb = Tb[q];
+                            float2 xa = Ta[q * qstride], xb = Tb[q * qstride];
+                            if (async && s == 0 && (d.k_lo + q == 0 || 2 * (d.k_lo + q) == NF)) {
+                                xa = cscale(xa, 0.5f);
+                                xb = cscale(xb, 0.5f);
+                            }
                             y.x += xa.x - xb.y;
                             y.y += xa.y + xb.x;
                         }
                         if (hm) {
-                            const float2 xa = Tam[qm], xb = Tbm[qm];
+                            float2 xa = Tam[qm * qstride], xb = Tbm[qm * qstride];
+                            if (async && sb == 0 && (d.k_lo + qm == 0 || 2 * (d.k_lo + qm) == NF)) {
+                                xa = cscale(xa, 0.5f);
+                                xb = cscale(xb, 0.5f);
+                            }
                             // conj(xa) + i conj(xb)
                             y.x += xa.x + xb.y;
                             y.y += -xa.y + xb.x;
@@ -692,6 +735,11 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             }
             fft_first_from_regs<NF, TPF, true>(buf, u, tid);
             __syncthreads();
+            // the pair's rows are read for the last time above: fetch the next pair's
+            if (async && s == d.z - 1 && tid == 0 && 2 * (pr + 1) < d.B) {
+                mbar_expect_tx(rbar, pair_bytes);
+                bulk_g2s(Tst, tile_rows + (size_t)2 * (pr + 1) * d.nbo, pair_bytes, rbar);
+            }
             fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
             float2 v[16];
             fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);

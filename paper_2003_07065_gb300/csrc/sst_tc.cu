@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "sst_internal.h"
+#include "sst_async.cuh"
 #include "sst_kernels.cuh"
 
 namespace sst {
@@ -39,33 +40,7 @@ constexpr int B_TILE = BN * KB;              // 32 KB
 constexpr int STAGE = A_TILE + B_TILE;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
 constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait on a phase; false when the cycle budget runs out
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try(b, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
-}
 
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
     asm volatile(
@@ -623,14 +598,6 @@ __global__ void k_tc_hankel(const T *__restrict__ xp, int hop, int64_t rows, int
         const int64_t m = i / kpad, j = i % kpad;
         A[i] = xp[m * hop + j];
     }
-}
-
-// 1-D bulk copy global -> shared, completion counted on an mbarrier
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     su32(dst)),
-                 "l"(src), "r"(bytes), "r"(su32(bar))
-                 : "memory");
 }
 
 // per frame: the FFT form's epilogue on the contraction's S^g, S^g' (MODE_T,
