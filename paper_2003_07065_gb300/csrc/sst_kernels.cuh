@@ -625,7 +625,9 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
         else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
         const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
         tap[i] = ok ? n : INT_MIN;
-        gw[i] = ok ? __ldg(&d.g[n + d.M]) : 0.f;
+        // the inverse DFT's 1 / NF (a power of two, so exact) is applied here,
+        // once per tap, instead of to every spectrum input
+        gw[i] = ok ? __ldg(&d.g[n + d.M]) * cnorm : 0.f;
     }
 
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
@@ -687,8 +689,8 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             const float2 *Ta = Tst + (async ? s : s * nq), *Tam = Tst + (async ? sb : sb * nq);
             const float2 *Tb = Tst + (async ? d.nbo + s : (d.z + s) * nq);
             const float2 *Tbm = Tst + (async ? d.nbo + sb : (d.z + sb) * nq);
-            // first pass with the spectrum built in registers:
-            // Y_s[k] = (1/NF) (X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl]))
+            // first pass with the spectrum built in registers (the 1/NF is in gw):
+            // Y_s[k] = X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl])
             // Input k = j + r NF/R1 reads q = k - k_lo and, for the image,
             // qm = ((NF - k - dl) mod NF) - k_lo = (NF - dl - j - k_lo) - r NF/R1,
             // except at k = 0 with dl = 0 (qm = -k_lo).  The band is a small part
@@ -730,7 +732,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                             y.y += -xa.y + xb.x;
                         }
                     }
-                    u[bb][r] = cscale(y, cnorm);
+                    u[bb][r] = y;
                 }
             }
             fft_first_from_regs<NF, TPF, true>(buf, u, tid);
