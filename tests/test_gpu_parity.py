@@ -148,3 +148,20 @@ def test_plan_errors(sst):
     with pytest.raises(sst.SstError):
         sst.sst_forward(p.handle, x, 999, p.new_tfr(), p.workspace)
     p.close()
+
+
+def test_inverse_unaligned_rows(sst):
+    """T rows at an address that is not 16-byte aligned take the synchronous
+    staging path of the inverse; the result is the same."""
+    w = W.CHIRP_FM_64K
+    x = torch.from_numpy(w.signal()[0].astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    tfr, xhat = plan.forward_inverse(x)
+    flat = torch.empty(tfr.numel() + 2, dtype=torch.float32, device="cuda")
+    shifted = flat[2:].view(tfr.shape)          # 8 bytes past a 16-byte boundary
+    shifted.copy_(tfr)
+    assert shifted.data_ptr() % 16 == 8
+    xh2 = plan.inverse(shifted)
+    torch.cuda.synchronize()
+    assert torch.equal(xhat, xh2)
+    plan.close()
