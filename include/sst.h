@@ -243,6 +243,12 @@ sst_status sst_tc_contract(sst_tc_plan_t tc, const float *x_dev, int64_t n, void
  * if any contraction of this tensor plan gave up a device wait since the
  * last check; SST_OK otherwise. */
 sst_status sst_tc_check(sst_tc_plan_t tc, void *stream);
+/* Test hook for the timeout path (cluster 1 only): in the next contraction
+ * one CTA withholds its first operand load, so its bounded waits run out
+ * after about a second each and the contraction returns early with its
+ * output undefined; the next sst_tc_check reports SST_ETIMEOUT and the
+ * context stays usable.  Nothing faults or hangs. */
+sst_status sst_tc_plan_test_withhold(sst_tc_plan_t tc);
 
 /* ---- Batched execution (many channels, uneven lengths, mixed parameters).
  * A batch groups the channels' work by DFT length and runs each group as one

@@ -215,6 +215,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUte
     volatile int *issued_s = (volatile int *)(tmem_slot + 1);
     volatile int *consumed_s = issued_s + 1;
     volatile int *failed_s = issued_s + 2;
+    const bool withhold = err[1] != 0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // cluster c of CL CTAs takes super tiles c, c + clusters, ...: CL row
     // blocks x one column block, row block CL i + rank for this CTA
@@ -270,6 +271,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUte
                 const CUtensorMap *ma = (pass == 2) ? &tmA1 : &tmA0;
                 const CUtensorMap *mb = (pass == 1) ? &tmB1 : &tmB0;
                 uint8_t *sa = smem + s * STAGE, *sb = sa + A_TILE;
+                // test hook (err[1] != 0): CTA 0 withholds its first stage, so the
+                // product's bounded waits run out and report, with no fault
+                if (it == 0 && blockIdx.x == 0 && withhold) continue;
                 mbar_expect_tx(&full[s], STAGE);
                 tma_2d(sa, ma, &full[s], kt * KEL, m0);
                 if (CL == 1)
@@ -363,13 +367,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUte
     }
     fence_before();
     __syncthreads();
-    // on an error, wait (bounded) for loads issued but never consumed
+    // on an error, wait (bounded, each) for loads issued but never consumed
     if (tid == 0 && *issued_s > *consumed_s) {
         for (int it = *consumed_s; it < *issued_s; ++it)
-            if (!mbar_wait(&full[it % STAGES], (it / STAGES) & 1)) {
-                atomicOr(err, 32);
-                break;
-            }
+            if (!mbar_wait(&full[it % STAGES], (it / STAGES) & 1)) atomicOr(err, 32);
     }
     __syncthreads();
     // no CTA leaves while a peer may still deliver to its shared memory
@@ -736,6 +737,7 @@ struct sst_tc_plan {
     CUtensorMap tB[3][2];                    // basis (hi, lo) with a box of BN / CL rows, CL = 1, 2, 4
     int cl = 1;                              // CTAs per cluster sharing the basis tile; 0: CTA pairs
     int grid[4] = {0, 0, 0, 0};              // persistent grid per variant (cluster 1, 2, 4, pair)
+    bool withhold = false;                   // test hook, see sst_tc_plan_test_withhold
 };
 
 namespace {
@@ -888,7 +890,7 @@ SST_API sst_status sst_tc_plan_create(sst_plan_t base, int32_t form, sst_tc_plan
     cudaError_t e = tf32 ? cudaMemcpy(t->B0, bf.data(), belems * 4, cudaMemcpyHostToDevice)
                          : cudaMemcpy(t->B0, bh.data(), belems * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !tf32) e = cudaMemcpy(t->B1, bl.data(), belems * 2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(t->err, 0, 1024);   // error word, test-hook word
     if (e != cudaSuccess) {
         cudaFree(t->dmem);
         delete t;
@@ -1018,6 +1020,7 @@ static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) 
     const int mtiles = (int)(t->fpad / BM), ntiles = t->npad / BN;
     const int vi = variant_index(t->cl);
     const int bi = t->cl == 0 ? 1 : (t->cl == 4 ? 2 : t->cl == 2 ? 1 : 0);   // basis box: BN / (CTAs sharing it)
+    if (t->withhold) SST_CU(cudaMemsetAsync(t->err + 1, 0xff, sizeof(int), st), "test hook");
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = gemm_config(t->grid[vi], t->cl, st, at);
     SST_LAUNCHED_K(PK_STFT, st,
@@ -1025,6 +1028,17 @@ static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) 
                                       (int)d.F, t->npad, t->ncols, mtiles, ntiles, ktiles, passes,
                                       (unsigned *)t->partial, t->err),
                    "tensor contraction");
+    if (t->withhold) {
+        SST_CU(cudaMemsetAsync(t->err + 1, 0, sizeof(int), st), "test hook");
+        t->withhold = false;
+    }
+    return SST_OK;
+}
+
+SST_API sst_status sst_tc_plan_test_withhold(sst_tc_plan_t t) {
+    if (!t) return fail(SST_EINVAL, "plan is NULL");
+    if (t->cl != 1) return fail(SST_EINVAL, "the test hook needs cluster 1");
+    t->withhold = true;
     return SST_OK;
 }
 

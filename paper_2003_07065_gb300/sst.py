@@ -88,6 +88,7 @@ def load():
         "sst_tc_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_tc_contract": ([_vp, _vp, _i64, _vp], ctypes.c_int),
         "sst_tc_check": ([_vp, _vp], ctypes.c_int),
+        "sst_tc_plan_test_withhold": ([_vp], ctypes.c_int),
         "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
                               ctypes.POINTER(_vp)], ctypes.c_int),
         "sst_batch_workspace": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -286,6 +287,10 @@ def sst_tc_contract(tc, x, n, stream=None):
 
 def sst_tc_check(tc, stream=None):
     _check(load().sst_tc_check(tc, _stream(stream)))
+
+
+def sst_tc_plan_test_withhold(tc):
+    _check(load().sst_tc_plan_test_withhold(tc))
 
 
 def sst_fp32_peak(stream=None) -> float:

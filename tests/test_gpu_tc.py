@@ -286,3 +286,28 @@ def test_pair_variant(sst, form):
     st["same_as_cluster1"] = bool(torch.equal(V, V1))
     print("pair", form, {k: (f"{v:.3e}" if isinstance(v, float) else v) for k, v in st.items()})
     plan.close()
+
+
+def test_bounded_wait_reports_timeout(sst):
+    """A contraction whose operand load is withheld (test hook) gives up its
+    bounded waits and reports SST_ETIMEOUT; the context stays usable and the
+    next contraction is exact again."""
+    p = SMALL[0]
+    gen = np.random.default_rng(3)
+    x32 = (np.cos(np.arange(p["n"]) * 0.3) + 0.1 * gen.standard_normal(p["n"])).astype(np.float32)
+    x = torch.from_numpy(x32).cuda()
+    plan = sst.Plan(**p)
+    h = plan._tc_handle("bf16x3")
+    sst.sst_tc_plan_set_cluster(h, 1)
+    V0, _ = plan.tc_stft(x, "bf16x3")
+    sst.sst_tc_plan_test_withhold(h)
+    V = torch.empty_like(V0)
+    Vd = torch.empty_like(V0)
+    sst.sst_tc_stft(h, x, plan.n, V, Vd)
+    with pytest.raises(sst.SstError) as e:
+        sst.sst_tc_check(h)
+    assert e.value.status == 5
+    V1, _ = plan.tc_stft(x, "bf16x3")       # the hook is one-shot; check passes again
+    torch.cuda.synchronize()
+    assert torch.equal(V0, V1)
+    plan.close()
