@@ -411,8 +411,16 @@ __device__ __forceinline__ void tacc_add(uint32_t *__restrict__ acc, int stride,
     atomicAdd(&acc[3 * stride + l], (uint32_t)(int32_t)(b >> 16));
 }
 
+// The exact sum v = hi 2^16 + lo (|v| < 2^45) rounded once to float.  v is
+// split as h 2^21 + r with |h| < 2^24 and 0 <= r < 2^21, both exact in float,
+// and one fused multiply-add rounds h 2^21 + r: the correctly rounded value,
+// as a 64-bit integer conversion would give, from 32-bit conversions only
+// (the 64-bit one is several times slower here).
 __device__ __forceinline__ float tacc_value(uint32_t lo, uint32_t hi, const FwdScale &fs) {
-    return (__ll2float_rn((long long)(int32_t)hi * 65536LL + (long long)lo) * fs.r1) * fs.r2;
+    const long long v = ((long long)(int32_t)hi << 16) + (long long)lo;
+    const int h = (int)(v >> 21);
+    const int r = (int)(v & 0x1fffff);
+    return (fmaf((float)h, 2097152.f, (float)r) * fs.r1) * fs.r2;
 }
 
 // Reads fine bins 4 q .. 4 q + 3 (those below nbo) into Trow and clears them.
