@@ -157,13 +157,14 @@ __global__ void k_spec_fix_src(SpecBuf sb, const SstScalars *__restrict__ sc, fl
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const SpecSrc r = sb.src[i];
         if (r.bin < 0 || !(r.mag2 > gamma2)) continue;
-        const long long a = __float2ll_rn((r.vr * s1) * s2);
-        const long long b = __float2ll_rn((r.vi * s1) * s2);
+        uint32_t alo, ahi, blo, bhi;   // as tacc_add
+        tacc_split((r.vr * s1) * s2, alo, ahi);
+        tacc_split((r.vi * s1) * s2, blo, bhi);
         uint32_t *w = sb.bin[r.bin].w;
-        atomicAdd(&w[0], (uint32_t)(a & 0xffff));
-        atomicAdd(&w[1], (uint32_t)(int32_t)(a >> 16));
-        atomicAdd(&w[2], (uint32_t)(b & 0xffff));
-        atomicAdd(&w[3], (uint32_t)(int32_t)(b >> 16));
+        atomicAdd(&w[0], alo);
+        atomicAdd(&w[1], ahi);
+        atomicAdd(&w[2], blo);
+        atomicAdd(&w[3], bhi);
     }
 }
 

@@ -401,14 +401,31 @@ __device__ __forceinline__ FwdScale fwd_scale(const SstDev &d, const SstScalars 
     return f;
 }
 
+// The fixed-point value a = round(x) (round half to even, |x| < 2^45) split
+// as a = hi 2^16 + lo, 0 <= lo < 2^16, without a 64-bit conversion (several
+// times slower here): below 2^23 through a 32-bit one; above, x is already an
+// integer and x - floor(x / 2^16) 2^16 is exact.
+__device__ __forceinline__ void tacc_split(float x, uint32_t &lo, uint32_t &hi) {
+    if (fabsf(x) < 8388608.f) {
+        const int a = __float2int_rn(x);
+        lo = (uint32_t)a & 0xffffu;
+        hi = (uint32_t)(a >> 16);
+    } else {
+        const float hf = floorf(x * (1.f / 65536.f));
+        lo = (uint32_t)(int)fmaf(-hf, 65536.f, x);
+        hi = (uint32_t)(int)hf;
+    }
+}
+
 // Adds a source (V scaled by 2^e) to fine bin l of the T accumulators.
 __device__ __forceinline__ void tacc_add(uint32_t *__restrict__ acc, int stride, int l, float2 V, const FwdScale &fs) {
-    const long long a = __float2ll_rn((V.x * fs.s1) * fs.s2);
-    const long long b = __float2ll_rn((V.y * fs.s1) * fs.s2);
-    atomicAdd(&acc[l], (uint32_t)(a & 0xffff));
-    atomicAdd(&acc[stride + l], (uint32_t)(int32_t)(a >> 16));
-    atomicAdd(&acc[2 * stride + l], (uint32_t)(b & 0xffff));
-    atomicAdd(&acc[3 * stride + l], (uint32_t)(int32_t)(b >> 16));
+    uint32_t alo, ahi, blo, bhi;
+    tacc_split((V.x * fs.s1) * fs.s2, alo, ahi);
+    tacc_split((V.y * fs.s1) * fs.s2, blo, bhi);
+    atomicAdd(&acc[l], alo);
+    atomicAdd(&acc[stride + l], ahi);
+    atomicAdd(&acc[2 * stride + l], blo);
+    atomicAdd(&acc[3 * stride + l], bhi);
 }
 
 // The exact sum v = hi 2^16 + lo (|v| < 2^45) rounded once to float.  v is
