@@ -139,14 +139,18 @@ template <int NF>
 __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDev &d, int tid, const float2 (&v)[16]) {
     constexpr int NS = NF / 16;
     if (Cfg<NF>::TPF == NS || tid < NS) {
+        // k = q = tid + r NS lands at zc[kb0 + r NS] when 0 <= kb0 + r NS <= k_hi - k_lo,
+        // its mirror NF - q at zm[km0 - r NS]: one unsigned compare per store
+        const unsigned span = (unsigned)(d.k_hi - d.k_lo);
+        const int kb0 = tid - d.k_lo, km0 = NF - tid - d.k_lo;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            const int q = tid + r * NS;
-            const int kb = q - d.k_lo;
-            if (kb >= 0 && q <= d.k_hi) zc[kb] = v[r];
-            const int qm = (NF - q) & (NF - 1);
-            const int km = qm - d.k_lo;
-            if (km >= 0 && qm <= d.k_hi) zm[km] = v[r];
+            if ((unsigned)(kb0 + r * NS) <= span) zc[kb0 + r * NS] = v[r];
+            if (r == 0 && tid == 0) {   // q = 0 is its own mirror
+                if (d.k_lo == 0) zm[0] = v[0];
+            } else if ((unsigned)(km0 - r * NS) <= span) {
+                zm[km0 - r * NS] = v[r];
+            }
         }
     }
 }
