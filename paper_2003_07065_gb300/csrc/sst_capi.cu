@@ -463,7 +463,13 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->smem_absmax = kt->smem_frame + sizeof(float2) * (kt->smem_frame - 128) / sizeof(float2);  // two frame buffers
     // inverse: frame buffer, the pair's two T rows regrouped by sub-grid, overlap-add segment
     pl->smem_inv = kt->smem_frame + 2 * sizeof(float2) * (size_t)z * nb + sizeof(float) * (size_t)d.seg_len;
-    pl->inv_kind = (L <= nf / 2 + 1) ? KIND_INV : KIND_INV_WIDE;
+    // pruned kernels where the band (and, for the forward, the window) leaves
+    // part of the radix-16 first pass empty
+    const int bcls = band_class(nf, kt->r1, (int)k_hi);
+    const bool half_window = L <= nf / 2 + 1;
+    pl->inv_kind = half_window ? kind_cls(KIND_INV, bcls) : KIND_INV_WIDE;
+    pl->kind_fwd_t = kind_cls(KIND_FWD_T, half_window ? bcls : 0);
+    pl->kind_fwd_spec = kind_cls(KIND_FWD_SPEC, half_window ? bcls : 0);
     const size_t smax = prop.sharedMemPerBlockOptin;
     if (pl->smem_fwd_t > smax || pl->smem_inv > smax) {
         cudaFree(pl->dmem);
@@ -471,7 +477,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         return fail(SST_EUNSUPPORTED, "shared memory need (%zu / %zu B) exceeds %zu B", pl->smem_fwd_t,
                     pl->smem_inv, smax);
     }
-    struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {KIND_FWD_T, pl->smem_fwd_t},
+    struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {pl->kind_fwd_t, pl->smem_fwd_t},
         {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {pl->inv_kind, pl->smem_inv}};
     for (auto &k : kinds) {
         ce = raise_smem(kt, k.kind, k.bytes);
@@ -485,7 +491,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         return (int)std::max<int64_t>(g_, 1);
     };
     pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 3) / 4);
-    pl->grid_fwd = grid_for(KIND_FWD_T, pl->smem_fwd_t, F);
+    pl->grid_fwd = grid_for(pl->kind_fwd_t, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
 
     // ---- one-pass relative threshold (default for relative plans)
@@ -493,9 +499,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
                         (spec_in_frame(nb, nbo, (int)((kt->smem_frame - 128) / sizeof(float2))) ? 0 : spec_smem_bytes(nbo));
     pl->spec = d.relative && !(p.flags & SST_TWO_PASS) && pl->smem_fwd_spec <= smax;
     if (pl->spec) {
-        ce = raise_smem(kt, KIND_FWD_SPEC, pl->smem_fwd_spec);
+        ce = raise_smem(kt, pl->kind_fwd_spec, pl->smem_fwd_spec);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
-        pl->grid_fwd_spec = grid_for(KIND_FWD_SPEC, pl->smem_fwd_spec, F);
+        pl->grid_fwd_spec = grid_for(pl->kind_fwd_spec, pl->smem_fwd_spec, F);
         // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
         pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop + 1));
         // records: 1/64 of the sources, plus the chunk tails each CTA may leave unused
@@ -640,7 +646,7 @@ static sst_status run_forward_spec(sst_plan_t pl, const float *x, float *tfr, vo
     SstDev df = d;
     df.spec = sb;
     SST_LAUNCHED_K(PK_FORWARD, st,
-                   pl->kt->forward(df, KIND_FWD_SPEC, x, sc, tfr, nullptr, pl->grid_fwd_spec, pl->smem_fwd_spec, st),
+                   pl->kt->forward(df, pl->kind_fwd_spec, x, sc, tfr, nullptr, pl->grid_fwd_spec, pl->smem_fwd_spec, st),
                    "one-pass forward launch");
     const int gfix = pl->num_sms * 4;
     SST_LAUNCHED_K(PK_OTHER, st, (k_spec_fix_src<<<gfix, 256, 0, st>>>(sb, sc, pl->gamma_frac2), cudaGetLastError()),
@@ -658,7 +664,7 @@ static sst_status run_forward_spec(sst_plan_t pl, const float *x, float *tfr, vo
                     cudaGetLastError()),
                    "gamma launch");
     SST_LAUNCHED_K(PK_FORWARD, st,
-                   pl->kt->forward(dg, KIND_FWD_T, x, sc, tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   pl->kt->forward(dg, pl->kind_fwd_t, x, sc, tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
                    "forward launch");
     return SST_OK;
 }
@@ -668,7 +674,7 @@ static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *w
     sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
     if (s != SST_OK) return s;
     SST_LAUNCHED_K(PK_FORWARD, st,
-                   pl->kt->forward(pl->d, KIND_FWD_T, x, ws_scalars(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   pl->kt->forward(pl->d, pl->kind_fwd_t, x, ws_scalars(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
                    "forward launch");
     return SST_OK;
 }
@@ -815,7 +821,7 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     cudaStream_t st = (cudaStream_t)stream;
     s = run_prepass(plan, x_dev, sc, partial, st, nullptr, false);
     if (s != SST_OK) return s;
-    SST_CU(plan->kt->forward(plan->d, KIND_FWD_T, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
+    SST_CU(plan->kt->forward(plan->d, plan->kind_fwd_t, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
            "forward launch");
     count_launch();
     return SST_OK;

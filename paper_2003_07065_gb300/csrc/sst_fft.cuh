@@ -136,6 +136,76 @@ template <bool INV> __device__ __forceinline__ void dft16(float2 *v) {
     t = v[11]; v[11] = v[14]; v[14] = t;
 }
 
+// 4-point DFT whose inputs a_i with bit i of M clear are known to be zero
+// (their registers are not read).  M = 0 leaves the outputs unset: they are
+// zero, and the caller treats them as such.
+template <bool INV, int M> __device__ __forceinline__ void dft4m(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    if constexpr (M == 15) {
+        dft4<INV>(a0, a1, a2, a3);
+    } else if constexpr (M != 0) {
+        constexpr bool e0 = M & 1, e1 = M & 2, e2 = M & 4, e3 = M & 8;
+        const float2 zero = make_float2(0.f, 0.f);
+        // s0 = a0 + a2, d0 = a0 - a2, s1 = a1 + a3, d1 = -+i (a1 - a3)
+        float2 s0, d0, s1, d1;
+        if constexpr (e0 && e2) { s0 = cadd(a0, a2); d0 = csub(a0, a2); }
+        else if constexpr (e0) { s0 = a0; d0 = a0; }
+        else if constexpr (e2) { s0 = a2; d0 = make_float2(-a2.x, -a2.y); }
+        else { s0 = zero; d0 = zero; }
+        if constexpr (e1 && e3) { s1 = cadd(a1, a3); d1 = rot90<INV>(csub(a1, a3)); }
+        else if constexpr (e1) { s1 = a1; d1 = rot90<INV>(a1); }
+        else if constexpr (e3) { s1 = a3; d1 = rot90<INV>(make_float2(-a3.x, -a3.y)); }
+        else { s1 = zero; d1 = zero; }
+        constexpr bool h0 = e0 || e2, h1 = e1 || e3;
+        if constexpr (h0 && h1) {
+            a0 = cadd(s0, s1); a2 = csub(s0, s1); a1 = cadd(d0, d1); a3 = csub(d0, d1);
+        } else if constexpr (h0) {
+            a0 = s0; a2 = s0; a1 = d0; a3 = d0;
+        } else {
+            a0 = s1; a2 = make_float2(-s1.x, -s1.y); a1 = d1; a3 = make_float2(-d1.x, -d1.y);
+        }
+    }
+}
+
+// 16-point DFT (as dft16) of inputs v[r] that are zero where bit r of MASK is
+// clear; zero inputs are not read and the operations they would feed are
+// left out (for spectra and windows that occupy part of the frame only).
+template <bool INV, unsigned MASK> __device__ __forceinline__ void dft16m(float2 *v) {
+    if constexpr (MASK == 0xffffu) {
+        dft16<INV>(v);
+    } else {
+        // group n2 holds inputs r = n2, n2 + 4, n2 + 8, n2 + 12
+        constexpr int G0 = ((MASK >> 0) & 1) | ((MASK >> 3) & 2) | ((MASK >> 6) & 4) | ((MASK >> 9) & 8);
+        constexpr int G1 = ((MASK >> 1) & 1) | ((MASK >> 4) & 2) | ((MASK >> 7) & 4) | ((MASK >> 10) & 8);
+        constexpr int G2 = ((MASK >> 2) & 1) | ((MASK >> 5) & 2) | ((MASK >> 8) & 4) | ((MASK >> 11) & 8);
+        constexpr int G3 = ((MASK >> 3) & 1) | ((MASK >> 6) & 2) | ((MASK >> 9) & 4) | ((MASK >> 12) & 8);
+        dft4m<INV, G0>(v[0], v[4], v[8], v[12]);
+        dft4m<INV, G1>(v[1], v[5], v[9], v[13]);
+        dft4m<INV, G2>(v[2], v[6], v[10], v[14]);
+        dft4m<INV, G3>(v[3], v[7], v[11], v[15]);
+        if constexpr (G1 != 0) { v[5] = w16<INV, 1>(v[5]); v[9] = w16<INV, 2>(v[9]); v[13] = w16<INV, 3>(v[13]); }
+        if constexpr (G2 != 0) { v[6] = w16<INV, 2>(v[6]); v[10] = w16<INV, 4>(v[10]); v[14] = w16<INV, 6>(v[14]); }
+        if constexpr (G3 != 0) { v[7] = w16<INV, 3>(v[7]); v[11] = w16<INV, 6>(v[11]); v[15] = w16<INV, 9>(v[15]); }
+        // second step: group k1 holds Y[n2][k1] at v[4 k1 + n2], present where G(n2) != 0
+        constexpr int H = (G0 ? 1 : 0) | (G1 ? 2 : 0) | (G2 ? 4 : 0) | (G3 ? 8 : 0);
+        const float2 zero = make_float2(0.f, 0.f);
+        dft4m<INV, H>(v[0], v[1], v[2], v[3]);
+        dft4m<INV, H>(v[4], v[5], v[6], v[7]);
+        dft4m<INV, H>(v[8], v[9], v[10], v[11]);
+        dft4m<INV, H>(v[12], v[13], v[14], v[15]);
+        if constexpr (H == 0) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = zero;
+        }
+        float2 t;
+        t = v[1]; v[1] = v[4]; v[4] = t;
+        t = v[2]; v[2] = v[8]; v[8] = t;
+        t = v[3]; v[3] = v[12]; v[12] = t;
+        t = v[6]; v[6] = v[9]; v[9] = t;
+        t = v[7]; v[7] = v[13]; v[13] = t;
+        t = v[11]; v[11] = v[14]; v[14] = t;
+    }
+}
+
 template <int R, bool INV> __device__ __forceinline__ void dft_r(float2 *v) {
     if constexpr (R == 2) dft2<INV>(v[0], v[1]);
     else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
@@ -314,16 +384,19 @@ __device__ __forceinline__ void fft_middle(float2 *buf, const float2 *__restrict
 // x[j + r NF/R1] in v[b][r]; the R1-point DFT is applied and the results
 // stored in autosorted order (span 1: x'[j R1 + r]).  No barrier inside;
 // the caller must __syncthreads() before the next pass.
-template <int NF, int TPF, bool INV>
+// MASK (R1 = 16 only): inputs r whose bit is clear are zero and not read.
+template <int NF, int TPF, bool INV, unsigned MASK = 0xffffu>
 __device__ __forceinline__ void fft_first_from_regs(float2 *buf, float2 (*v)[FftPlan<NF>::R1], int tid) {
     constexpr int R1 = FftPlan<NF>::R1;
     constexpr int NBF = NF / R1;
     constexpr int PER = (NBF + TPF - 1) / TPF;
+    static_assert(MASK == 0xffffu || R1 == 16, "input masks need a radix-16 first pass");
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
         const int j = tid + b * TPF;
         if (PER * TPF == NBF || j < NBF) {
-            dft_r<R1, INV>(v[b]);
+            if constexpr (MASK == 0xffffu) dft_r<R1, INV>(v[b]);
+            else dft16m<INV, MASK>(v[b]);
             // outputs j R1 .. j R1 + R1 - 1 share one pad block (R1 divides 16)
             const int pb = padded(j * R1);
 #pragma unroll

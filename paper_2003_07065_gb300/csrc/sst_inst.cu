@@ -13,14 +13,28 @@ namespace {
 constexpr int NF = SST_NF;
 using C = Cfg<NF>;
 
+constexpr int CLS1 = cls_for<NF>(1), CLS2 = cls_for<NF>(2);
+
+int cls_of(int kind) { return kind >> KIND_CLS_SHIFT; }
+
+template <int MODE> const void *forward_kernel(int cls) {
+    if (cls == 1) return (const void *)k_forward<NF, MODE, CLS1>;
+    if (cls == 2) return (const void *)k_forward<NF, MODE, CLS2>;
+    return (const void *)k_forward<NF, MODE, 0>;
+}
+
 const void *kernel_of(int kind) {
-    switch (kind) {
+    const int cls = cls_of(kind);
+    switch (kind & ((1 << KIND_CLS_SHIFT) - 1)) {
         case KIND_ABSMAX: return (const void *)k_absmax<NF>;
-        case KIND_FWD_T: return (const void *)k_forward<NF, MODE_T>;
+        case KIND_FWD_T: return forward_kernel<MODE_T>(cls);
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
-        case KIND_FWD_SPEC: return (const void *)k_forward<NF, MODE_SPEC>;
-        case KIND_INV: return (const void *)k_inverse<NF, true>;
+        case KIND_FWD_SPEC: return forward_kernel<MODE_SPEC>(cls);
+        case KIND_INV:
+            if (cls == 1) return (const void *)k_inverse<NF, true, CLS1>;
+            if (cls == 2) return (const void *)k_inverse<NF, true, CLS2>;
+            return (const void *)k_inverse<NF, true>;
         case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
         case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
         case KIND_B_FWD: return (const void *)k_forward_batch<NF>;
@@ -47,11 +61,20 @@ cudaError_t absmax(const SstDev &d, const float *x, float *partial, int grid, si
     return cudaGetLastError();
 }
 
+template <int MODE>
+void launch_forward(int cls, const SstDev &d, const float *x, const SstScalars *sc, void *out0, void *out1, int grid,
+                    size_t smem, cudaStream_t st) {
+    if (cls == 1) k_forward<NF, MODE, CLS1><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+    else if (cls == 2) k_forward<NF, MODE, CLS2><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+    else k_forward<NF, MODE, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+}
+
 cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0, void *out1,
                     int grid, size_t smem, cudaStream_t st) {
-    switch (kind) {
+    const int cls = cls_of(kind);
+    switch (kind & ((1 << KIND_CLS_SHIFT) - 1)) {
         case KIND_FWD_T:
-            k_forward<NF, MODE_T><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+            launch_forward<MODE_T>(cls, d, x, sc, out0, out1, grid, smem, st);
             break;
         case KIND_FWD_STFT:
             k_forward<NF, MODE_STFT><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
@@ -60,7 +83,7 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
             k_forward<NF, MODE_MAP><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         case KIND_FWD_SPEC:
-            k_forward<NF, MODE_SPEC><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+            launch_forward<MODE_SPEC>(cls, d, x, sc, out0, out1, grid, smem, st);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -68,7 +91,12 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
 }
 
 cudaError_t inverse(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st) {
-    if (kind == KIND_INV)
+    const unsigned grid = (unsigned)d.ntiles;
+    if (kind == kind_cls(KIND_INV, 1))
+        k_inverse<NF, true, CLS1><<<grid, C::TPF, smem, st>>>(d, T, partial);
+    else if (kind == kind_cls(KIND_INV, 2))
+        k_inverse<NF, true, CLS2><<<grid, C::TPF, smem, st>>>(d, T, partial);
+    else if (kind == KIND_INV)
         k_inverse<NF, true><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
     else if (kind == KIND_INV_WIDE)
         k_inverse<NF, false><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
@@ -89,7 +117,7 @@ cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nit
     return cudaGetLastError();
 }
 
-const KernelTable table = {NF, C::TPF, (size_t)C::BUF * sizeof(float2) + 128, set_smem, occupancy,
+const KernelTable table = {NF, C::R1, C::TPF, (size_t)C::BUF * sizeof(float2) + 128, set_smem, occupancy,
                            absmax, forward, inverse, batch};
 
 }  // namespace

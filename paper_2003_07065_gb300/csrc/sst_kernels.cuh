@@ -27,6 +27,24 @@ template <int NF> struct Cfg {
     static constexpr int MINB = (768 / TPF < 1) ? 1 : ((768 / TPF > 8) ? 8 : 768 / TPF);
 };
 
+// Pruning classes of the radix-16 first pass (STEP = NF / 16; a class is 0
+// for any other first radix).  A band [k_lo, k_hi] of class 1 (k_hi < 3 STEP)
+// and its mirror NF - k sit at positions j + r STEP with r in [0, 2] and
+// [13, 15] only; class 2 (k_hi < 5 STEP): r in [0, 4] and [11, 15].  So the
+// inverse's spectrum input and the forward's band output touch those r only.
+// A forward of class c > 0 also has a window of L <= NF/2 + 1 taps, nonzero at
+// r in [0, 4] and [12, 15] only.  Masks: bit r set = position r in use.
+__host__ __device__ constexpr int band_class(int nf, int r1, int k_hi) {
+    return r1 != 16 ? 0 : (k_hi < 3 * (nf / 16) ? 1 : (k_hi < 5 * (nf / 16) ? 2 : 0));
+}
+template <int NF> __host__ __device__ constexpr unsigned band_mask(int cls) {
+    return (FftPlan<NF>::R1 != 16 || cls == 0) ? 0xffffu : (cls == 1 ? 0xE007u : 0xF81Fu);
+}
+template <int NF> __host__ __device__ constexpr unsigned window_mask(int cls) {
+    return (FftPlan<NF>::R1 != 16 || cls == 0) ? 0xffffu : 0xF01Fu;
+}
+template <int NF> __host__ __device__ constexpr int cls_for(int cls) { return FftPlan<NF>::R1 == 16 ? cls : 0; }
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -75,8 +93,9 @@ __device__ __forceinline__ float2 frame_sample(const SstDev &d, const float *__r
 // First-pass inputs of one frame (or pair): u[b][r] = sample at FFT position
 // j + r NF/R1, j = tid + b TPF.  Interior frames (window inside [0, n)) with
 // L <= NF take a fast path: each position holds at most one tap, j = p or
-// p - NF, read through 32-bit offsets from the frame centre.
-template <int NF, bool PAIR>
+// p - NF, read through 32-bit offsets from the frame centre.  Positions r
+// whose bit in WMASK is clear hold no tap and are left unset.
+template <int NF, bool PAIR, unsigned WMASK = 0xffffu>
 __device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>::R1], const SstDev &d,
                                              const float *__restrict__ x, int64_t c1, int64_t c2, bool has2,
                                              int tid) {
@@ -92,6 +111,7 @@ __device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>:
             const int j = tid + b * C::TPF;
 #pragma unroll
             for (int r = 0; r < C::R1; ++r) {
+                if (!((WMASK >> r) & 1u)) continue;
                 const int p = j + r * (NF / C::R1);
                 const bool lo = p <= d.M, hi = p >= NF - d.M;
                 const int jj = lo ? p : p - NF;
@@ -112,21 +132,22 @@ __device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>:
         const int j = tid + b * C::TPF;
 #pragma unroll
         for (int r = 0; r < C::R1; ++r)
-            u[b][r] = (C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1)
-                          ? frame_sample<NF, PAIR>(d, x, j + r * (NF / C::R1), c1, c2, has2)
-                          : make_float2(0.f, 0.f);
+            if ((WMASK >> r) & 1u)
+                u[b][r] = (C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1)
+                              ? frame_sample<NF, PAIR>(d, x, j + r * (NF / C::R1), c1, c2, has2)
+                              : make_float2(0.f, 0.f);
     }
 }
 
 // Forward FFT of frame(s) (c1, c2 are frame centres): gather fused into the
 // first pass, outputs X[j + r NF/16] left in v (thread j = tid < NF/16).
-template <int NF, bool PAIR>
+template <int NF, bool PAIR, unsigned WMASK = 0xffffu>
 __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const float *__restrict__ x, int64_t c1,
                                             int64_t c2, bool has2, int tid, float2 (&v)[16]) {
     using C = Cfg<NF>;
     float2 u[C::PER1][C::R1];
-    gather_first<NF, PAIR>(u, d, x, c1, c2, has2, tid);
-    fft_first_from_regs<NF, C::TPF, false>(buf, u, tid);
+    gather_first<NF, PAIR, WMASK>(u, d, x, c1, c2, has2, tid);
+    fft_first_from_regs<NF, C::TPF, false, WMASK>(buf, u, tid);
     __syncthreads();
     fft_middle<NF, C::TPF, C::R1, false>(buf, d.tw, tid);
     fft_last_to_regs<NF, C::TPF, false>(buf, d.tw, tid, v);
@@ -134,8 +155,9 @@ __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const 
 
 // Scatter the last-pass outputs needed by the Hermitian split into buf:
 // zc[k - k_lo] = X[k] and zm[k - k_lo] = X[(NF - k) mod NF] for k in the band.
-// Caller syncs afterwards.
-template <int NF>
+// Only the positions r set in OMASK can hold a band bin.  Caller syncs
+// afterwards.
+template <int NF, unsigned OMASK = 0xffffu>
 __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDev &d, int tid, const float2 (&v)[16]) {
     constexpr int NS = NF / 16;
     if (Cfg<NF>::TPF == NS || tid < NS) {
@@ -145,6 +167,7 @@ __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDe
         const int kb0 = tid - d.k_lo, km0 = NF - tid - d.k_lo;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
+            if (!((OMASK >> r) & 1u)) continue;
             if ((unsigned)(kb0 + r * NS) <= span) zc[kb0 + r * NS] = v[r];
             if (r == 0 && tid == 0) {   // q = 0 is its own mirror
                 if (d.k_lo == 0) zm[0] = v[0];
@@ -474,8 +497,8 @@ __device__ __forceinline__ void tacc_take4(uint32_t *__restrict__ acc, int strid
 // One frame m of the forward transform.  The T accumulators (tacc_stride(nbo) words x 4) must be
 // zero on entry and are zero again on return (MODE_T, MODE_SPEC).  MODE_SPEC
 // also needs sf (set up here for every frame) and the CTA's record cursor,
-// and folds max |S^g|^2 into *vmax.
-template <int NF, int MODE>
+// and folds max |S^g|^2 into *vmax.  CLS: pruning class (see band_class).
+template <int NF, int MODE, int CLS = 0>
 __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
                                               float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
                                               float2 *buf, uint32_t *acc, int tid, SpecFrame *sf = nullptr,
@@ -483,9 +506,9 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     float2 v[16];
-    forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);
+    forward_fft<NF, false, window_mask<NF>(CLS)>(buf, d, x, m * d.hop, 0, false, tid, v);
     float2 *zc = buf, *zm = buf + d.nb;
-    scatter_band<NF>(zc, zm, d, tid, v);
+    scatter_band<NF, band_mask<NF>(CLS)>(zc, zm, d, tid, v);
     if (MODE == MODE_SPEC && tid == 0) sf->nmarg = 0;   // (sf may live in the frame buffer)
     __syncthreads();
 
@@ -548,7 +571,7 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     // __syncthreads inside the next frame's FFT
 }
 
-template <int NF, int MODE>
+template <int NF, int MODE, int CLS = 0>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
 k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
           float2 *__restrict__ out0, void *__restrict__ out1) {
@@ -579,7 +602,7 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
     SpecCursor cur = {0u, 0u, 0u, 0u};
     // (the first __syncthreads in forward_frame orders this before any atomic)
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
-        forward_frame<NF, MODE>(d, x, fs, out0, out1, m, buf, acc, tid, sf, &vmax, &cur);
+        forward_frame<NF, MODE, CLS>(d, x, fs, out0, out1, m, buf, acc, tid, sf, &vmax, &cur);
     if (MODE == MODE_SPEC) {
         vmax = warp_max(vmax);
         if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
@@ -615,8 +638,9 @@ template <bool NARROW> struct InvTaps {
 
 // One inverse tile; smem4 is the kernel's dynamic shared memory.  Ends with a
 // barrier-free write of the tile's segment (callers looping over tiles sync
-// before the next tile zeroes the segment).
-template <int NF, bool NARROW>
+// before the next tile zeroes the segment).  CLS: band class (see
+// band_class); the spectrum inputs at other positions are not formed.
+template <int NF, bool NARROW, int CLS = 0>
 __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__restrict__ T, float *__restrict__ partial,
                                              int64_t tile, float4 *smem4, int tid) {
     using C = Cfg<NF>;
@@ -735,6 +759,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                 const int qm0 = NF - dl - j - d.k_lo;
 #pragma unroll
                 for (int r = 0; r < C::R1; ++r) {
+                    if (!((band_mask<NF>(CLS) >> r) & 1u)) continue;
                     float2 y = make_float2(0.f, 0.f);
                     const int q = q0 + r * STEP;
                     const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
@@ -764,7 +789,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                     u[bb][r] = y;
                 }
             }
-            fft_first_from_regs<NF, TPF, true>(buf, u, tid);
+            fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
             __syncthreads();
             // the pair's rows are read for the last time above: fetch the next pair's
             if (async && s == d.z - 1 && tid == 0 && 2 * (pr + 1) < d.B) {
@@ -813,11 +838,11 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
 
 #define SST_INV_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
 
-template <int NF, bool NARROW>
+template <int NF, bool NARROW, int CLS = 0>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, SST_INV_MINB)
 k_inverse(SstDev d, const float2 *__restrict__ T, float *__restrict__ partial) {
     extern __shared__ float4 smem4[];
-    inverse_tile<NF, NARROW>(d, T, partial, blockIdx.x, smem4, threadIdx.x);
+    inverse_tile<NF, NARROW, CLS>(d, T, partial, blockIdx.x, smem4, threadIdx.x);
 }
 
 __device__ __forceinline__ float recip_norm(const SstDev &d, int64_t p) {

@@ -12,8 +12,15 @@ namespace sst {
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
        KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10, KIND_COUNT = 11 };
 
+// A forward (KIND_FWD_T, KIND_FWD_SPEC) or inverse (KIND_INV) kind may carry a
+// pruning class (band_class, 1 or 2) in the bits from KIND_CLS_SHIFT up;
+// tables whose first radix is not 16 run class 0 for every class.
+constexpr int KIND_CLS_SHIFT = 8;
+inline int kind_cls(int kind, int cls) { return kind | (cls << KIND_CLS_SHIFT); }
+
 struct KernelTable {
     int nf;
+    int r1;              // radix of the first FFT pass
     int tpf;             // threads per CTA
     size_t smem_frame;   // bytes of the padded frame buffer plus reduction scratch
     // raise the dynamic shared-memory limit of a kernel kind
