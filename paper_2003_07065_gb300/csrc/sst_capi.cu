@@ -459,6 +459,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
 
     // ---- shared memory and grids
     pl->smem_fwd_x = kt->smem_frame;
+    // (forward kernels of class > 0 add the band's mirror values: below)
     pl->smem_fwd_t = kt->smem_frame + tacc_bytes(nbo);
     pl->smem_absmax = kt->smem_frame + sizeof(float2) * (kt->smem_frame - 128) / sizeof(float2);  // two frame buffers
     // inverse: frame buffer, the pair's two T rows regrouped by sub-grid, overlap-add segment
@@ -470,6 +471,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->inv_kind = half_window ? kind_cls(KIND_INV, bcls) : KIND_INV_WIDE;
     pl->kind_fwd_t = kind_cls(KIND_FWD_T, half_window ? bcls : 0);
     pl->kind_fwd_spec = kind_cls(KIND_FWD_SPEC, half_window ? bcls : 0);
+    if (half_window && bcls > 0) pl->smem_fwd_t += mirror_bytes(nb);
     const size_t smax = prop.sharedMemPerBlockOptin;
     if (pl->smem_fwd_t > smax || pl->smem_inv > smax) {
         cudaFree(pl->dmem);

@@ -407,8 +407,8 @@ __device__ __forceinline__ void fft_first_from_regs(float2 *buf, float2 (*v)[Fft
 
 // Last pass into registers: butterfly j (< NF/16) loads x[j + r NF/16],
 // applies W_NF^{r j}, and leaves the outputs X[j + r NF/16] in v[r].  Ends
-// with a __syncthreads(), after which buf may be reused.
-template <int NF, int TPF, bool INV>
+// with a __syncthreads() (SYNC), after which buf may be reused.
+template <int NF, int TPF, bool INV, bool SYNC = true>
 __device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2 *__restrict__ tw, int tid,
                                                  float2 (&v)[16]) {
     constexpr int NS = NF / 16;
@@ -420,7 +420,7 @@ __device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2
         twiddle16<INV>(v, tw + tw_offset<NF, NS>(), NS, j);
         dft16<INV>(v);
     }
-    __syncthreads();
+    if constexpr (SYNC) __syncthreads();
 }
 
 // Whole in-place FFT of buf (natural order in and out), for callers that do

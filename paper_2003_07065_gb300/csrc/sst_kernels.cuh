@@ -141,7 +141,8 @@ __device__ __forceinline__ void gather_first(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>:
 
 // Forward FFT of frame(s) (c1, c2 are frame centres): gather fused into the
 // first pass, outputs X[j + r NF/16] left in v (thread j = tid < NF/16).
-template <int NF, bool PAIR, unsigned WMASK = 0xffffu>
+// SYNC: end with a barrier, after which buf may be written.
+template <int NF, bool PAIR, unsigned WMASK = 0xffffu, bool SYNC = true>
 __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const float *__restrict__ x, int64_t c1,
                                             int64_t c2, bool has2, int tid, float2 (&v)[16]) {
     using C = Cfg<NF>;
@@ -150,7 +151,7 @@ __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const 
     fft_first_from_regs<NF, C::TPF, false, WMASK>(buf, u, tid);
     __syncthreads();
     fft_middle<NF, C::TPF, C::R1, false>(buf, d.tw, tid);
-    fft_last_to_regs<NF, C::TPF, false>(buf, d.tw, tid, v);
+    fft_last_to_regs<NF, C::TPF, false, SYNC>(buf, d.tw, tid, v);
 }
 
 // Scatter the last-pass outputs needed by the Hermitian split into buf:
@@ -173,6 +174,27 @@ __device__ __forceinline__ void scatter_band(float2 *zc, float2 *zm, const SstDe
                 if (d.k_lo == 0) zm[0] = v[0];
             } else if ((unsigned)(km0 - r * NS) <= span) {
                 zm[km0 - r * NS] = v[r];
+            }
+        }
+    }
+}
+
+// Store only the mirrors of the band: mz[k - k_lo] = X[(NF - k) mod NF] for k
+// in the band (the zm half of scatter_band), for readers that take X[k]
+// itself from the registers of thread k mod NF/16.  Caller syncs afterwards.
+template <int NF, unsigned OMASK>
+__device__ __forceinline__ void store_mirror(float2 *mz, const SstDev &d, int tid, const float2 (&v)[16]) {
+    constexpr int NS = NF / 16;
+    if (Cfg<NF>::TPF == NS || tid < NS) {
+        const unsigned span = (unsigned)(d.k_hi - d.k_lo);
+        const int km0 = NF - tid - d.k_lo;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (!((OMASK >> r) & 1u)) continue;
+            if (r == 0 && tid == 0) {
+                if (d.k_lo == 0) mz[0] = v[0];
+            } else if ((unsigned)(km0 - r * NS) <= span) {
+                mz[km0 - r * NS] = v[r];
             }
         }
     }
@@ -304,8 +326,6 @@ enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2, MODE_SPEC = 3 };
 // exact threshold (beyond it the call falls back to the two-pass path)
 constexpr int SPEC_MCAP = 256;
 struct SpecFrame {
-    int nmarg;                 // sources listed for this frame
-    int pad[3];
     float4 item[SPEC_MCAP];    // (l as int bits, S^g re, S^g im, |S^g|^2)
     int binidx[SPEC_MCAP];     // the bin record of each listed source
 };
@@ -336,15 +356,15 @@ __device__ __forceinline__ unsigned spec_take(const SpecBuf &b, unsigned &cur, u
     cur += k;
     return r;
 }
-// Warp 0, after the frame's sources are listed: one bin record per distinct
-// fine bin (with the exact sums of the sources already kept there, read
-// before the accumulators are cleared), then one source record per listed
-// source pointing at its bin's record.
-__device__ __forceinline__ void spec_records(const SstDev &d, SpecFrame *sf, const uint32_t *acc, int64_t m,
-                                             int lane, SpecCursor *cur) {
-    const int n = min(sf->nmarg, SPEC_MCAP);
+// Warp 0, after the frame's nm sources are listed: one bin record per
+// distinct fine bin (with the exact sums of the sources already kept there,
+// read before the accumulators are cleared), then one source record per
+// listed source pointing at its bin's record.
+__device__ __forceinline__ void spec_records(const SstDev &d, SpecFrame *sf, int nm, const uint32_t *acc,
+                                             int64_t m, int lane, SpecCursor *cur) {
+    const int n = min(nm, SPEC_MCAP);
     const int stride = tacc_stride(d.nbo);
-    if (lane == 0 && sf->nmarg > SPEC_MCAP) d.spec.ctl[3] = 1u;
+    if (lane == 0 && nm > SPEC_MCAP) d.spec.ctl[3] = 1u;
     for (int c = 0; c < n; c += 32) {
         const int i = c + lane;
         const int l = i < n ? __float_as_int(sf->item[i].x) : -1;
@@ -403,6 +423,8 @@ __device__ __forceinline__ void spec_records(const SstDev &d, SpecFrame *sf, con
         }
     }
 }
+// bytes of the band's mirror values (forward kernels of class > 0)
+__host__ __device__ constexpr size_t mirror_bytes(int nb) { return (8 * (size_t)nb + 15) & ~(size_t)15; }
 // bytes of MODE_SPEC shared state
 __host__ __device__ __forceinline__ size_t spec_smem_bytes(int nbo) {
     return sizeof(SpecFrame);
@@ -494,66 +516,95 @@ __device__ __forceinline__ void tacc_take4(uint32_t *__restrict__ acc, int strid
     }
 }
 
+// Band bin kk (k = k_lo + kk) of frame m from X[k] = zk and X[NF - k] = zn:
+// the Hermitian split, then by MODE the STFT pair, the map entry, or the
+// reassignment of the source into the T accumulators (MODE_SPEC: sources
+// between the threshold bounds are listed in sf instead, *nmarg counting them).
+template <int MODE>
+__device__ __forceinline__ void frame_bin(const SstDev &d, const FwdScale &fs, float2 *__restrict__ out0,
+                                          void *__restrict__ out1, int64_t m, int kk, float2 zk, float2 zn,
+                                          uint32_t *acc, SpecFrame *sf, int *nmarg, float *vmax) {
+    const int k = d.k_lo + kk;
+    const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+    const float2 Vd = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+    const size_t o = (size_t)m * d.nb + kk;
+    if (MODE == MODE_STFT) {
+        out0[o] = V;
+        reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
+        return;
+    }
+    const float mag2 = V.x * V.x + V.y * V.y;
+    // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36)
+    const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
+    int l = -1;
+    if (mag2 > fs.gamma2) {
+        const float f = floorf(fmaf((float)d.z, delta, 0.5f));
+        l = -2;
+        if (f > -1073741824.f && f < 1073741824.f) {
+            const int lc = d.z * (k - d.k_lo) + (int)f;
+            if (lc >= 0 && lc < d.nbo) l = lc;
+        }
+    }
+    if (MODE == MODE_MAP) {
+        reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
+        reinterpret_cast<int32_t *>(out1)[o] = l;
+        return;
+    }
+    if (MODE == MODE_SPEC) {
+        *vmax = fmaxf(*vmax, mag2);
+        if (l >= 0 && !(mag2 > fs.g_ub2)) {
+            // kept only if |S^g| exceeds the exact threshold: list it, flag its bin
+            const int i = atomicAdd(nmarg, 1);
+            if (i < SPEC_MCAP) sf->item[i] = make_float4(__int_as_float(l), V.x, V.y, mag2);
+            return;
+        }
+    }
+    if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
+}
+
 // One frame m of the forward transform.  The T accumulators (tacc_stride(nbo) words x 4) must be
 // zero on entry and are zero again on return (MODE_T, MODE_SPEC).  MODE_SPEC
-// also needs sf (set up here for every frame) and the CTA's record cursor,
-// and folds max |S^g|^2 into *vmax.  CLS: pruning class (see band_class).
+// also needs sf and nmarg (both set up here for every frame; nmarg outside
+// the frame buffer) and the CTA's record cursor, and folds max |S^g|^2 into
+// *vmax.  CLS: pruning class (see band_class); for CLS > 0 the band values
+// X[k] stay in the registers of the thread that computed them and only the
+// mirrors X[NF - k] pass through mz (nb float2 outside the frame buffer), so
+// the last FFT pass needs no barrier of its own.
 template <int NF, int MODE, int CLS = 0>
 __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
                                               float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
                                               float2 *buf, uint32_t *acc, int tid, SpecFrame *sf = nullptr,
-                                              float *vmax = nullptr, SpecCursor *cur = nullptr) {
+                                              int *nmarg = nullptr, float *vmax = nullptr,
+                                              SpecCursor *cur = nullptr, float2 *mz = nullptr) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
+    constexpr bool REG = CLS > 0;
+    constexpr unsigned OMASK = band_mask<NF>(CLS);
     float2 v[16];
-    forward_fft<NF, false, window_mask<NF>(CLS)>(buf, d, x, m * d.hop, 0, false, tid, v);
+    forward_fft<NF, false, window_mask<NF>(CLS), !REG>(buf, d, x, m * d.hop, 0, false, tid, v);
     float2 *zc = buf, *zm = buf + d.nb;
-    scatter_band<NF, band_mask<NF>(CLS)>(zc, zm, d, tid, v);
-    if (MODE == MODE_SPEC && tid == 0) sf->nmarg = 0;   // (sf may live in the frame buffer)
+    if constexpr (REG) store_mirror<NF, OMASK>(mz, d, tid, v);
+    else scatter_band<NF, OMASK>(zc, zm, d, tid, v);
+    if (MODE == MODE_SPEC && tid == 0) *nmarg = 0;
     __syncthreads();
 
+    if constexpr (REG) {
+        if (TPF == NS || tid < NS) {
+            const unsigned span = (unsigned)(d.k_hi - d.k_lo);
+            const int kb0 = tid - d.k_lo;
 #pragma unroll
-    for (int i = 0; i < C::KMAX; ++i) {
-        const int kk = tid + i * TPF;
-        if (kk < d.nb) {
-            const int k = d.k_lo + kk;
-            const float2 zk = zc[kk];
-            const float2 zn = zm[kk];
-            const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-            const float2 Vd = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
-            const size_t o = (size_t)m * d.nb + kk;
-            if (MODE == MODE_STFT) {
-                out0[o] = V;
-                reinterpret_cast<float2 *>(out1)[o] = make_float2(Vd.x * d.dscale, Vd.y * d.dscale);
-                continue;
+            for (int r = 0; r < 16; ++r) {
+                if (!((OMASK >> r) & 1u)) continue;
+                const int kk = kb0 + r * NS;
+                if ((unsigned)kk <= span) frame_bin<MODE>(d, fs, out0, out1, m, kk, v[r], mz[kk], acc, sf, nmarg, vmax);
             }
-            const float mag2 = V.x * V.x + V.y * V.y;
-            // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36)
-            const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
-            int l = -1;
-            if (mag2 > fs.gamma2) {
-                const float f = floorf(fmaf((float)d.z, delta, 0.5f));
-                l = -2;
-                if (f > -1073741824.f && f < 1073741824.f) {
-                    const int lc = d.z * (k - d.k_lo) + (int)f;
-                    if (lc >= 0 && lc < d.nbo) l = lc;
-                }
-            }
-            if (MODE == MODE_MAP) {
-                reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
-                reinterpret_cast<int32_t *>(out1)[o] = l;
-                continue;
-            }
-            if (MODE == MODE_SPEC) {
-                *vmax = fmaxf(*vmax, mag2);
-                if (l >= 0 && !(mag2 > fs.g_ub2)) {
-                    // kept only if |S^g| exceeds the exact threshold: list it, flag its bin
-                    const int i = atomicAdd(&sf->nmarg, 1);
-                    if (i < SPEC_MCAP) sf->item[i] = make_float4(__int_as_float(l), V.x, V.y, mag2);
-                    continue;
-                }
-            }
-            if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < C::KMAX; ++i) {
+            const int kk = tid + i * TPF;
+            if (kk < d.nb) frame_bin<MODE>(d, fs, out0, out1, m, kk, zc[kk], zm[kk], acc, sf, nmarg, vmax);
         }
     }
     // all band reads and atomics done before the T row is read and the next
@@ -562,9 +613,12 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     if (MODE != MODE_T && MODE != MODE_SPEC) return;
     float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
     const int stride = tacc_stride(d.nbo);
-    if (MODE == MODE_SPEC && sf->nmarg > 0) {   // (block-uniform)
-        if (tid < 32) spec_records(d, sf, acc, m, tid, cur);
-        __syncthreads();   // records read the sums before they are cleared, and sf before the next FFT
+    if (MODE == MODE_SPEC) {
+        const int nm = *nmarg;
+        if (nm > 0) {   // (block-uniform)
+            if (tid < 32) spec_records(d, sf, nm, acc, m, tid, cur);
+            __syncthreads();   // records read the sums before they are cleared, and sf before the next FFT
+        }
     }
     for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
     // the zeroing above is ordered before the next frame's atomics by the
@@ -589,20 +643,24 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
         fs.g_ub2 = sc->g_ub2;
     }
     const int stride = tacc_stride(d.nbo);
-    // MODE_SPEC state: in the frame buffer after the band values when it fits
-    // there (no extra shared memory, so no loss of occupancy), else after the
-    // accumulators
+    // CLS > 0: the band's mirror values after the accumulators
+    float2 *mz = reinterpret_cast<float2 *>(acc + 4 * stride);
+    // MODE_SPEC state: the source counter in the frame buffer's slack; the
+    // list in the frame buffer after the band values when it fits there (no
+    // extra shared memory, so no loss of occupancy), else after the
+    // accumulators (and the mirrors)
+    int *nmarg = reinterpret_cast<int *>(buf + C::BUF);
     const size_t band_bytes = (16 * (size_t)d.nb + 15) & ~(size_t)15;
     SpecFrame *sf = (spec_in_frame(d.nb, d.nbo, C::BUF))
                         ? reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(buf) + band_bytes)
-                        : reinterpret_cast<SpecFrame *>(acc + 4 * stride);
+                        : reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(mz) + (CLS > 0 ? mirror_bytes(d.nb) : 0));
     if (MODE == MODE_T || MODE == MODE_SPEC)
         for (int i = tid; i < 4 * stride; i += C::TPF) acc[i] = 0u;
     float vmax = 0.f;
     SpecCursor cur = {0u, 0u, 0u, 0u};
     // (the first __syncthreads in forward_frame orders this before any atomic)
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
-        forward_frame<NF, MODE, CLS>(d, x, fs, out0, out1, m, buf, acc, tid, sf, &vmax, &cur);
+        forward_frame<NF, MODE, CLS>(d, x, fs, out0, out1, m, buf, acc, tid, sf, nmarg, &vmax, &cur, mz);
     if (MODE == MODE_SPEC) {
         vmax = warp_max(vmax);
         if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));

@@ -113,6 +113,17 @@ EDGE = [
          relative=True),
     dict(n=12000, fs=16000.0, L=2049, sigma=256.0, hop=16, nfft=2048, f_lo=3000.0, f_hi=8000.0, z=1,
          gamma=1e-3, relative=True),
+    # pruned radix-16 first pass: band class 1 (k_hi < 3 Nf/16) and class 2 (k_hi < 5 Nf/16) with a
+    # half-length window, at Nf 256 and 4096, k_lo = 0 and > 0, odd z, absolute gamma = 0 (odd z only
+    # at Nf 256: the oracle's zNf-point inverse is a plain DFT when zNf is not a power of two)
+    dict(n=1500, fs=2000.0, L=129, sigma=16.0, hop=6, nfft=256, f_lo=0.0, f_hi=100.0, z=3, gamma=1e-3,
+         relative=True),
+    dict(n=2500, fs=2000.0, L=101, sigma=12.0, hop=3, nfft=256, f_lo=200.0, f_hi=500.0, z=1, gamma=0.0,
+         relative=False),
+    dict(n=30011, fs=16000.0, L=2049, sigma=256.0, hop=24, nfft=4096, f_lo=100.0, f_hi=1500.0, z=2,
+         gamma=1e-3, relative=True),
+    dict(n=9001, fs=16000.0, L=1537, sigma=192.0, hop=40, nfft=4096, f_lo=0.0, f_hi=3500.0, z=2,
+         gamma=1e-3, relative=True),
 ]
 
 
