@@ -534,8 +534,14 @@ __device__ __forceinline__ void frame_bin(const SstDev &d, const FwdScale &fs, f
         return;
     }
     const float mag2 = V.x * V.x + V.y * V.y;
-    // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36)
-    const float delta = -d.c_if * ((Vd.y * V.x - Vd.x * V.y) / mag2);
+    // reassignment offset in bins: -(Nf / 2 pi) Im(S^g' / S^g)   (Eq. 13, 36).
+    // The quotient by the fast reciprocal is within 2 ulp for a divisor in
+    // [2^-126, 2^126]; the (rare) others take the IEEE division.
+    const float num = Vd.y * V.x - Vd.x * V.y;
+    float quo;
+    if (mag2 >= 0x1p-126f && mag2 <= 0x1p126f) quo = __fdividef(num, mag2);
+    else quo = num / mag2;
+    const float delta = -d.c_if * quo;
     int l = -1;
     if (mag2 > fs.gamma2) {
         const float f = floorf(fmaf((float)d.z, delta, 0.5f));
