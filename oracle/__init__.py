@@ -238,6 +238,67 @@ def delta_f(fs: float, nfft: int, z: int = 1) -> float:
     return _load().oro_delta_f(fs, nfft, z)
 
 
+# ------------------------------------------------- after the path: zones,
+# ridges, concentration (plain numpy in FP64 plus the inverse above)
+def zone_mask(nbo: int, ridge, half_width: int) -> np.ndarray:
+    """The zone M_q[m] of Eq. 15 as a boolean (frames x nbo) mask: output bin
+    l of frame m belongs to it iff ridge[m] >= 0 and |l - ridge[m]| <=
+    half_width (a band offset in both directions from the ridge, Sec. 2.2)."""
+    ridge = np.asarray(ridge, dtype=np.int64)
+    l = np.arange(nbo)[None, :]
+    c = ridge[:, None]
+    return (c >= 0) & (np.abs(l - c) <= half_width)
+
+
+def zone_inverse(T, ridge, half_width: int, k_lo: int, nfft: int, z: int, g, hop: int,
+                 n: int, p0: int = 0, np_: int | None = None, mt0: int = 0):
+    """Component recovery by time-frequency filtering (the closing paragraph
+    of Sec. 2.3): the Eq. 25-26 inverse of T with every coefficient outside
+    the zone of Eq. 15 set to zero.  ridge[i] belongs to frame mt0 + i."""
+    T = np.asarray(T, dtype=np.complex128)
+    Tq = np.where(zone_mask(T.shape[1], ridge, half_width), T, 0.0)
+    return inverse(Tq, k_lo, nfft, z, g, hop, n, p0, np_, mt0)
+
+
+def ridge(T, l_lo: int, l_hi: int, smooth: int) -> np.ndarray:
+    """Ridge of one component, one output bin per frame (reading: the paper
+    extracts ridges, Sec. 2.2 and Sec. 5, without stating how).  The energy
+    E[m, l] = sum over |d| <= smooth (frames inside [0, F)) of |T[m + d, l]|^2
+    is maximised over l in [l_lo, l_hi]; ties go to the smallest l; a frame
+    with E = 0 throughout the band gets -1."""
+    P = np.abs(np.asarray(T, dtype=np.complex128)) ** 2
+    F = P.shape[0]
+    band = P[:, l_lo:l_hi + 1]
+    out = np.empty(F, dtype=np.int64)
+    for m in range(F):
+        a, b = max(0, m - smooth), min(F, m + smooth + 1)
+        E = band[a:b].sum(axis=0)
+        i = int(np.argmax(E))   # first of the maxima
+        out[m] = l_lo + i if E[i] > 0.0 else -1
+    return out
+
+
+def ridge_hz(ridge_bins, k_lo: int, z: int, fs: float, nfft: int) -> np.ndarray:
+    """Frequency of output bin l: (k_lo + l / z) fs / Nf (Eq. 28's fine grid)."""
+    r = np.asarray(ridge_bins, dtype=np.float64)
+    return np.where(r >= 0, (k_lo + r / z) * fs / nfft, np.nan)
+
+
+def renyi(T, alpha: float = 3.0, cell: float = 1.0) -> float:
+    """Renyi entropy of order alpha (Eq. 32) of the distribution P = |T|^2 on
+    the TF grid: (1 / (1 - alpha)) log2 sum (P / sum P)^alpha, plus log2 of the
+    grid cell's area (du dxi) when the integrals are read as sums over cells
+    of that area (cell = 1: the plain discrete form)."""
+    if alpha <= 0 or alpha == 1:
+        raise ValueError("alpha must be positive and not 1")
+    P = np.abs(np.asarray(T, dtype=np.complex128)) ** 2
+    tot = P.sum()
+    if tot <= 0:
+        raise ValueError("empty distribution")
+    p = P / tot
+    return float(np.log2(np.sum(p ** alpha)) / (1.0 - alpha) + np.log2(cell))
+
+
 # ---------------------------------------------------------------- pipeline
 def band_bins(fs: float, nfft: int, f_lo: float, f_hi: float):
     """Band [f_lo, f_hi] Hz -> inclusive coarse bins, rounding half up."""
