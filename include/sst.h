@@ -121,6 +121,46 @@ sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, float *tf
 sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n, float *xhat_dev,
                        void *workspace_dev, void *stream);
 
+/* Component recovery by time-frequency filtering (Sec. 2.3, last paragraph;
+ * the zone M_q[m] of Eq. 15): sst_inverse of T with every coefficient
+ * outside the zone set to zero.  Frame m's zone is the output bins l with
+ * |l - ridge[m]| <= half_width, empty where ridge[m] < 0 (a ridge from
+ * sst_ridge, or the caller's own IF track in output bins).
+ *   ridge_dev  : F int32 on the device, 4-byte aligned, read only
+ *   half_width : >= 0, in output bins (z per coarse bin)
+ * T itself is not modified. */
+sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64_t n, const int32_t *ridge_dev,
+                            int32_t half_width, float *xhat_dev, void *workspace_dev, void *stream);
+
+/* Ridge of one component, one output bin per frame.  The paper extracts
+ * ridges (Sec. 2.2 builds the Eq. 15 zone around them; Sec. 5 tracks IFs)
+ * without stating a rule; this one is: E[m, l] = sum over |d| <= smooth,
+ * 0 <= m + d < F, of |T[m + d, l]|^2 (FP32, d ascending), and ridge[m] is
+ * the smallest l in [l_lo, l_hi] maximising E[m, l], or -1 when E[m, l] = 0
+ * throughout.  Its frequency is (k_lo + l/z) fs/Nf.
+ *   tfr_dev : frames x bins complex (row-major, 2*bins floats per frame),
+ *             8-byte aligned
+ *   0 <= l_lo <= l_hi < bins;  0 <= smooth <= SST_RIDGE_MAX_SMOOTH
+ *   ridge_dev : frames int32, fully overwritten
+ * No workspace; asynchronous on `stream`. */
+#define SST_RIDGE_MAX_SMOOTH 32
+sst_status sst_ridge(const float *tfr_dev, int64_t frames, int32_t bins, int32_t l_lo, int32_t l_hi,
+                     int32_t smooth, int32_t *ridge_dev, void *stream);
+
+/* Renyi entropy of order alpha (Eq. 32; Sec. 3.2 uses alpha = 3) of the
+ * distribution P = |T|^2 over a rows x cols grid (row stride ld complex
+ * values): (1 / (1 - alpha)) log2 sum (P / sum P)^alpha + log2(cell), cell
+ * being the area du dxi of a grid cell when the integrals are read as sums
+ * over cells (1: the plain discrete form).  One pass over the data with a
+ * running scale per thread (no overflow of P^alpha), partial sums combined
+ * in FP64 in a fixed order (deterministic).
+ *   alpha > 0, alpha != 1;  out_dev : one double on the device
+ *   workspace_dev : sst_renyi_workspace_bytes() bytes, 256-byte aligned
+ * Returns SST_EINVAL for an empty grid; an all-zero grid gives NaN. */
+size_t sst_renyi_workspace_bytes(void);
+sst_status sst_renyi(const float *tfr_dev, int64_t rows, int32_t cols, int64_t ld, double alpha, double cell,
+                     double *out_dev, void *workspace_dev, void *stream);
+
 /* sst_forward followed by sst_inverse.  tfr_dev receives T and may not be
  * NULL in this version (the inverse reads it back). */
 sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,

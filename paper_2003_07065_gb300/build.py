@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsst.so")
 NFS = (64, 128, 256, 512, 1024, 2048, 4096, 8192)
-HOST_UNITS = ("sst_capi", "sst_batch", "sst_stream", "sst_tc")
+HOST_UNITS = ("sst_capi", "sst_batch", "sst_stream", "sst_tc", "sst_post")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

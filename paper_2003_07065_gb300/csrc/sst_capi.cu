@@ -681,8 +681,12 @@ static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *w
     return SST_OK;
 }
 
-static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st) {
-    SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(pl->d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
+static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st,
+                              const int32_t *zone = nullptr, int zone_hw = 0) {
+    SstDev d = pl->d;
+    d.zone = zone;
+    d.zone_hw = zone_hw;
+    SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
                    "inverse launch");
     int64_t blocks = (pl->d.n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
@@ -705,6 +709,17 @@ SST_API sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n,
     if (s != SST_OK) return s;
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
+}
+
+SST_API sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64_t n, const int32_t *ridge_dev,
+                                    int32_t half_width, float *xhat_dev, void *ws, void *stream) {
+    sst_status s = check_call(plan, tfr_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    if (!ridge_dev) return fail(SST_EINVAL, "ridge pointer is NULL");
+    if (((uintptr_t)ridge_dev) & 3) return fail(SST_EINVAL, "ridge must be 4-byte aligned");
+    if (half_width < 0 || half_width > (1 << 28)) return fail(SST_EINVAL, "half_width = %d out of range", half_width);
+    return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream, ridge_dev, half_width);
 }
 
 SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,

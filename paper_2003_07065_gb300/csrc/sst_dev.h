@@ -61,7 +61,16 @@ struct SstDev {
     const unsigned *gate;  // when set, the pre-pass and forward kernels run only if *gate != 0
     int sample_stride;     // pre-pass: every sample_stride-th group of four frames (0 or 1: all)
     SpecBuf spec;          // forward MODE_SPEC records
+    // component recovery (sst_inverse_zone): when set, the inverse keeps only
+    // the coefficients of output bins l with |l - zone[m]| <= zone_hw (none
+    // where zone[m] < 0), the zone of Eq. 15
+    const int32_t *zone;
+    int zone_hw;
 };
+
+__host__ __device__ __forceinline__ bool in_zone(int l, int c, int hw) {
+    return c >= 0 && (unsigned)(l - c + hw) <= (unsigned)(2 * hw);
+}
 
 __host__ __device__ __forceinline__ int64_t trow_of(const SstDev &d, int64_t m) {
     return d.trow_cap ? m % d.trow_cap : m;

@@ -776,6 +776,9 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
         // synchronous staging: both rows (contiguous in T), regrouped by
         // sub-grid, with the 1/2 weight of the DC and Nyquist destinations
         // (Hermitian completion)
+        // zone centres of the pair (component recovery only)
+        const int za = d.zone ? d.zone[a] : 0;
+        const int zb = d.zone ? (hasb ? d.zone[b] : -1) : 0;
         for (int f = 0; f < 2 && !async; ++f) {
             const float2 *src = T + (size_t)trow_of(d, a + f) * d.nbo;
             const bool have = f == 0 || hasb;
@@ -784,13 +787,21 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                 const float w0 = (k == 0 || 2 * k == NF) ? 0.5f : 1.f;
                 for (int s = 0; s < d.z; ++s) {
                     const int l = d.z * q + s;
-                    float2 t = (have && l < d.nbo) ? __ldg(&src[l]) : make_float2(0.f, 0.f);
+                    const bool keep = !d.zone || in_zone(l, f ? zb : za, d.zone_hw);
+                    float2 t = (have && l < d.nbo && keep) ? __ldg(&src[l]) : make_float2(0.f, 0.f);
                     if (s == 0) t = cscale(t, w0);
                     Tst[(f * d.z + s) * nq + q] = t;
                 }
             }
         }
         __syncthreads();
+        if (async && d.zone) {   // (block-uniform) rows as copied: clear what lies outside the zones
+            for (int i = tid; i < 2 * d.nbo; i += TPF) {
+                const int f = i >= d.nbo ? 1 : 0;
+                if (!in_zone(i - f * d.nbo, f ? zb : za, d.zone_hw)) Tst[i] = make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+        }
 
         float2 racc[TP::NACC];
 #pragma unroll

@@ -68,6 +68,12 @@ def load():
         "sst_forward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_inverse_zone": ([_vp, _vp, _i64, _vp, ctypes.c_int32, _vp, _vp, _vp], ctypes.c_int),
+        "sst_ridge": ([_vp, _i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp],
+                      ctypes.c_int),
+        "sst_renyi_workspace_bytes": ([], ctypes.c_size_t),
+        "sst_renyi": ([_vp, _i64, ctypes.c_int32, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp],
+                      ctypes.c_int),
         "sst_forward_inverse_host": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_stft": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -207,6 +213,25 @@ def sst_forward(plan, x, n, tfr, workspace, stream=None):
 
 def sst_inverse(plan, tfr, n, xhat, workspace, stream=None):
     _check(load().sst_inverse(plan, _ptr(tfr), n, _ptr(xhat), _ptr(workspace), _stream(stream)))
+
+
+def sst_inverse_zone(plan, tfr, n, ridge, half_width, xhat, workspace, stream=None):
+    _check(load().sst_inverse_zone(plan, _ptr(tfr), n, _ptr(ridge), int(half_width), _ptr(xhat), _ptr(workspace),
+                                   _stream(stream)))
+
+
+def sst_ridge(tfr, frames, bins, l_lo, l_hi, smooth, ridge, stream=None):
+    _check(load().sst_ridge(_ptr(tfr), int(frames), int(bins), int(l_lo), int(l_hi), int(smooth), _ptr(ridge),
+                            _stream(stream)))
+
+
+def sst_renyi_workspace_bytes():
+    return int(load().sst_renyi_workspace_bytes())
+
+
+def sst_renyi(tfr, rows, cols, ld, alpha, cell, out, workspace, stream=None):
+    _check(load().sst_renyi(_ptr(tfr), int(rows), int(cols), int(ld), float(alpha), float(cell), _ptr(out),
+                            _ptr(workspace), _stream(stream)))
 
 
 def sst_forward_inverse(plan, x, n, tfr, xhat, workspace, stream=None):
@@ -501,6 +526,31 @@ class Plan:
         xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
         sst_inverse(self.handle, tfr, self.n, xhat, self.workspace)
         return xhat
+
+    def inverse_zone(self, tfr, ridge, half_width, xhat=None):
+        """Component recovery: the inverse restricted to |l - ridge[m]| <= half_width."""
+        import torch
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
+        sst_inverse_zone(self.handle, tfr, self.n, ridge, half_width, xhat, self.workspace)
+        return xhat
+
+    def ridge(self, tfr, l_lo=0, l_hi=None, smooth=0, out=None):
+        """Ridge (output bin per frame) of the component in [l_lo, l_hi]."""
+        import torch
+        l_hi = self.bins - 1 if l_hi is None else l_hi
+        out = torch.empty(self.frames, dtype=torch.int32, device=self.device) if out is None else out
+        sst_ridge(tfr, self.frames, self.bins, l_lo, l_hi, smooth, out)
+        return out
+
+    def renyi(self, tfr, alpha=3.0, cell=1.0, out=None):
+        """Renyi entropy (Eq. 32) of |T|^2 as a one-element float64 device tensor."""
+        import torch
+        if getattr(self, "_renyi_ws", None) is None:
+            self._renyi_ws = torch.empty(max(sst_renyi_workspace_bytes(), 256), dtype=torch.uint8,
+                                         device=self.device)
+        out = torch.empty(1, dtype=torch.float64, device=self.device) if out is None else out
+        sst_renyi(tfr, self.frames, self.bins, self.bins, alpha, cell, out, self._renyi_ws)
+        return out
 
     def forward_inverse(self, x, tfr=None, xhat=None):
         import torch
