@@ -535,6 +535,225 @@ def run_stream(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ steps after the transform
+POST_METRIC = "input samples/s through ridge + zone inverse + Renyi entropy"
+POST_SMOOTH, POST_HW, POST_ALPHA = 2, 16, 3.0
+
+
+def oracle_post_rate(w, budget_s: float = 10.0, n_sample: int = 1 << 15):
+    """The oracle's ridge, zone inverse and entropy on the T of a bounded
+    prefix of the workload (the transform itself untimed); samples/s."""
+    import oracle as O
+    noisy, _ = w.signal()
+    x = noisy[:n_sample].astype(np.float32).astype(np.float64)
+    r = O.sst(x, w.fs, w.L, w.sigma, w.hop, w.nfft, w.f_lo, w.f_hi, w.z, w.gamma, w.relative)
+    g, _ = O.window(w.L, w.sigma)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        rid = O.ridge(r.T, 0, r.T.shape[1] - 1, POST_SMOOTH)
+        O.zone_inverse(r.T, rid, POST_HW, r.k_lo, w.nfft, w.z, g, w.hop, len(x))
+        O.renyi(r.T, POST_ALPHA)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 64:
+            break
+    return reps * n_sample / el, O.get_threads(), f"{reps} x first {n_sample} samples of {w.name}", el
+
+
+def run_post(args):
+    """One step = the steps after the transform on the run-up workload's T
+    (runup_16m_post; runup_4m_post is the profiling-sized case)
+    produced once, untimed: sst_ridge over the whole band (smoothing over
+    +-2 frames), sst_inverse_zone around that ridge (+-16 output bins) and
+    sst_renyi (alpha = 3) of T.  The zone inverse is the dominant kernel (FP32
+    ALU roofline); the ridge and the entropy stream T (HBM roofline each)."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = W.ALL[args.workload[:-len("_post")]]
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle as O
+        O.build()
+        O.set_threads(0)
+        vals = []
+        for _ in range(args.warmup):
+            oracle_post_rate(w, budget_s=0.0, n_sample=1 << 13)
+        for _ in range(args.steps):
+            v, threads, sample, _ = oracle_post_rate(w, budget_s=max(1.0, 30.0 / max(args.steps, 1)))
+            vals.append(v)
+        value = statistics.mean(vals)
+        print(json.dumps({
+            "impl": "reference", "metric": POST_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "smooth": POST_SMOOTH, "half_width": POST_HW,
+                       "alpha": POST_ALPHA},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2003_07065_gb300 import build, sst
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    build.build()
+    sst.load()
+    noisy, _ = w.signal()
+    x_host = torch.from_numpy(noisy.astype(np.float32)).pin_memory()
+    x = x_host.cuda()
+    plan = sst.Plan(**w.params())
+    tfr = plan.forward(x)
+    F, bins = plan.frames, plan.bins
+    ridge = torch.empty(F, dtype=torch.int32, device="cuda")
+    xq = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    ent = torch.empty(1, dtype=torch.float64, device="cuda")
+    rws = torch.empty(max(sst.sst_renyi_workspace_bytes(), 256), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def do_ridge():
+        sst.sst_ridge(tfr, F, bins, 0, bins - 1, POST_SMOOTH, ridge, stream)
+
+    def do_zone():
+        sst.sst_inverse_zone(plan.handle, tfr, w.n, ridge, POST_HW, xq, plan.workspace, stream)
+
+    def do_renyi():
+        sst.sst_renyi(tfr, F, bins, bins, POST_ALPHA, 1.0, ent, rws, stream)
+
+    def step():
+        do_ridge()
+        do_zone()
+        do_renyi()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = sst.sst_launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = timed(step, args.steps)
+    if dist is not None:
+        dist.barrier()
+    launches = sst.sst_launch_count() - launches0
+    clocks = sampler.stop()
+    t_ms = sum(step_ms)
+    if dist is not None:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * w.n * args.steps / (t_ms / 1e3)
+    # each kernel alone, for its roofline
+    ridge_ms = statistics.mean(timed(do_ridge, args.steps))
+    zone_ms = statistics.mean(timed(do_zone, args.steps))
+    renyi_ms = statistics.mean(timed(do_renyi, args.steps))
+
+    # end to end through the C ABI with host buffers: x in, forward, the three
+    # steps, and the component, the ridge and the entropy out
+    xq_host = torch.empty(w.n, dtype=torch.float32).pin_memory()
+    ridge_host = torch.empty(F, dtype=torch.int32).pin_memory()
+    ent_host = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        x.copy_(x_host, non_blocking=True)
+        sst.sst_forward(plan.handle, x, w.n, tfr, plan.workspace, stream)
+        step()
+        xq_host.copy_(xq, non_blocking=True)
+        ridge_host.copy_(ridge, non_blocking=True)
+        ent_host.copy_(ent, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e_s = time.perf_counter() - e0
+    if dist is not None:
+        tt = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_s = float(tt.item())
+    e2e = world * w.n * args.steps / e_s
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak = sst.sst_fp32_peak(stream)
+    fl = flops_per_frame(w)
+    t_bytes = F * bins * 8
+    zone_flops = fl["inverse"] * F
+    ridge_bytes = t_bytes + F * 4            # T once (algorithmic) + the ridge written
+    renyi_bytes = 2 * t_bytes                # two passes: the exact maximum, then the sums
+    roof = {"bound": "alu", "kernel": "inverse_zone", "achieved": zone_flops / (zone_ms / 1e3) / 1e12,
+            "peak": peak, "unit": "TFLOP/s", "frac": zone_flops / (zone_ms / 1e3) / 1e12 / peak, "traffic": None,
+            "peak_note": "FP32 FMA throughput measured in this run (sst_fp32_peak)",
+            "algorithmic_flops_per_launch": zone_flops, "avg_launch_ms": zone_ms,
+            "others": {
+                "ridge": {"bound": "hbm", "avg_launch_ms": ridge_ms, "algorithmic_bytes": ridge_bytes,
+                          "achieved_gbs": ridge_bytes / (ridge_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                          "frac": ridge_bytes / (ridge_ms / 1e3) / 1e9 / hbm if hbm else None},
+                "renyi": {"bound": "hbm", "avg_launch_ms": renyi_ms, "algorithmic_bytes": renyi_bytes,
+                          "achieved_gbs": renyi_bytes / (renyi_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                          "frac": renyi_bytes / (renyi_ms / 1e3) / 1e9 / hbm if hbm else None}}}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        O.set_threads(0)
+        v, threads, sample, el = oracle_post_rate(w, budget_s=10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample, "seconds": el,
+               "cpu_model": cpu_model()}
+    line = {
+        "metric": POST_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "frames": F, "bins": bins, "smooth": POST_SMOOTH,
+                   "half_width": POST_HW, "alpha": POST_ALPHA, "tfr_bytes": t_bytes,
+                   "l2": f"flushed before each timed step (2x L2 write); T ({t_bytes / 1e9:.1f} GB) also exceeds L2",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "kernels": {"ridge": {"ms": ridge_ms}, "inverse_zone": {"ms": zone_ms}, "renyi": {"ms": renyi_ms}},
+        "entropy_bits": float(ent.item()),
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n,
+                "d2h_bytes_per_step": 4 * w.n + 4 * F + 8,
+                "note": "x in, forward, ridge, zone inverse, entropy, component + ridge + entropy out"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +761,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="runup_16m",
-                    choices=sorted(W.ALL) + ["batch256", "stream64", "precision64k_tc"])
+                    choices=sorted(W.ALL) + ["batch256", "stream64", "precision64k_tc", "runup_16m_post",
+                                             "runup_4m_post"])
     ap.add_argument("--seconds", type=float, default=12.0, help="stream64: simulated real-time seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -552,6 +772,8 @@ def main():
         return run_stream(args)
     if args.workload == "precision64k_tc":
         return run_tensor(args)
+    if args.workload.endswith("_post"):
+        return run_post(args)
     w = W.ALL[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
