@@ -136,7 +136,7 @@ def _check_ridge(got, want, T, l_lo, l_hi, smooth):
 
 
 @pytest.mark.parametrize("name", list(CFGS))
-@pytest.mark.parametrize("smooth", [0, 2, 9, 32])
+@pytest.mark.parametrize("smooth", [0, 2, 4, 9, 32])
 def test_ridge_matches_oracle(sst, name, smooth):
     p, _, r = _oracle(name)
     F, nbo = r.T.shape
