@@ -1,15 +1,20 @@
-"""Parity at the benchmark's full size: the run-up workload at N = 2^24
-(524288 frames, Nf 4096, L 2049, hop 32, z = 4, band 0-6.4 kHz, gamma =
-1e-3 max|V|), run by the GPU exactly as the benchmark runs it (one
-sst_forward_inverse with the default one-pass threshold), checked against
-the oracle on outputs it can compute one by one:
+"""Parity at the benchmarks' full sizes, each run by the GPU exactly as the
+benchmark runs it, checked against the oracle on outputs it can compute one
+by one:
 
-* the threshold base: max|V| of the GPU's loudest frame recomputed by the
-  oracle, and no sampled frame louder;
-* 512 sampled frames (the first and last included): STFT, reassignment map
-  and T rows, with the oracle's threshold (1e-3 of that max);
-* x_hat on three 512-sample windows (the start, the end and an interior one),
-  from the oracle's T of every frame covering them."""
+* runup_16m: N = 2^24 (524288 frames, Nf 4096, L 2049, hop 32, z = 4, band
+  0-6.4 kHz, gamma = 1e-3 max|V|), one sst_forward_inverse with the default
+  one-pass threshold;
+* batch256: the 256 mixed channels (204 M samples, 138 GB of TFRs) in one
+  captured graph, four channels checked (the longest, the shortest and two
+  others).
+
+Per checked signal: the threshold base (max|V| of the GPU's loudest frame
+recomputed by the oracle, and no sampled frame louder); sampled frames (the
+first two, the last two and the loudest included): STFT, reassignment map and
+T rows under the oracle's threshold (gamma times that max); x_hat on
+512-sample windows (the start, the end and interior ones) from the oracle's T
+of every frame covering them."""
 import numpy as np
 import pytest
 
@@ -32,52 +37,48 @@ def sst():
     return S
 
 
-def test_runup_16m_sampled_parity(sst):
-    w = W.RUNUP_16M
-    noisy, _ = w.signal()
-    x32 = noisy.astype(np.float32)
+def sampled_check(plan, p, x32, tfr, xhat, n_frames, n_windows, seed):
+    """Compare one signal's GPU outputs (tfr, xhat on the device) with the
+    oracle on sampled frames and windows; returns the map mismatch rate."""
     x64 = x32.astype(np.float64)
-    plan = sst.Plan(**w.params())
-    F, nbo, nf, hop, z = plan.frames, plan.bins, w.nfft, w.hop, w.z
-    M = (w.L - 1) // 2
+    F, nbo, nf, hop, z = plan.frames, plan.bins, p["nfft"], p["hop"], p["z"]
+    M = (p["L"] - 1) // 2
     x = torch.from_numpy(x32).cuda()
-    tfr, xhat = plan.forward_inverse(x)           # the benchmark's call
-    V_g, Vd_g = plan.stft(x)
+    V_g, _ = plan.stft(x)
     _, dest_g = plan.reassign_map(x)
-    torch.cuda.synchronize()
-
-    g, dg = O.window(w.L, w.sigma)
-    k_lo, k_hi = O.band_bins(w.fs, nf, w.f_lo, w.f_hi)
+    g, dg = O.window(p["L"], p["sigma"])
+    k_lo, k_hi = O.band_bins(p["fs"], nf, p["f_lo"], p["f_hi"])
     assert (k_lo, k_hi) == (plan.k_lo, plan.k_hi)
 
-    # ---- the threshold base
+    # the threshold base
     mag2 = V_g[..., 0] ** 2 + V_g[..., 1] ** 2
     m_star = int(torch.argmax(mag2.max(dim=1).values).item())
     vmax_g = float(mag2.max().sqrt().item())
     V1, _ = O.stft(x64, g, dg, hop, nf, k_lo, k_hi, m_star, 1)
     vmax = float(np.abs(V1).max())
     assert abs(vmax_g - vmax) <= STFT_RTOL * vmax, (vmax_g, vmax)
-    gamma = w.gamma * vmax
+    gamma = p["gamma"] * vmax
 
-    # ---- sampled frames
-    rng = np.random.default_rng(2024)
-    frames = np.unique(np.concatenate([[0, 1, F - 2, F - 1, m_star], rng.choice(F, 507, replace=False)]))
-    V_or = np.empty((len(frames), plan.nb), np.complex128)
-    dest_or = np.empty((len(frames), plan.nb), np.int64)
-    om_or = np.empty((len(frames), plan.nb))
+    # sampled frames
+    rng = np.random.default_rng(seed)
+    extra = rng.choice(F, min(F, n_frames), replace=False)
+    frames = np.unique(np.concatenate([[0, min(1, F - 1), max(F - 2, 0), F - 1, m_star], extra]))
+    nb = plan.nb
+    V_or = np.empty((len(frames), nb), np.complex128)
+    dest_or = np.empty((len(frames), nb), np.int64)
+    om_or = np.empty((len(frames), nb))
     T_or = np.empty((len(frames), nbo), np.complex128)
     for i, m in enumerate(frames):
-        r = O.sst(x64, w.fs, w.L, w.sigma, hop, nf, w.f_lo, w.f_hi, z, w.gamma, True, m0=int(m), nm=1,
-                  gamma_abs=gamma)
+        r = O.sst(x64, p["fs"], p["L"], p["sigma"], hop, nf, p["f_lo"], p["f_hi"], z, p["gamma"], True,
+                  m0=int(m), nm=1, gamma_abs=gamma)
         V_or[i], dest_or[i], om_or[i], T_or[i] = r.V[0], r.dest[0], r.omega[0], r.T[0]
     assert np.abs(V_or).max() <= vmax * (1 + STFT_RTOL), "a sampled frame is louder than the threshold base"
     idx = torch.from_numpy(frames).cuda()
-    Vg = as_complex(V_g[idx].cpu().numpy())
-    assert np.abs(Vg - V_or).max() <= STFT_RTOL * vmax
+    assert np.abs(as_complex(V_g[idx].cpu().numpy()) - V_or).max() <= STFT_RTOL * vmax
     dg_rows = dest_g[idx].cpu().numpy().astype(np.int64)
     moved, rate = check_map(dg_rows, dest_or, V_or, gamma, nbo)
     # T: 1e-5 max|V| plus, at both destinations of every moved source and of
-    # every source within the STFT bar of gamma (the one-pass forward's own
+    # every source within the STFT bar of gamma (a threshold from the GPU's own
     # maximum may differ from the map's in the last bit), its modulus
     Tg = as_complex(tfr[idx].cpu().numpy())
     allow = np.zeros(T_or.shape)
@@ -95,16 +96,17 @@ def test_runup_16m_sampled_parity(sst):
     err = np.abs(Tg - T_or)
     assert (err <= T_RTOL * vmax + allow).all(), f"T mismatch, max err {err.max():.3e}"
 
-    # ---- reconstruction windows
+    # reconstruction windows
     xh = xhat.cpu().numpy().astype(np.float64)
-    n, npw = w.n, 512
-    for p0 in (0, n - npw, int(rng.integers(npw, n - 2 * npw))):
+    n = p["n"]
+    npw = min(512, n)
+    starts = [0, n - npw] + [int(v) for v in rng.integers(0, max(1, n - npw), n_windows - 2)]
+    for p0 in starts:
         mlo = max(0, -(-(p0 - M) // hop))
         mhi = min(F - 1, (p0 + npw - 1 + M) // hop)
-        r = O.sst(x64, w.fs, w.L, w.sigma, hop, nf, w.f_lo, w.f_hi, z, w.gamma, True, m0=mlo,
+        r = O.sst(x64, p["fs"], p["L"], p["sigma"], hop, nf, p["f_lo"], p["f_hi"], z, p["gamma"], True, m0=mlo,
                   nm=mhi - mlo + 1, inverse_range=(p0, npw), gamma_abs=gamma)
-        cov = torch.arange(mlo, mhi + 1, device="cuda")
-        dgc = dest_g[cov].cpu().numpy().astype(np.int64)
+        dgc = dest_g[torch.arange(mlo, mhi + 1, device="cuda")].cpu().numpy().astype(np.int64)
         nr = np.abs(np.abs(r.V) - gamma) <= STFT_RTOL * vmax
         mv = (dgc != r.dest) & ~nr
         # a source moved by one fine bin changes r~ by at most (2/Nf)|V| min(2, 2 pi M/(z Nf)),
@@ -115,8 +117,50 @@ def test_runup_16m_sampled_parity(sst):
             per = max(per, (2.0 / nf) * np.abs(r.V[mv]).max() * min(2.0, 2 * np.pi * M / (z * nf)))
         if nr.any():
             per = max(per, (2.0 / nf) * np.abs(r.V[nr]).max())
-        allow = per * np.ceil(w.L / hop) / (np.sqrt(2.0) / hop * 0.5)
+        allow_x = per * np.ceil(p["L"] / hop) / (np.sqrt(2.0) / hop * 0.5)
         e = np.abs(xh[p0:p0 + npw] - r.xhat).max()
-        assert e <= XHAT_RTOL * np.abs(r.xhat).max() + allow, (p0, e, np.abs(r.xhat).max(), allow)
+        assert e <= XHAT_RTOL * np.abs(r.xhat).max() + allow_x, (p0, e, np.abs(r.xhat).max(), allow_x)
+    del V_g, dest_g, mag2
+    return rate
+
+
+def test_runup_16m_sampled_parity(sst):
+    w = W.RUNUP_16M
+    noisy, _ = w.signal()
+    x32 = noisy.astype(np.float32)
+    plan = sst.Plan(**w.params())
+    x = torch.from_numpy(x32).cuda()
+    tfr, xhat = plan.forward_inverse(x)           # the benchmark's call
+    torch.cuda.synchronize()
+    rate = sampled_check(plan, w.params(), x32, tfr, xhat, n_frames=507, n_windows=3, seed=2024)
     plan.close()
     assert rate <= MAP_RATE
+
+
+def test_batch256_sampled_parity(sst):
+    chans = W.batch_channels(256)
+    plans, keep, items = [], [], []
+    for params, x in chans:
+        pl = sst.Plan(**params)
+        xd = torch.from_numpy(x).cuda()
+        t = pl.new_tfr()
+        xh = torch.empty(pl.n, dtype=torch.float32, device="cuda")
+        plans.append(pl)
+        keep.append((xd, t, xh))
+        items.append((pl.handle, xd, pl.n, t, xh))
+    b = sst.sst_batch_create(items, graph=True)    # the benchmark's launch
+    ws = torch.empty(max(sst.sst_batch_workspace(b), 256), dtype=torch.uint8, device="cuda")
+    sst.sst_batch_run(b, ws)
+    torch.cuda.synchronize()
+    lengths = np.array([p["n"] for p, _ in chans])
+    longest, shortest = int(lengths.argmax()), int(lengths.argmin())
+    others = [int(i) for i in np.random.default_rng(7).choice(len(chans), 6, replace=False)
+              if int(i) not in (longest, shortest)][:2]
+    for i in [longest, shortest] + others:
+        params, x = chans[i]
+        _, t, xh = keep[i]
+        rate = sampled_check(plans[i], params, x, t, xh, n_frames=96, n_windows=3, seed=100 + i)
+        assert rate <= MAP_RATE, (i, rate)
+    sst.sst_batch_destroy(b)
+    for pl in plans:
+        pl.close()
