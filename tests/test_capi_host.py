@@ -106,3 +106,27 @@ def test_host_calls_return_promptly(lib):
             "        print(e.status)\n" % ROOT)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
+
+
+def test_post_steps_reject_bad_arguments_on_host(lib):
+    """sst_ridge, sst_renyi and sst_inverse_zone validate before any CUDA call
+    (the pointers below are never dereferenced)."""
+    L = lib.load()
+    t, r = 1 << 12, 1 << 13          # 8-byte aligned stand-ins for device pointers
+    assert L.sst_ridge(None, 10, 20, 0, 19, 0, r, None) == 1
+    assert L.sst_ridge(t, 10, 20, 0, 20, 0, r, None) == 1          # l_hi past the bins
+    assert L.sst_ridge(t, 10, 20, 5, 4, 0, r, None) == 1           # empty band
+    assert L.sst_ridge(t, 10, 20, 0, 19, 33, r, None) == 1         # smoothing past the limit
+    assert L.sst_ridge(t, 10, 20, 0, 19, -1, r, None) == 1
+    assert L.sst_ridge(t + 4, 10, 20, 0, 19, 0, r, None) == 1      # TFR not 8-byte aligned
+    assert L.sst_ridge(t, 0, 20, 0, 19, 0, r, None) == 1           # no frames
+    ws, out = 1 << 16, 1 << 14
+    assert L.sst_renyi_workspace_bytes() >= 256
+    assert L.sst_renyi(None, 10, 20, 20, 3.0, 1.0, out, ws, None) == 1
+    assert L.sst_renyi(t, 10, 20, 20, 1.0, 1.0, out, ws, None) == 1   # alpha = 1
+    assert L.sst_renyi(t, 10, 20, 20, 0.0, 1.0, out, ws, None) == 1
+    assert L.sst_renyi(t, 10, 20, 20, 3.0, 0.0, out, ws, None) == 1   # cell area
+    assert L.sst_renyi(t, 0, 20, 20, 3.0, 1.0, out, ws, None) == 1    # empty grid
+    assert L.sst_renyi(t, 10, 20, 19, 3.0, 1.0, out, ws, None) == 1   # row stride below the columns
+    assert L.sst_renyi(t, 10, 20, 20, 3.0, 1.0, out, ws + 8, None) == 1   # workspace alignment
+    assert L.sst_inverse_zone(None, t, 10, r, 3, out, ws, None) == 1
