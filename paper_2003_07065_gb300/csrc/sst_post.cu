@@ -1,7 +1,7 @@
 // Steps after the transform: ridge extraction on T (the ridges that Sec. 2.2
 // builds the Eq. 15 zone around and Sec. 5 tracks) and the Renyi entropy of
-// Eq. 32 (the concentration measure of Sec. 3.2).  Both read T once from HBM
-// and are bound by it.
+// Eq. 32 (the concentration measure of Sec. 3.2).  Both stream T from HBM:
+// the ridge once, the entropy twice (its exact maximum, then its sums).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
