@@ -7,9 +7,10 @@ by one:
   one-pass threshold;
 * batch256: the 256 mixed channels (204 M samples, 138 GB of TFRs) in one
   captured graph, four channels checked (the longest, the shortest and two
-  others).
+  others);
+* stream64: 64 streams in the benchmark's shape, three compared whole.
 
-Per checked signal: the threshold base (max|V| of the GPU's loudest frame
+Per checked signal of the first two: the threshold base (max|V| of the GPU's loudest frame
 recomputed by the oracle, and no sampled frame louder); sampled frames (the
 first two, the last two and the loudest included): STFT, reassignment map and
 T rows under the oracle's threshold (gamma times that max); x_hat on
@@ -164,3 +165,67 @@ def test_batch256_sampled_parity(sst):
     sst.sst_batch_destroy(b)
     for pl in plans:
         pl.close()
+
+
+def test_stream64_fullsize_parity(sst):
+    """The streaming configuration at its benchmark shape: 64 streams at
+    25.6 kHz (Nf 2048, hop 16, band 0-8 kHz, z = 2), each 40 chunks of 8192
+    samples (12.8 s), pushed round-robin with a tick per round; three streams
+    deliver their TFR and are compared whole with the oracle (the bars of the
+    single-stream oracle test), the other 61 run reconstruction-only.  Each
+    checked stream's absolute threshold is 1e-3 of the oracle's own max|V|."""
+    from paper_2003_07065_gb300 import signals
+    fs, chunk, nchunks, nstreams = 25600.0, 8192, 40, 64
+    P = dict(fs=fs, L=1025, sigma=128.0, hop=16, nfft=2048, f_lo=0.0, f_hi=8000.0, z=2)
+    n = chunk * nchunks
+    sigs = [signals.chirp_fm_mix(n, fs, 10.0, seed=(5, 1000 + i))[0].astype(np.float32) for i in range(nstreams)]
+    checked = (0, 31, 63)
+    g, dg = O.window(P["L"], P["sigma"])
+    k_lo, k_hi = O.band_bins(fs, P["nfft"], P["f_lo"], P["f_hi"])
+    gammas = {i: 1e-3 * O.global_max_abs_v(sigs[i].astype(np.float64), g, dg, P["hop"], P["nfft"], k_lo, k_hi)
+              for i in checked}
+    svc = sst.sst_service_create(nstreams, 64 << 30)
+    ids = [sst.sst_stream_open(svc, 8.0, chunk, gamma=gammas.get(i, 0.02), xhat_only=i not in checked, **P)
+           for i in range(nstreams)]
+    nb = P["z"] * k_hi + 1
+    acc = {i: ([], []) for i in range(nstreams)}
+
+    def drain_all():
+        fins = []
+        for i, sid in enumerate(ids):
+            fin = False
+            while True:
+                t, fc, xq, fsmp, fin = sst.sst_stream_poll(svc, sid, nb)
+                if len(t):
+                    acc[i][0].append(t)
+                if len(xq):
+                    acc[i][1].append(xq)
+                if not len(t) and not len(xq):
+                    break
+            fins.append(fin)
+        return fins
+
+    for c in range(nchunks):
+        for i, sid in enumerate(ids):
+            sst.sst_stream_push(svc, sid, sigs[i][c * chunk:(c + 1) * chunk])
+            if c == nchunks - 1:
+                sst.sst_stream_close(svc, sid)
+        sst.sst_service_tick(svc)
+        drain_all()
+    for _ in range(1000):
+        sst.sst_service_tick(svc)
+        if all(drain_all()):
+            break
+    sst.sst_service_destroy(svc)
+    for i in range(nstreams):
+        assert sum(len(a) for a in acc[i][1]) == n, i
+    for i in checked:
+        T = np.concatenate(acc[i][0])
+        xh = np.concatenate(acc[i][1]).astype(np.float64)
+        r = O.sst(sigs[i].astype(np.float64), fs, P["L"], P["sigma"], P["hop"], P["nfft"], P["f_lo"], P["f_hi"],
+                  P["z"], gammas[i], False, inverse_range=(0, n))
+        assert T.shape == r.T.shape, (i, T.shape, r.T.shape)
+        vmax = np.abs(r.V).max()
+        diff = np.abs(T - r.T) > 1e-5 * vmax
+        assert diff.sum() <= max(4, 1e-4 * diff.size), (i, diff.sum())
+        assert np.abs(xh - r.xhat).max() <= 1e-3 * np.abs(r.xhat).max(), i
