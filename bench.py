@@ -159,6 +159,23 @@ def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
 
 
 # ------------------------------------------------------------------ reference arm
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over the ranks of the process group (x itself without
+    one): the job's time is its slowest replica's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank per step, the
+    job takes the slowest rank's time (weak scaling)."""
+    return world * units_per_rank * steps / seconds
+
+
 def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -661,12 +678,8 @@ def run_post(args):
         dist.barrier()
     launches = sst.sst_launch_count() - launches0
     clocks = sampler.stop()
-    t_ms = sum(step_ms)
-    if dist is not None:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * w.n * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(sum(step_ms), dist)
+    value = job_rate(world, w.n, args.steps, t_ms / 1e3)
     # each kernel alone, for its roofline
     ridge_ms = statistics.mean(timed(do_ridge, args.steps))
     zone_ms = statistics.mean(timed(do_zone, args.steps))
@@ -692,12 +705,8 @@ def run_post(args):
     e0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    e_s = time.perf_counter() - e0
-    if dist is not None:
-        tt = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
-    e2e = world * w.n * args.steps / e_s
+    e_s = max_over_ranks(time.perf_counter() - e0, dist)
+    e2e = job_rate(world, w.n, args.steps, e_s)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -841,12 +850,8 @@ def main():
     launches = sst.sst_launch_count() - launches0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = sum(step_ms)
-    if dist is not None:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * w.n * args.steps / (t_ms / 1e3)
+    t_ms = max_over_ranks(sum(step_ms), dist)
+    value = job_rate(world, w.n, args.steps, t_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers
     for _ in range(2):
@@ -855,12 +860,8 @@ def main():
     e0 = time.perf_counter()
     for _ in range(args.steps):
         sst.sst_forward_inverse_host(plan.handle, x_host, w.n, xhat_host, x, tfr, xhat, plan.workspace, stream)
-    e_s = time.perf_counter() - e0
-    if dist is not None:
-        tt = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
-    e2e = world * w.n * args.steps / e_s
+    e_s = max_over_ranks(time.perf_counter() - e0, dist)
+    e2e = job_rate(world, w.n, args.steps, e_s)
 
     if rank != 0:
         if dist is not None:
