@@ -49,6 +49,21 @@ def test_zones_tiling_the_band_add_up_to_the_inverse():
     assert np.abs(parts[0]).max() > 0 and np.abs(parts[1]).max() > 0
 
 
+@pytest.mark.parametrize("z", [1, 3])
+def test_zone_tiling_small_grid(z):
+    """The tiling identity with an odd subdivision (its zNf-point inverse is a
+    plain DFT in the oracle, so the grid is kept small) and without one."""
+    n, fs, nfft, L, sigma, hop = 3000, 8000.0, 256, 129, 16.0, 8
+    x = S.tone(n, fs, 37.0 * fs / nfft, amp=0.8, phase=0.2) + S.tone(n, fs, 90.3 * fs / nfft, amp=0.4, phase=1.0)
+    r = O.sst(x, fs, L, sigma, hop, nfft, 0.0, fs / 2, z, 0.0, False, inverse_range=(0, n))
+    g, _ = O.window(L, sigma)
+    F, nbo = r.T.shape
+    w = (nbo + 2) // 6 + 1
+    total = sum(O.zone_inverse(r.T, np.full(F, c, np.int64), w, r.k_lo, nfft, z, g, hop, n)
+                for c in (w, 3 * w + 1, 5 * w + 2))
+    np.testing.assert_allclose(total, r.xhat, rtol=0, atol=1e-12 * np.abs(r.xhat).max())
+
+
 def test_zone_edge_is_inclusive_and_no_ridge_means_empty():
     F, nbo, l0, w = 40, 64, 20, 3
     T = np.zeros((F, nbo), np.complex128)
