@@ -128,7 +128,8 @@ sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n, float *
  * sst_ridge, or the caller's own IF track in output bins).
  *   ridge_dev  : F int32 on the device, 4-byte aligned, read only
  *   half_width : >= 0, in output bins (z per coarse bin)
- * T itself is not modified. */
+ * T itself is not modified.  Errors: as sst_inverse, and SST_EINVAL for a
+ * NULL or misaligned ridge or a negative half_width. */
 sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64_t n, const int32_t *ridge_dev,
                             int32_t half_width, float *xhat_dev, void *workspace_dev, void *stream);
 
@@ -142,7 +143,8 @@ sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64_t n, co
  *             8-byte aligned
  *   0 <= l_lo <= l_hi < bins;  0 <= smooth <= SST_RIDGE_MAX_SMOOTH
  *   ridge_dev : frames int32, fully overwritten
- * No workspace; asynchronous on `stream`. */
+ * No workspace; asynchronous on `stream`.  Errors: SST_EINVAL (pointers,
+ * alignment, band or smooth out of range, before any CUDA call), SST_ECUDA. */
 #define SST_RIDGE_MAX_SMOOTH 32
 sst_status sst_ridge(const float *tfr_dev, int64_t frames, int32_t bins, int32_t l_lo, int32_t l_hi,
                      int32_t smooth, int32_t *ridge_dev, void *stream);
@@ -156,7 +158,8 @@ sst_status sst_ridge(const float *tfr_dev, int64_t frames, int32_t bins, int32_t
  * in FP64 in a fixed order (deterministic).
  *   alpha > 0, alpha != 1;  out_dev : one double on the device
  *   workspace_dev : sst_renyi_workspace_bytes() bytes, 256-byte aligned
- * Returns SST_EINVAL for an empty grid; an all-zero grid gives NaN. */
+ * Errors: SST_EINVAL (pointers, alignment, an empty grid, ld < cols, alpha,
+ * cell; before any CUDA call), SST_ECUDA.  An all-zero grid gives NaN. */
 size_t sst_renyi_workspace_bytes(void);
 sst_status sst_renyi(const float *tfr_dev, int64_t rows, int32_t cols, int64_t ld, double alpha, double cell,
                      double *out_dev, void *workspace_dev, void *stream);
