@@ -299,6 +299,69 @@ def renyi(T, alpha: float = 3.0, cell: float = 1.0) -> float:
     return float(np.log2(np.sum(p ** alpha)) / (1.0 - alpha) + np.log2(cell))
 
 
+# ------------------------------------------------------- second-order IF
+# The paper names a second-order extension as future work (Sec. 6) without
+# formulas.  Written here from the STFT's derivatives in the paper's
+# convention, V^h[m, k] = sum_j x[m H + j] h[j] e^{-i w j} (Eq. 8-9, phase
+# measured from the frame centre, w = 2 pi k / Nf): for any window h,
+# d/dt V^h = -V^{h'} + i w V^h, d/dw V^h = -i V^{t h}.  Hence the complex IF
+# w~ = w + i V^{g'}/V (its real part is Eq. 13), the complex time
+# t~ = t + V^{tg}/V, and the local chirp rate
+# q~ = (d/dt w~) / (d/dt t~) = i ((V^{g'})^2 - V^{g''} V) / (V^{tg} V^{g'} - V^{tg'} V);
+# the second-order IF is Re(w~ + q~ (t - t~)) = Re(w~ - q~ V^{tg}/V), which a
+# linear chirp returns exactly.
+def window2(L: int, sigma: float):
+    """g'' = (j^2/sigma^4 - 1/sigma^2) g, t g = j g and t g' = j g' on j = -M..M
+    (derivatives of the Gaussian of Sec. 2.1, in samples)."""
+    g, dg = window(L, sigma)
+    j = np.arange(L, dtype=np.float64) - (L - 1) // 2
+    return g, dg, (j * j / sigma ** 4 - 1.0 / sigma ** 2) * g, j * g, j * dg
+
+
+def if2(x, L: int, sigma: float, hop: int, nfft: int, k_lo: int, k_hi: int, m0: int = 0,
+        nm: int | None = None):
+    """First- and second-order IF estimates in coarse bins for frames
+    [m0, m0 + nm), bins [k_lo, k_hi], with V; where the chirp-rate denominator
+    vanishes (no local chirp can be measured) the second-order value is the
+    first-order one.  Returns (V, omega1, omega2, q) with q in bins per
+    sample."""
+    g, dg, d2g, tg, tdg = window2(L, sigma)
+    V, Vd = stft(x, g, dg, hop, nfft, k_lo, k_hi, m0, nm)
+    V2, Vt = stft(x, d2g, tg, hop, nfft, k_lo, k_hi, m0, nm)
+    Vtd, _ = stft(x, tdg, tdg, hop, nfft, k_lo, k_hi, m0, nm)
+    k = np.arange(k_lo, k_hi + 1, dtype=np.float64)[None, :]
+    w = 2 * np.pi * k / nfft
+    with np.errstate(divide="ignore", invalid="ignore"):
+        wt = w + 1j * Vd / V
+        den = Vt * Vd - Vtd * V
+        q = 1j * (Vd * Vd - V2 * V) / den
+        w2 = np.where(np.abs(den) > 0, (wt - q * Vt / V).real, wt.real)
+    to_bins = nfft / (2 * np.pi)
+    return V, wt.real * to_bins, w2 * to_bins, q * to_bins
+
+
+def reassign2(V, omega2, k_lo: int, k_hi: int, z: int, gamma: float):
+    """Eq. 27-29 with the second-order IF: each source with |V| > gamma goes to
+    l = floor(z (omega2 - k_lo) + 1/2) when 0 <= l <= z N_r.  Returns (dest, T)
+    with dest -1 below the threshold, -2 off the grid."""
+    V = np.asarray(V, dtype=np.complex128)
+    nm, nb = V.shape
+    nbo = z * (k_hi - k_lo) + 1
+    dest = np.full((nm, nb), -1, dtype=np.int64)
+    T = np.zeros((nm, nbo), dtype=np.complex128)
+    for m in range(nm):
+        for kk in range(nb):
+            if not abs(V[m, kk]) > gamma or not np.isfinite(omega2[m, kk]):
+                continue
+            l = int(np.floor(z * (omega2[m, kk] - k_lo) + 0.5))
+            if 0 <= l < nbo:
+                dest[m, kk] = l
+                T[m, l] += V[m, kk]
+            else:
+                dest[m, kk] = -2
+    return dest, T
+
+
 # ---------------------------------------------------------------- pipeline
 def band_bins(fs: float, nfft: int, f_lo: float, f_hi: float):
     """Band [f_lo, f_hi] Hz -> inclusive coarse bins, rounding half up."""
@@ -355,6 +418,36 @@ def sst(x, fs: float, L: int, sigma: float, hop: int, nfft: int, f_lo: float,
         p0, np_ = inverse_range
         xhat = inverse(T, k_lo, nfft, z, g, hop, n, p0, np_, mt0=m0)
     return Result(V, Vd, omega, dest, T, leak, gam, k_lo, k_hi, m0, xhat)
+
+
+def sst2(x, fs: float, L: int, sigma: float, hop: int, nfft: int, f_lo: float, f_hi: float, z: int,
+         gamma: float, relative: bool, m0: int = 0, nm: int | None = None,
+         inverse_range: tuple[int, int] | None = None, gamma_abs: float | None = None) -> Result:
+    """sst with the second-order IF (if2) in the reassignment: the same STFT,
+    threshold (gamma, or gamma max|V| over all frames when relative), grid
+    (Eq. 27-29) and inverse (Eq. 25-26).  Result.omega holds the second-order
+    IF; leak is not tracked (zeros)."""
+    x = _c(x)
+    n = len(x)
+    g, dg = window(L, sigma)
+    k_lo, k_hi = band_bins(fs, nfft, f_lo, f_hi)
+    F = frames(n, hop)
+    if nm is None:
+        nm = F - m0
+    V, _, omega2, _ = if2(x, L, sigma, hop, nfft, k_lo, k_hi, m0, nm)
+    if gamma_abs is not None:
+        gam = float(gamma_abs)
+    elif relative:
+        gam = gamma * global_max_abs_v(x, g, dg, hop, nfft, k_lo, k_hi)
+    else:
+        gam = float(gamma)
+    dest, T = reassign2(V, omega2, k_lo, k_hi, z, gam)
+    _, Vd = stft(x, g, dg, hop, nfft, k_lo, k_hi, m0, nm)
+    xhat = None
+    if inverse_range is not None:
+        p0, np_ = inverse_range
+        xhat = inverse(T, k_lo, nfft, z, g, hop, n, p0, np_, mt0=m0)
+    return Result(V, Vd, omega2, dest, T, np.zeros(nm, np.complex128), gam, k_lo, k_hi, m0, xhat)
 
 
 def global_max_abs_v(x, g, dg, hop, nfft, k_lo, k_hi, chunk: int = 4096) -> float:
