@@ -318,13 +318,16 @@ def window2(L: int, sigma: float):
     return g, dg, (j * j / sigma ** 4 - 1.0 / sigma ** 2) * g, j * g, j * dg
 
 
+IF2_MIN_DT = 1e-3   # |d/dt t~| = |V^{tg} V^{g'} - V^{tg'} V| / |V|^2 below this: first order
+
+
 def if2(x, L: int, sigma: float, hop: int, nfft: int, k_lo: int, k_hi: int, m0: int = 0,
         nm: int | None = None):
     """First- and second-order IF estimates in coarse bins for frames
-    [m0, m0 + nm), bins [k_lo, k_hi], with V; where the chirp-rate denominator
-    vanishes (no local chirp can be measured) the second-order value is the
-    first-order one.  Returns (V, omega1, omega2, q) with q in bins per
-    sample."""
+    [m0, m0 + nm), bins [k_lo, k_hi], with V.  Where the complex time barely
+    moves with t (|d/dt t~| <= IF2_MIN_DT, e.g. at an impulse) the chirp rate
+    is ill-conditioned and the second-order value is the first-order one.
+    Returns (V, omega1, omega2, q) with q in bins per sample."""
     g, dg, d2g, tg, tdg = window2(L, sigma)
     V, Vd = stft(x, g, dg, hop, nfft, k_lo, k_hi, m0, nm)
     V2, Vt = stft(x, d2g, tg, hop, nfft, k_lo, k_hi, m0, nm)
@@ -335,7 +338,7 @@ def if2(x, L: int, sigma: float, hop: int, nfft: int, k_lo: int, k_hi: int, m0: 
         wt = w + 1j * Vd / V
         den = Vt * Vd - Vtd * V
         q = 1j * (Vd * Vd - V2 * V) / den
-        w2 = np.where(np.abs(den) > 0, (wt - q * Vt / V).real, wt.real)
+        w2 = np.where(np.abs(den) > IF2_MIN_DT * np.abs(V) ** 2, (wt - q * Vt / V).real, wt.real)
     to_bins = nfft / (2 * np.pi)
     return V, wt.real * to_bins, w2 * to_bins, q * to_bins
 

@@ -98,3 +98,14 @@ def test_sst2_equals_sst_on_a_tone():
     np.testing.assert_allclose(b.T[inner], a.T[inner], rtol=0, atol=1e-12 * np.abs(a.T).max())
     ps = slice(2 * M + HOP, n - 2 * M - HOP)
     np.testing.assert_allclose(b.xhat[ps], a.xhat[ps], rtol=0, atol=1e-12 * np.abs(a.xhat).max())
+
+
+def test_impulse_falls_back_to_first_order():
+    """At an impulse the complex time does not move with t (d/dt t~ = 0): the
+    chirp rate is undefined and the second-order IF is the first-order one."""
+    n = 8192
+    x = np.zeros(n)
+    x[4000] = 1.0
+    V, w1, w2, q = O.if2(x, L, SIGMA, HOP, NFFT, 10, 500, m0=4000 // HOP - 2, nm=5)
+    ok = np.abs(V) > 1e-6 * np.abs(V).max()
+    np.testing.assert_array_equal(w2[ok], w1[ok])
