@@ -50,3 +50,28 @@ def test_single_rank_needs_no_group():
     import bench
     assert bench.max_over_ranks(7.5) == 7.5
     assert bench.job_rate(1, 100, 3, 0.5) == 600.0
+
+
+def test_roofline_arithmetic_of_the_headline_workload():
+    """The per-frame algorithmic counts the benchmark's roofline divides by,
+    for runup_16m (Nf 4096, L 2049, z = 4, 513 band bins, 2049 output bins):
+    forward 5 Nf log2 Nf + 4 L + 20 nb, inverse 2.5 z Nf log2 Nf + 8 z L;
+    T written once by the forward and read once by the inverse."""
+    import bench
+    from paper_2003_07065_gb300 import workloads as W
+    w = W.RUNUP_16M
+    fl, by = bench.flops_per_frame(w), bench.bytes_per_frame(w)
+    assert fl["forward"] == 5 * 4096 * 12 + 4 * 2049 + 20 * 513 == 264216
+    assert fl["inverse"] == 2.5 * 4 * 4096 * 12 + 8 * 4 * 2049 == 557088
+    assert by["forward"] == 4 * 32 + 8 * 2049 and by["inverse"] == 8 * 2049 + 4 * 32
+    F = -(-w.n // w.hop)
+    assert F == 524288 and by["inverse"] * F == 8661237760
+
+
+def test_oracle_baseline_sample_is_bounded():
+    """The CPU baseline times the oracle on a bounded prefix of the workload
+    (whole path: STFTs, IF, reassignment, inverse) and reports samples/s."""
+    import bench
+    from paper_2003_07065_gb300 import workloads as W
+    v, threads, sample, el = bench.oracle_sample_rate(W.RUNUP_16M, budget_s=0.0, n_max=1 << 12)
+    assert v > 0 and threads >= 1 and "first 4096 samples of runup_16m" in sample
