@@ -1,7 +1,8 @@
-"""The benchmark's multi-rank bookkeeping, on CPU: with --gpus N every rank
-runs its own replica and the job's time is the slowest rank's.  Two gloo
-ranks (world size 2, rendezvous on 127.0.0.1) must agree on that time and on
-the whole-job rate computed from it."""
+"""The benchmark's host-side logic, on CPU.  Multi-rank bookkeeping: with
+--gpus N every rank runs its own replica and the job's time is the slowest
+rank's; two gloo ranks (world size 2, rendezvous on 127.0.0.1) must agree on
+that time and on the whole-job rate computed from it.  Also the roofline's
+per-frame counts and the bounded oracle baseline."""
 import multiprocessing as mp
 import os
 import socket
