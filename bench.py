@@ -384,8 +384,8 @@ def run_tensor(args):
     import torch
     from paper_2003_07065_gb300 import build, sst
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
-    sst.load()
+    build.build_tc()
+    sst.load_tc()
     w = W.PRECISION_64K
     noisy, clean = w.signal()
     x = torch.from_numpy(noisy.astype(np.float32)).cuda()

@@ -76,6 +76,17 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
     }
 }
 
+cudaError_t launch_absx(const float *x, int64_t n, float *partial, int grid, cudaStream_t st) {
+    k_absx<<<grid, 256, 0, st>>>(x, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma(const float *partial, int count, float frac2, int from_x, float bound_mul, int log2_nb,
+                         SstScalars *sc, float *maxv_out, const unsigned *gate, cudaStream_t st) {
+    k_gamma<<<1, 256, 0, st>>>(partial, count, frac2, from_x, bound_mul, log2_nb, sc, maxv_out, gate);
+    return cudaGetLastError();
+}
+
 // ---- one-pass relative threshold (run_forward_spec)
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -11,16 +11,26 @@
 #include "sst_launch.h"
 
 #define SST_API extern "C" __attribute__((visibility("default")))
+// helpers of libsst.so that the tensor-form library (libsst_tc.so, linked
+// against it) calls too, so both share one error message, launch counter
+// and profile record
+#define SST_SHARED __attribute__((visibility("default")))
 
 namespace sst {
 
 // error reporting: sets the thread-local message returned by sst_last_error
-sst_status fail(sst_status s, const char *fmt, ...);
-sst_status cuda_fail(cudaError_t e, const char *what);
-void count_launch();
+SST_SHARED sst_status fail(sst_status s, const char *fmt, ...);
+SST_SHARED sst_status cuda_fail(cudaError_t e, const char *what);
+SST_SHARED void count_launch();
 // raise (never lower) a kernel's dynamic shared-memory limit, so plans,
 // batches and streams with different needs can share the kernels
 cudaError_t raise_smem(const KernelTable *kt, int kind, size_t bytes);
+// launchers of two small kernels of libsst.so (k_absx: max |x| per CTA into
+// partial[0, grid); k_gamma: the call scalars from pre-pass partials)
+SST_SHARED cudaError_t launch_absx(const float *x, int64_t n, float *partial, int grid, cudaStream_t st);
+SST_SHARED cudaError_t launch_gamma(const float *partial, int count, float frac2, int from_x, float bound_mul,
+                                    int log2_nb, SstScalars *sc, float *maxv_out, const unsigned *gate,
+                                    cudaStream_t st);
 
 #define SST_CU(call, what)                                      \
     do {                                                        \
@@ -30,8 +40,8 @@ cudaError_t raise_smem(const KernelTable *kt, int kind, size_t bytes);
 
 // per-kernel timing (sst_profile_enable): events around each launch
 enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER };
-bool profiling_on();
-void profile_record(int kind, cudaEvent_t a, cudaEvent_t b);
+SST_SHARED bool profiling_on();
+SST_SHARED void profile_record(int kind, cudaEvent_t a, cudaEvent_t b);
 
 struct ProfScope {
     int kind;

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "sst_internal.h"
+#include "sst_tc.h"
 #include "sst_async.cuh"
 #include "sst_kernels.cuh"
 
@@ -1127,12 +1128,10 @@ static sst_status tc_scalars(sst_tc_plan_t t, const float *x, cudaStream_t st) {
         // into one word and every epilogue CTA derives gamma and the scale
     } else {
         const int grid = (int)std::min<int64_t>((d.n + 255) / 256, 1024);
-        SST_LAUNCHED_K(PK_ABSMAX, st, (k_absx<<<grid, 256, 0, st>>>(x, d.n, t->partial + 1), cudaGetLastError()),
-                       "absx launch");
+        SST_LAUNCHED_K(PK_ABSMAX, st, launch_absx(x, d.n, t->partial + 1, grid, st), "absx launch");
         SST_LAUNCHED_K(PK_GAMMA, st,
-                       (k_gamma<<<1, 256, 0, st>>>(t->partial + 1, grid, t->base->gamma_frac2, 1, t->base->sum_abs_g,
-                                                   d.log2_nb, t->sc, nullptr, nullptr),
-                        cudaGetLastError()),
+                       launch_gamma(t->partial + 1, grid, t->base->gamma_frac2, 1, t->base->sum_abs_g, d.log2_nb,
+                                    t->sc, nullptr, nullptr, st),
                        "gamma launch");
     }
     return SST_OK;

@@ -1,10 +1,12 @@
-"""ctypes binding of libsst.so (declared in include/sst.h).
+"""ctypes binding of libsst.so (declared in include/sst.h) and of the
+tensor-core band form's libsst_tc.so (include/sst_tc.h).
 
 Argument marshalling only: every function here forwards to the C entry point
 of the same name, passing device pointers (``tensor.data_ptr()``) and the
-``cudaStream_t`` of a torch stream.  The library must have been built
-(``paper_2003_07065_gb300.build.build()``); loading fails loudly otherwise,
-and there is no CPU fallback.
+``cudaStream_t`` of a torch stream.  The libraries must have been built
+(``paper_2003_07065_gb300.build.build()``, ``build.build_tc()``); loading
+fails loudly otherwise, and there is no CPU fallback.  libsst_tc.so is loaded
+only when a ``sst_tc_*`` function is first called.
 """
 from __future__ import annotations
 
@@ -50,6 +52,11 @@ def lib_path() -> str:
     return _build.LIB
 
 
+def tc_loaded() -> bool:
+    """Whether this process has loaded libsst_tc.so."""
+    return _tc_lib is not None
+
+
 def load():
     """Load libsst.so; raises if it has not been built."""
     global _lib
@@ -82,19 +89,6 @@ def load():
         "sst_fp32_peak": ([ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
         "sst_threshold_stats": ([_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
-        "sst_tc_plan_create": ([_vp, ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
-        "sst_tc_plan_destroy": ([_vp], None),
-        "sst_tc_plan_query": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64),
-                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
-        "sst_tc_plan_set_cluster": ([_vp, ctypes.c_int32], ctypes.c_int),
-        "sst_tc_plan_tune": ([_vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)],
-                             ctypes.c_int),
-        "sst_tc_forward": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
-        "sst_tc_stft": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
-        "sst_tc_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
-        "sst_tc_contract": ([_vp, _vp, _i64, _vp], ctypes.c_int),
-        "sst_tc_check": ([_vp, _vp], ctypes.c_int),
-        "sst_tc_plan_test_withhold": ([_vp], ctypes.c_int),
         "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
                               ctypes.POINTER(_vp)], ctypes.c_int),
         "sst_batch_workspace": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -137,6 +131,44 @@ def load():
         f.argtypes = args
         f.restype = res
     _lib = lib
+    return lib
+
+
+_tc_lib = None
+
+
+def load_tc():
+    """Load libsst_tc.so, the tensor-core band form (single-GPU programs
+    only; it links against libsst.so, loaded first).  Raises if it has not
+    been built (``build.build_tc()``)."""
+    global _tc_lib
+    if _tc_lib is not None:
+        return _tc_lib
+    load()
+    path = _build.TC_LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsst_tc.so not built at {path}: run paper_2003_07065_gb300.build.build_tc()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "sst_tc_plan_create": ([_vp, ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
+        "sst_tc_plan_destroy": ([_vp], None),
+        "sst_tc_plan_query": ([_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i64),
+                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "sst_tc_plan_set_cluster": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sst_tc_plan_tune": ([_vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)],
+                             ctypes.c_int),
+        "sst_tc_forward": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+        "sst_tc_stft": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_tc_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_tc_contract": ([_vp, _vp, _i64, _vp], ctypes.c_int),
+        "sst_tc_check": ([_vp, _vp], ctypes.c_int),
+        "sst_tc_plan_test_withhold": ([_vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _tc_lib = lib
     return lib
 
 
@@ -269,53 +301,53 @@ FORMS = {"bf16": SST_FORM_BF16, "bf16x3": SST_FORM_BF16X3, "tf32": SST_FORM_TF32
 
 def sst_tc_plan_create(plan, form: int) -> int:
     h = _vp()
-    _check(load().sst_tc_plan_create(plan, form, ctypes.byref(h)))
+    _check(load_tc().sst_tc_plan_create(plan, form, ctypes.byref(h)))
     return h.value
 
 
 def sst_tc_plan_destroy(tc) -> None:
-    load().sst_tc_plan_destroy(tc)
+    load_tc().sst_tc_plan_destroy(tc)
 
 
 def sst_tc_plan_query(tc) -> dict:
     hv, fl, cl = ctypes.c_int32(), _i64(), ctypes.c_int32()
-    _check(load().sst_tc_plan_query(tc, ctypes.byref(hv), ctypes.byref(fl), ctypes.byref(cl)))
+    _check(load_tc().sst_tc_plan_query(tc, ctypes.byref(hv), ctypes.byref(fl), ctypes.byref(cl)))
     return {"hankel_view": bool(hv.value), "gemm_flops": fl.value, "cluster": cl.value}
 
 
 def sst_tc_plan_set_cluster(tc, cluster: int) -> None:
-    _check(load().sst_tc_plan_set_cluster(tc, cluster))
+    _check(load_tc().sst_tc_plan_set_cluster(tc, cluster))
 
 
 def sst_tc_plan_tune(tc, x, n, stream=None) -> tuple:
     """(chosen cluster size, its contraction time in ms)."""
     cl, ms = ctypes.c_int32(), ctypes.c_float()
-    _check(load().sst_tc_plan_tune(tc, _ptr(x), n, _stream(stream), ctypes.byref(cl), ctypes.byref(ms)))
+    _check(load_tc().sst_tc_plan_tune(tc, _ptr(x), n, _stream(stream), ctypes.byref(cl), ctypes.byref(ms)))
     return cl.value, ms.value
 
 
 def sst_tc_forward(tc, x, n, tfr, stream=None):
-    _check(load().sst_tc_forward(tc, _ptr(x), n, _ptr(tfr), _stream(stream)))
+    _check(load_tc().sst_tc_forward(tc, _ptr(x), n, _ptr(tfr), _stream(stream)))
 
 
 def sst_tc_stft(tc, x, n, V, Vd, stream=None):
-    _check(load().sst_tc_stft(tc, _ptr(x), n, _ptr(V), _ptr(Vd), _stream(stream)))
+    _check(load_tc().sst_tc_stft(tc, _ptr(x), n, _ptr(V), _ptr(Vd), _stream(stream)))
 
 
 def sst_tc_reassign_map(tc, x, n, omega, dest, stream=None):
-    _check(load().sst_tc_reassign_map(tc, _ptr(x), n, _ptr(omega), _ptr(dest), _stream(stream)))
+    _check(load_tc().sst_tc_reassign_map(tc, _ptr(x), n, _ptr(omega), _ptr(dest), _stream(stream)))
 
 
 def sst_tc_contract(tc, x, n, stream=None):
-    _check(load().sst_tc_contract(tc, _ptr(x), n, _stream(stream)))
+    _check(load_tc().sst_tc_contract(tc, _ptr(x), n, _stream(stream)))
 
 
 def sst_tc_check(tc, stream=None):
-    _check(load().sst_tc_check(tc, _stream(stream)))
+    _check(load_tc().sst_tc_check(tc, _stream(stream)))
 
 
 def sst_tc_plan_test_withhold(tc):
-    _check(load().sst_tc_plan_test_withhold(tc))
+    _check(load_tc().sst_tc_plan_test_withhold(tc))
 
 
 def sst_fp32_peak(stream=None) -> float:

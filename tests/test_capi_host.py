@@ -12,11 +12,12 @@ from paper_2003_07065_gb300 import build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
+def declared_functions(header=None):
+    """Functions declared in include/<header> (every header when None)."""
     names = set()
     inc = os.path.join(ROOT, "include")
     for f in os.listdir(inc):
-        if f.endswith(".h"):
+        if f.endswith(".h") and (header is None or f == header):
             txt = open(os.path.join(inc, f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
             names |= set(re.findall(r"\b(sst_[a-z0-9_]+)\s*\(", txt))
@@ -25,7 +26,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    path = build.build()
+    build.build()
+    build.build_tc()
     from paper_2003_07065_gb300 import sst as S
     S.load()
     return S
@@ -39,8 +41,45 @@ def test_header_declares_entry_points():
 
 def test_library_exports_every_declared_symbol(lib):
     so = ctypes.CDLL(build.LIB)
-    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    missing = [n for n in declared_functions("sst.h") if not hasattr(so, n)]
     assert not missing, missing
+    assert set(declared_functions()) == set(declared_functions("sst.h")) | set(declared_functions("sst_tc.h"))
+
+
+def test_tensor_library_exports_its_symbols(lib):
+    so = ctypes.CDLL(build.TC_LIB)
+    names = declared_functions("sst_tc.h")
+    assert names and all(n.startswith("sst_tc_") for n in names)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # the tensor form lives in its own library only
+    base = ctypes.CDLL(build.LIB)
+    assert not any(hasattr(base, n) for n in names)
+
+
+def test_multi_gpu_library_has_no_cluster_multicast_loads():
+    """libsst.so, the library every multi-GPU program loads, is built from
+    csrc/*.cu, *.cuh, *.h alone: none of them issues a multicast TMA load or
+    a multicast commit (the tensor form, which does, is csrc/tc/, built into
+    libsst_tc.so)."""
+    csrc = os.path.join(ROOT, "paper_2003_07065_gb300", "csrc")
+    for f in os.listdir(csrc):
+        path = os.path.join(csrc, f)
+        if os.path.isfile(path) and f.endswith((".cu", ".cuh", ".h")):
+            assert "multicast" not in open(path).read(), f
+
+
+def test_binding_loads_tensor_library_only_on_demand():
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2003_07065_gb300 import build, sst\n"
+            "build.build(); sst.load()\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "assert 'libsst.so' in maps and 'libsst_tc.so' not in maps, 'tc loaded'\n"
+            "assert not sst.tc_loaded()\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
 
 
 def test_status_strings(lib):

@@ -37,8 +37,8 @@ def sst():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2003_07065_gb300 import build, sst as S
-    build.build()
-    S.load()
+    build.build_tc()
+    S.load_tc()
     return S
 
 
