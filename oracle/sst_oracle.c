@@ -273,6 +273,27 @@ int oro_normaliser(const double *g, int L, int hop, int64_t F, int64_t p0, int64
 /* must cover every frame that touches the output range.                     */
 /* mode 0 = Eq. 26 normaliser, mode 1 = Eq. 11 WOLA normaliser (Sum g^2).     */
 /* ------------------------------------------------------------------------ */
+/* r~[m, t] for t in [0, L) of one frame (Eq. 25 on the zero-padded z Nf grid),
+ * from its T row; re, im are G = z Nf doubles of scratch. */
+static void frame_rtilde(const double *Trow, int k_lo, int nbo, int nfft, int z, int L, int M,
+                         double *re, double *im, double *rt)
+{
+    int64_t G = (int64_t)z * nfft;
+    memset(re, 0, sizeof(double) * (size_t)G);
+    memset(im, 0, sizeof(double) * (size_t)G);
+    for (int l = 0; l < nbo; ++l) {
+        int64_t kk = (int64_t)z * k_lo + l;
+        double w = (kk == 0 || 2 * kk == G) ? 0.5 : 1.0;
+        double a = -2.0 * ORO_PI * (double)((kk * M) % G) / (double)G;
+        double c = cos(a), s = sin(a);
+        double tr = Trow[2 * l], ti = Trow[2 * l + 1];
+        re[kk] += w * (tr * c - ti * s);
+        im[kk] += w * (tr * s + ti * c);
+    }
+    transform(re, im, G, +1);
+    for (int t = 0; t < L; ++t) rt[t] = (2.0 / (double)nfft) * re[t % G];
+}
+
 int oro_inverse(const double *T, int64_t mt0, int64_t ntf, int k_lo, int nbo, int nfft, int z,
                 const double *g, int L, int hop, int64_t n, int64_t p0, int64_t np,
                 int mode, double *xhat)
@@ -289,38 +310,49 @@ int oro_inverse(const double *T, int64_t mt0, int64_t ntf, int k_lo, int nbo, in
     if (mhi > F - 1) mhi = F - 1;
     if (mlo < mt0 || mhi > mt0 + ntf - 1) return -3;  /* T does not cover the range */
 
+    /* Frames are taken in chunks: the r~ of a chunk's frames are independent
+     * (Eq. 25) and computed in parallel; they are then overlap-added one frame
+     * after another in ascending frame order (Eq. 26), so every output sample
+     * sums its frames in the same order for any number of threads. */
+    const int64_t chunk = 256;
     double *num = (double *)calloc((size_t)np, sizeof(double));
-    double *re = (double *)malloc(sizeof(double) * (size_t)G);
-    double *im = (double *)malloc(sizeof(double) * (size_t)G);
-    if (!num || !re || !im) { free(num); free(re); free(im); return -2; }
-
-    /* frames in ascending order; each adds its windowed segment */
-    for (int64_t m = mlo; m <= mhi; ++m) {
-        const double *Trow = T + 2 * (size_t)(m - mt0) * nbo;
-        memset(re, 0, sizeof(double) * (size_t)G);
-        memset(im, 0, sizeof(double) * (size_t)G);
-        for (int l = 0; l < nbo; ++l) {
-            int64_t kk = (int64_t)z * k_lo + l;
-            double w = (kk == 0 || 2 * kk == G) ? 0.5 : 1.0;
-            double a = -2.0 * ORO_PI * (double)((kk * M) % G) / (double)G;
-            double c = cos(a), s = sin(a);
-            double tr = Trow[2 * l], ti = Trow[2 * l + 1];
-            re[kk] += w * (tr * c - ti * s);
-            im[kk] += w * (tr * s + ti * c);
+    double *seg = (double *)malloc(sizeof(double) * (size_t)chunk * (size_t)L);
+    if (!num || !seg) { free(num); free(seg); return -2; }
+    int failed = 0;
+    for (int64_t c0 = mlo; c0 <= mhi && !failed; c0 += chunk) {
+        int64_t cn = (mhi - c0 + 1 < chunk) ? mhi - c0 + 1 : chunk;
+#pragma omp parallel
+        {
+            double *re = (double *)malloc(sizeof(double) * (size_t)G);
+            double *im = (double *)malloc(sizeof(double) * (size_t)G);
+            if (!re || !im) {
+#pragma omp atomic write
+                failed = 1;
+            }
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < cn; ++i)
+                if (re && im)
+                    frame_rtilde(T + 2 * (size_t)(c0 + i - mt0) * nbo, k_lo, nbo, nfft, z, L, M, re, im,
+                                 seg + (size_t)i * L);
+            free(re);
+            free(im);
         }
-        transform(re, im, G, +1);
-        for (int t = 0; t < L; ++t) {
-            int64_t p = m * (int64_t)hop - M + t;
-            if (p < p0 || p > pend) continue;
-            double rt = (2.0 / (double)nfft) * re[t % G];
-            num[p - p0] += g[t] * rt;
+        if (failed) break;
+        for (int64_t i = 0; i < cn; ++i) {
+            int64_t m = c0 + i;
+            for (int t = 0; t < L; ++t) {
+                int64_t p = m * (int64_t)hop - M + t;
+                if (p < p0 || p > pend) continue;
+                num[p - p0] += g[t] * seg[(size_t)i * L + t];
+            }
         }
     }
+    if (failed) { free(num); free(seg); return -2; }
     for (int64_t i = 0; i < np; ++i) {
         double D = normaliser(g, L, hop, F, p0 + i, mode);
         xhat[i] = num[i] / D;
     }
-    free(num); free(re); free(im);
+    free(num); free(seg);
     return 0;
 }
 

@@ -293,6 +293,32 @@ def test_inverse_matches_brute_force_eq25():
         np.testing.assert_allclose(xr, num / den, atol=1e-12 * np.abs(num / den).max())
 
 
+def test_inverse_independent_of_thread_count():
+    """The inverse computes each frame's r~ (Eq. 25) in parallel and
+    overlap-adds them in ascending frame order (Eq. 26): one thread and all
+    threads give the same bits, over several frame chunks and a sub-range."""
+    n, hop, nfft, L, z = 6000, 5, 128, 97, 2
+    x = np.random.default_rng(31).standard_normal(n)
+    g, dg = O.window(L, 12.0)
+    k_lo, k_hi = 3, 50
+    V, Vd = O.stft(x, g, dg, hop, nfft, k_lo, k_hi)
+    _, _, T, _ = O.reassign(V, Vd, k_lo, k_hi, nfft, z, 1e-3 * np.abs(V).max())
+    before = O.get_threads()
+    try:
+        O.set_threads(1)
+        one = O.inverse(T, k_lo, nfft, z, g, hop, n)
+        part1 = O.inverse(T, k_lo, nfft, z, g, hop, n, p0=1234, np_=2345)
+        O.set_threads(0)
+        many = O.inverse(T, k_lo, nfft, z, g, hop, n)
+        partn = O.inverse(T, k_lo, nfft, z, g, hop, n, p0=1234, np_=2345)
+    finally:
+        O.set_threads(before)
+    assert T.shape[0] > 3 * 256   # several chunks of frames
+    assert np.array_equal(one, many)
+    assert np.array_equal(part1, partn)
+    assert np.array_equal(one[1234:1234 + 2345], part1)
+
+
 @pytest.mark.parametrize("z,frac", [(1, 0.0), (2, 0.5), (4, 0.25)])
 def test_inverse_reconstructs_tone(z, frac):
     """A tone on a (fine) bin centre is squeezed into one bin and the direct
