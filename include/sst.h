@@ -98,6 +98,40 @@ void sst_plan_destroy(sst_plan_t plan);
 sst_status sst_plan_query(sst_plan_t plan, int64_t *frames, int32_t *bins,
                           int32_t *k_lo, int32_t *k_hi, size_t *workspace_bytes);
 
+/* ---- Parameter guard (Sec. 4).  How far the frequency axis may be
+ * downsampled before synchrosqueezing stops sharpening the TFR.  A Gaussian
+ * window of standard deviation sigma_s seconds spreads a ridge over
+ * sigma_f = 1 / (2 pi sigma_s) Hz (Eq. 35).  Coefficients still move to the
+ * ridge while the coarse interval Delta f = fs / nfft = Hf fs / n (Eq. 12,
+ * Hf = n / nfft) stays below 1.5 sigma_f (Eq. 37), i.e. Hf < 3 n / (4 pi
+ * sigma_s fs) (Eq. 38), or, by the finite-difference model of Eq. 43-45,
+ * below sqrt(2) sigma_f (Eq. 46), i.e. Hf < sqrt(2) sigma_f n / fs.
+ * Subdivision (z) refines the output grid, not Delta f, so it does not
+ * enter the bounds.  sigma_s = sigma / fs for the built-in window; for a
+ * supplied window g it is taken from the second moment of g^2,
+ * sigma^2 = 2 sum j^2 g[j]^2 / sum g[j]^2 (exact for a Gaussian). */
+typedef struct {
+    double sigma_s;          /* window standard deviation, seconds */
+    double sigma_f_hz;       /* Eq. 35 */
+    double hf;               /* Hf = n / nfft */
+    double hf_max_eq38;      /* Eq. 38 bound on Hf */
+    double hf_max_eq46;      /* Eq. 46 bound on Hf */
+    double delta_f_hz;       /* coarse frequency interval fs / nfft (Eq. 12) */
+    double delta_f_fine_hz;  /* output grid interval fs / (z nfft) (Eq. 28) */
+    double delta_f_max_eq37_hz;  /* 1.5 sigma_f (Eq. 37) */
+    double delta_f_max_eq46_hz;  /* sqrt(2) sigma_f (Eq. 46) */
+    uint32_t flags;          /* SST_GUARD_*: the bounds Hf reaches or exceeds */
+} sst_param_report;
+#define SST_GUARD_EQ38 0x1u  /* Hf >= the Eq. 38 bound */
+#define SST_GUARD_EQ46 0x2u  /* Hf >= the Eq. 46 bound */
+/* Fills *out for a parameter set.  Host arithmetic only: no device is
+ * needed or touched.  SST_EINVAL for parameters sst_plan_create rejects as
+ * invalid (out untouched).  A plan beyond a bound is not an error: the flags
+ * report it and the caller decides. */
+sst_status sst_params_check(const sst_params *params, sst_param_report *out);
+/* The same report for an existing plan. */
+sst_status sst_plan_check(sst_plan_t plan, sst_param_report *out);
+
 /* Forward SST (Sec. 2.2, 2.4): per frame, the packed Nf-point FFT of
  * x*g + i*x*g' gives S^g and S^g' (Eq. 9, split by Hermitian symmetry), the
  * IF estimate omega = k - (Nf/2pi) Im(S^g'/S^g) (Eq. 13), the threshold

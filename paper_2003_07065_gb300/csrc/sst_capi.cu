@@ -297,6 +297,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     if (!pl) return fail(SST_ENOMEM, "host allocation failed");
     pl->p = p;
     pl->p.g = pl->p.dg = nullptr;
+    pl->custom_window = params->g != nullptr;
     pl->device = dev;
     pl->num_sms = prop.multiProcessorCount;
     pl->kt = kt;
@@ -550,6 +551,58 @@ SST_API sst_status sst_plan_query(sst_plan_t plan, int64_t *frames, int32_t *bin
     if (k_lo) *k_lo = plan->d.k_lo;
     if (k_hi) *k_hi = plan->d.k_hi;
     if (workspace_bytes) *workspace_bytes = plan->ws_bytes;
+    return SST_OK;
+}
+
+// ------------------------------------------------------------ parameter guard
+// Sec. 4: Eq. 35 (sigma_f), Eq. 37-38 and Eq. 46 (bounds on Hf = n / nfft).
+// sigma_samples is the window's standard deviation in samples.
+static void guard_report(const sst_params &p, double sigma_samples, sst_param_report *out) {
+    sst_param_report r;
+    memset(&r, 0, sizeof r);
+    r.sigma_s = sigma_samples / p.fs;
+    r.sigma_f_hz = 1.0 / (2.0 * M_PI * r.sigma_s);
+    r.hf = (double)p.n / (double)p.nfft;
+    r.hf_max_eq38 = 3.0 * (double)p.n / (4.0 * M_PI * r.sigma_s * p.fs);
+    r.hf_max_eq46 = std::sqrt(2.0) * r.sigma_f_hz * (double)p.n / p.fs;
+    r.delta_f_hz = p.fs / (double)p.nfft;
+    r.delta_f_fine_hz = p.fs / ((double)p.nfft * (double)p.z);
+    r.delta_f_max_eq37_hz = 1.5 * r.sigma_f_hz;
+    r.delta_f_max_eq46_hz = std::sqrt(2.0) * r.sigma_f_hz;
+    if (r.hf >= r.hf_max_eq38) r.flags |= SST_GUARD_EQ38;
+    if (r.hf >= r.hf_max_eq46) r.flags |= SST_GUARD_EQ46;
+    *out = r;
+}
+
+// standard deviation (samples) of a window: sqrt(2 sum j^2 g^2 / sum g^2),
+// which is sigma for g proportional to exp(-j^2 / (2 sigma^2))
+static double window_sigma(const double *g, int L) {
+    const int M = (L - 1) / 2;
+    double s0 = 0.0, s2 = 0.0;
+    for (int i = 0; i < L; ++i) {
+        const double j = (double)(i - M), e = g[i] * g[i];
+        s0 += e;
+        s2 += j * j * e;
+    }
+    return s0 > 0.0 ? std::sqrt(2.0 * s2 / s0) : 0.0;
+}
+
+SST_API sst_status sst_params_check(const sst_params *params, sst_param_report *out) {
+    if (!out) return fail(SST_EINVAL, "out is NULL");
+    sst_status st = validate(params);
+    if (st != SST_OK && st != SST_EUNSUPPORTED) return st;
+    const double sig = params->g ? window_sigma(params->g, params->L) : params->sigma;
+    if (!(sig > 0.0)) return fail(SST_EINVAL, "the window has no spread (sum of g^2 is zero)");
+    guard_report(*params, sig, out);
+    return SST_OK;
+}
+
+SST_API sst_status sst_plan_check(sst_plan_t plan, sst_param_report *out) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    if (!out) return fail(SST_EINVAL, "out is NULL");
+    const double sig = plan->custom_window ? window_sigma(plan->g64.data(), plan->p.L) : plan->p.sigma;
+    if (!(sig > 0.0)) return fail(SST_EINVAL, "the window has no spread (sum of g^2 is zero)");
+    guard_report(plan->p, sig, out);
     return SST_OK;
 }
 

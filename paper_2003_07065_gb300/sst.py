@@ -36,6 +36,18 @@ class sst_params(ctypes.Structure):
                 ("z", ctypes.c_int32), ("gamma", ctypes.c_double), ("flags", ctypes.c_uint32)]
 
 
+class sst_param_report(ctypes.Structure):
+    _fields_ = [("sigma_s", ctypes.c_double), ("sigma_f_hz", ctypes.c_double), ("hf", ctypes.c_double),
+                ("hf_max_eq38", ctypes.c_double), ("hf_max_eq46", ctypes.c_double),
+                ("delta_f_hz", ctypes.c_double), ("delta_f_fine_hz", ctypes.c_double),
+                ("delta_f_max_eq37_hz", ctypes.c_double), ("delta_f_max_eq46_hz", ctypes.c_double),
+                ("flags", ctypes.c_uint32)]
+
+
+SST_GUARD_EQ38 = 0x1
+SST_GUARD_EQ46 = 0x2
+
+
 class sst_batch_item(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("x", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("tfr", ctypes.c_void_p), ("xhat", ctypes.c_void_p)]
@@ -72,6 +84,8 @@ def load():
         "sst_plan_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sst_params_check": ([ctypes.POINTER(sst_params), ctypes.POINTER(sst_param_report)], ctypes.c_int),
+        "sst_plan_check": ([_vp, ctypes.POINTER(sst_param_report)], ctypes.c_int),
         "sst_forward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -225,6 +239,31 @@ def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float,
     _check(lib.sst_plan_create(ctypes.byref(p), ctypes.byref(out)))
     del keep
     return out.value
+
+
+def _report(r) -> dict:
+    out = {name: getattr(r, name) for name, _ in sst_param_report._fields_}
+    out["beyond_eq38"] = bool(r.flags & SST_GUARD_EQ38)
+    out["beyond_eq46"] = bool(r.flags & SST_GUARD_EQ46)
+    return out
+
+
+def sst_params_check(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
+                     z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
+                     g=None, dg=None) -> dict:
+    """Parameter guard of Sec. 4 (Eq. 35, 38, 46) for a parameter set; host
+    arithmetic, no device needed."""
+    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg)
+    r = sst_param_report()
+    _check(load().sst_params_check(ctypes.byref(p), ctypes.byref(r)))
+    del keep
+    return _report(r)
+
+
+def sst_plan_check(plan: int) -> dict:
+    r = sst_param_report()
+    _check(load().sst_plan_check(plan, ctypes.byref(r)))
+    return _report(r)
 
 
 def sst_plan_destroy(plan: int) -> None:
