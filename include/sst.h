@@ -242,6 +242,20 @@ sst_status sst_fp32_peak(double *tflops, void *stream);
 sst_status sst_threshold_stats(sst_plan_t plan, const void *workspace, int64_t *waiting, int64_t *bins,
                                int32_t *fell_back);
 
+/* Status of the last inverse (sst_inverse, sst_inverse_zone,
+ * sst_forward_inverse) that used `workspace`.  The inverse stages each pair
+ * of T rows in shared memory with one asynchronous bulk copy and waits for
+ * it with a bounded wait (about a second).  Should a wait ever give up, the
+ * tile is staged with ordinary loads instead, so the result is still
+ * correct, and this call reports SST_ETIMEOUT (with the reason in
+ * sst_last_error).  Synchronises `stream`; SST_OK otherwise. */
+sst_status sst_check(sst_plan_t plan, const void *workspace, void *stream);
+/* Test hook of that path: in the next inverse of this plan one CTA does not
+ * issue its first row copy, so its bounded waits run out (about two
+ * seconds), it stages its tile synchronously and the next sst_check reports
+ * SST_ETIMEOUT.  Nothing faults or hangs. */
+sst_status sst_test_withhold_row_copy(sst_plan_t plan);
+
 /* Forward SST (as sst_forward) that allocates nothing and takes no
  * workspace.  The paper has no counterpart: this exists for callers that
  * cannot call cudaMalloc at the point where they run the transform, e.g. a
@@ -257,12 +271,19 @@ sst_status sst_threshold_stats(sst_plan_t plan, const void *workspace, int64_t *
  * with SST_EUNSUPPORTED and a message giving both sizes.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.
+ * The address is cached per device for the life of the process; it does not
+ * survive cudaDeviceReset, so a process that resets a device must not call
+ * this entry point on that device afterwards.
  * All calls share the one array and it keeps the last call's contents; every
  * element a call reads is written earlier in the same call, so nothing needs
  * clearing.  Calls whose work overlaps on the GPU (other streams, other
  * threads, other plans) race on the array: serialise them. */
 #define SST_STATIC_SCRATCH_BYTES 65536
 sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *stream);
+/* Test hook: sst_forward_static treats the array as holding only `floats`
+ * floats (0 restores its real size), so that its rejection of plans that
+ * need more can be exercised. */
+sst_status sst_test_static_capacity(size_t floats);
 
 /* ---- Batched execution (many channels, uneven lengths, mixed parameters).
  * A batch groups the channels' work by DFT length and runs each group as one

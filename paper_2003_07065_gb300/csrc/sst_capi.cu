@@ -745,11 +745,17 @@ static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *w
     return SST_OK;
 }
 
+// the inverse's status word (SST_DEV_*), in the workspace's 256-byte header
+static unsigned *ws_status(sst_plan_t, void *ws) { return (unsigned *)((char *)ws + 192); }
+
 static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st,
                               const int32_t *zone = nullptr, int zone_hw = 0) {
     SstDev d = pl->d;
     d.zone = zone;
     d.zone_hw = zone_hw;
+    d.status = ws_status(pl, ws);
+    SST_CU(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st), "status reset");
+    d.test_withhold = pl->test_withhold.exchange(0) ? 1 : 0;
     SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
                    "inverse launch");
     int64_t blocks = (pl->d.n + 255) / 256;
@@ -867,6 +873,7 @@ static constexpr size_t kStaticHeader = 64;
 static __device__ __align__(256) float g_static_scratch[kStaticFloats];
 static std::mutex g_static_mu;
 static float *g_static_addr[256];
+static std::atomic<size_t> g_static_test_cap{0};   // test hook: a smaller capacity (0: the array's)
 
 static sst_status static_scratch_address(int dev, float **out) {
     if (dev < 0 || dev >= 256) return fail(SST_EUNSUPPORTED, "device ordinal %d out of range", dev);
@@ -888,9 +895,10 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     if (n != plan->d.n)
         return fail(SST_EINVAL, "n = %lld differs from the plan's n = %lld", (long long)n, (long long)plan->d.n);
     const size_t need = kStaticHeader + (size_t)plan->grid_absmax;
-    if (need > kStaticFloats)
+    const size_t cap = g_static_test_cap.load() ? std::min(g_static_test_cap.load(), kStaticFloats) : kStaticFloats;
+    if (need > cap)
         return fail(SST_EUNSUPPORTED, "this plan's pre-pass needs %zu scratch floats; the static array holds %zu",
-                    need, kStaticFloats);
+                    need, cap);
     int dev = -1;
     SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != plan->device) return fail(SST_EINVAL, "plan was created on device %d, current is %d", plan->device, dev);
@@ -905,6 +913,28 @@ SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64
     SST_CU(plan->kt->forward(plan->d, plan->kind_fwd_t, x_dev, sc, tfr_dev, nullptr, plan->grid_fwd, plan->smem_fwd_t, st),
            "forward launch");
     count_launch();
+    return SST_OK;
+}
+
+SST_API sst_status sst_test_static_capacity(size_t floats) {
+    g_static_test_cap.store(floats);
+    return SST_OK;
+}
+
+SST_API sst_status sst_check(sst_plan_t plan, const void *ws, void *stream) {
+    if (!plan || !ws) return fail(SST_EINVAL, "plan or workspace is NULL");
+    SST_CU(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronise");
+    unsigned w = 0;
+    SST_CU(cudaMemcpy(&w, (const char *)ws + 192, sizeof w, cudaMemcpyDeviceToHost), "status read");
+    if (w & SST_DEV_WAIT_EXPIRED)
+        return fail(SST_ETIMEOUT, "the inverse gave up waiting for a staged T row and staged it synchronously%s",
+                    (w & SST_DEV_COPY_LOST) ? "; the row copy had not landed after a second bounded wait" : "");
+    return SST_OK;
+}
+
+SST_API sst_status sst_test_withhold_row_copy(sst_plan_t plan) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    plan->test_withhold.store(1);
     return SST_OK;
 }
 

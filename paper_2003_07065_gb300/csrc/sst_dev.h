@@ -66,7 +66,17 @@ struct SstDev {
     // where zone[m] < 0), the zone of Eq. 15
     const int32_t *zone;
     int zone_hw;
+    // status word of the call (sst_check), or null: the inverse ORs in
+    // SST_DEV_WAIT_EXPIRED when a bounded wait on a staged T row gave up (the
+    // tile is then staged synchronously; results are unaffected), and
+    // SST_DEV_COPY_LOST when the row copy had still not landed after a
+    // second bounded wait
+    unsigned *status;
+    // test hook: CTA 0 does not issue its first row copy, so that wait expires
+    int test_withhold;
 };
+#define SST_DEV_WAIT_EXPIRED 0x1u
+#define SST_DEV_COPY_LOST 0x2u
 
 __host__ __device__ __forceinline__ bool in_zone(int l, int c, int hw) {
     return c >= 0 && (unsigned)(l - c + hw) <= (unsigned)(2 * hw);

@@ -755,7 +755,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     __syncthreads();
     if (async && tid == 0) {
         mbar_expect_tx(rbar, pair_bytes);
-        bulk_g2s(Tst, tile_rows, pair_bytes, rbar);
+        if (!(d.test_withhold && tile == 0)) bulk_g2s(Tst, tile_rows, pair_bytes, rbar);
     }
 
     for (int pr = 0; pr < d.B / 2; ++pr) {
@@ -768,7 +768,10 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             int ok = 1;
             if (tid == 0) {
                 ok = mbar_wait(rbar, (uint32_t)(pr & 1)) ? 1 : 0;
-                if (!ok) mbar_wait(rbar, (uint32_t)(pr & 1));
+                if (!ok) {
+                    const bool landed = mbar_wait(rbar, (uint32_t)(pr & 1));
+                    if (d.status) atomicOr(d.status, SST_DEV_WAIT_EXPIRED | (landed ? 0u : SST_DEV_COPY_LOST));
+                }
             }
             ok = __syncthreads_and(ok);
             if (!ok) async = false;

@@ -101,6 +101,9 @@ def load():
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
         "sst_fp32_peak": ([ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
+        "sst_check": ([_vp, _vp, _vp], ctypes.c_int),
+        "sst_test_static_capacity": ([ctypes.c_size_t], ctypes.c_int),
+        "sst_test_withhold_row_copy": ([_vp], ctypes.c_int),
         "sst_threshold_stats": ([_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
@@ -394,6 +397,20 @@ def sst_fp32_peak(stream=None) -> float:
     t = ctypes.c_double()
     _check(load().sst_fp32_peak(ctypes.byref(t), _stream(stream)))
     return t.value
+
+
+def sst_test_static_capacity(floats: int):
+    _check(load().sst_test_static_capacity(int(floats)))
+
+
+def sst_check(plan, workspace, stream=None):
+    """Raises SstError(SST_ETIMEOUT) if the last inverse on this workspace gave
+    up a bounded wait (its output is still correct)."""
+    _check(load().sst_check(plan, _ptr(workspace), _stream(stream)))
+
+
+def sst_test_withhold_row_copy(plan):
+    _check(load().sst_test_withhold_row_copy(plan))
 
 
 def sst_threshold_stats(plan, workspace) -> dict:

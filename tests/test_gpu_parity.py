@@ -176,3 +176,36 @@ def test_inverse_unaligned_rows(sst):
     torch.cuda.synchronize()
     assert torch.equal(xhat, xh2)
     plan.close()
+
+
+def test_inverse_wait_expiry_reported(sst):
+    """A row copy that never lands (test hook: CTA 0 does not issue it) makes
+    the inverse's bounded waits run out; that CTA stages its tile
+    synchronously, the result keeps its bits, sst_check reports SST_ETIMEOUT,
+    and the next inverse is clean again."""
+    w = W.CHIRP_FM_64K
+    x = torch.from_numpy(w.signal()[0].astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    tfr, xhat = plan.forward_inverse(x)
+    sst.sst_check(plan.handle, plan.workspace)
+    sst.sst_test_withhold_row_copy(plan.handle)
+    xh2 = plan.inverse(tfr)
+    with pytest.raises(sst.SstError) as e:
+        sst.sst_check(plan.handle, plan.workspace)
+    assert e.value.status == 5
+    assert torch.equal(xhat, xh2)
+    xh3 = plan.inverse(tfr)
+    sst.sst_check(plan.handle, plan.workspace)
+    assert torch.equal(xhat, xh3)
+    plan.close()
+
+
+def test_plan_check_matches_params_check(sst):
+    w = W.ALL["runup_256k"]
+    p = w.params()
+    plan = sst.Plan(**p)
+    a = sst.sst_plan_check(plan.handle)
+    b = sst.sst_params_check(**p)
+    assert a == b
+    assert a["hf"] == p["n"] / p["nfft"]
+    plan.close()
