@@ -1,5 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
-same seeded inputs (the oracle reads the same float32 samples, widened).
+same seeded inputs (the oracle reads the same float32 samples, widened), with
+the bars of tests/parity.py: STFT, map, T in replay mode (the oracle's V
+re-accumulated with the GPU's destination map), column mass, the inverse
+alone (the oracle's inverse of the GPU's T) and end to end (with the exact
+effect of every source the two sides place differently), and the SNR.
 
 Covers the small chirp/FM workload and the run-up workload at 2^18 - 37
 samples (many inverse tiles and a ragged tail) element by element, the
@@ -11,8 +15,7 @@ import pytest
 import oracle as O
 from paper_2003_07065_gb300 import workloads as W
 
-from parity import (SNR_DB, XHAT_RTOL, as_complex, check_map, check_mass, check_stft,
-                    check_tfr, snr_db)
+from parity import as_complex, compare
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,39 +53,6 @@ def run_oracle(params, x32):
     r = O.sst(x, p["fs"], p["L"], p["sigma"], p["hop"], p["nfft"], p["f_lo"], p["f_hi"], p["z"],
               p["gamma"], p["relative"], inverse_range=(0, len(x)))
     return r
-
-
-def compare(g, r, params, clean=None):
-    assert (g["k_lo"], g["k_hi"]) == (r.k_lo, r.k_hi)
-    assert g["bins"] == r.T.shape[1]
-    stats = {}
-    stats["stft"] = check_stft(g["V"], r.V, "V")
-    stats["stft_d"] = check_stft(g["Vd"], r.Vd, "Vd")
-    if params["relative"]:
-        vmax = np.abs(r.V).max()
-        assert abs(g["maxv"] - vmax) <= 1e-5 * vmax
-    moved, rate = check_map(g["dest"], r.dest, r.V, r.gamma, r.T.shape[1])
-    stats["map_rate"] = rate
-    stats["tfr"] = check_tfr(g["T"], r.T, r.V, moved, g["dest"], r.dest)
-    stats["mass"] = check_mass(g["T"], r.T, r.V, r.gamma, moved)
-    # reconstruction
-    xo = r.xhat
-    allow = 0.0
-    if moved.any():
-        # a source moved by one fine bin changes r~ by at most
-        # (2/Nf) |V| |1 - exp(i 2 pi j / (z Nf))| <= (2/Nf) |V| 2 pi M / (z Nf) per frame,
-        # summed over the <= L/hop frames covering a sample, divided by min D
-        nf, z, M, hop = params["nfft"], params["z"], (params["L"] - 1) // 2, params["hop"]
-        per = (2.0 / nf) * np.abs(r.V[moved]).max() * min(2.0, 2 * np.pi * M / (z * nf))
-        allow = per * np.ceil(params["L"] / hop) / (np.sqrt(2.0) / hop * 0.5)
-    err = np.abs(g["xhat"] - xo)
-    stats["xhat"] = err.max() / np.abs(xo).max()
-    assert err.max() <= XHAT_RTOL * np.abs(xo).max() + allow, f"xhat max err {err.max():.3e}"
-    if clean is not None:
-        s_g, s_o = snr_db(clean, g["xhat"]), snr_db(clean, xo)
-        stats["snr_gpu"], stats["snr_oracle"] = s_g, s_o
-        assert abs(s_g - s_o) <= SNR_DB, (s_g, s_o)
-    return stats
 
 
 @pytest.mark.parametrize("name", ["chirp_fm_64k", "runup_256k"])
