@@ -202,6 +202,19 @@ def snr_db(clean, xhat, sl=slice(None)):
     return 10 * np.log10(np.sum(c * c) / np.sum(e * e))
 
 
+def gpu_map(S, params, x_dev, two_pass=False):
+    """V, V' and the destination map of a single plan with these parameters
+    on the device signal x_dev (sst_stft, sst_reassign_map): the decisions the
+    batched and streamed paths share with it.  Returns numpy arrays."""
+    plan = S.Plan(**params, two_pass=two_pass)
+    V, Vd = plan.stft(x_dev)
+    _, dest = plan.reassign_map(x_dev)
+    out = dict(V=as_complex(V.cpu().numpy()), Vd=as_complex(Vd.cpu().numpy()),
+               dest=dest.cpu().numpy().astype(np.int64))
+    plan.close()
+    return out
+
+
 def compare(g, r, params, clean=None, inverse_range=None):
     """Every bar above for one signal.  g: the GPU's outputs (dict with T,
     dest, xhat and optionally V, Vd, maxv); r: the oracle's Result for the
