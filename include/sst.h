@@ -198,8 +198,19 @@ size_t sst_renyi_workspace_bytes(void);
 sst_status sst_renyi(const float *tfr_dev, int64_t rows, int32_t cols, int64_t ld, double alpha, double cell,
                      double *out_dev, void *workspace_dev, void *stream);
 
-/* sst_forward followed by sst_inverse.  tfr_dev receives T and may not be
- * NULL in this version (the inverse reads it back). */
+/* The whole path, forward (Sec. 2.2, 2.4) and direct inverse (Sec. 2.3).
+ * With tfr_dev non-NULL: sst_forward followed by sst_inverse, T written to
+ * tfr_dev and read back.  With tfr_dev NULL, T is not emitted and never
+ * reaches global memory: the inverse of frame m needs only column m of T
+ * (Eq. 25), so one kernel per tile of frames runs the forward of each pair
+ * of frames into T rows in shared memory and inverts them from there
+ * (Eq. 25-26).  A relative threshold then takes max|S^g| from a pre-pass
+ * over every frame (as SST_TWO_PASS plans do), since no T is left to settle
+ * afterwards.  The result equals that of a SST_TWO_PASS plan with a TFR
+ * output up to the rounding of the overlap-add.  Plans whose fused kernel
+ * would need more shared memory than the device offers per block (large Nf
+ * with a wide band and subdivision) return SST_EUNSUPPORTED for a NULL
+ * tfr_dev.  xhat_dev: n floats. */
 sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
                                float *xhat_dev, void *workspace_dev, void *stream);
 
@@ -387,7 +398,7 @@ uint64_t sst_launch_count(void);
  * sst_profile_collect waits for them, adds the elapsed times per kernel kind
  * into ms[kind] and counts[kind] (arrays of SST_PROFILE_KINDS entries),
  * and clears the record.  Kinds: see sst_profile_kind_name. */
-#define SST_PROFILE_KINDS 8
+#define SST_PROFILE_KINDS 9
 sst_status sst_profile_enable(int on);
 sst_status sst_profile_collect(double *ms, uint64_t *counts);
 const char *sst_profile_kind_name(int kind);

@@ -238,7 +238,7 @@ cudaError_t raise_smem(const KernelTable *kt, int kind, size_t bytes) {
 
 // ------------------------------------------------------------ profiling
 static const char *kPkNames[SST_PROFILE_KINDS] = {"absmax", "gamma", "forward", "stft", "map", "inverse",
-                                                  "finalize", "other"};
+                                                  "finalize", "other", "fused"};
 struct ProfRec { int kind; cudaEvent_t a, b; };
 static std::mutex g_prof_mu;
 static std::vector<ProfRec> g_prof;
@@ -504,6 +504,10 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         if (g_ > units) g_ = units;
         return (int)std::max<int64_t>(g_, 1);
     };
+    // fused forward + inverse: the plan supports it where its shared memory fits
+    pl->kind_fused = half_window ? kind_cls(KIND_FUSED, bcls) : KIND_FUSED_WIDE;
+    pl->smem_fused = fused_smem_bytes(kt->smem_frame, nb, nbo, d.seg_len, half_window ? bcls : 0);
+    pl->fused_ok = pl->smem_fused <= smax && raise_smem(kt, pl->kind_fused, pl->smem_fused) == cudaSuccess;
     pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 3) / 4);
     pl->grid_fwd = grid_for(pl->kind_fwd_t, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
@@ -792,12 +796,36 @@ SST_API sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream, ridge_dev, half_width);
 }
 
+// Forward + inverse with T kept on chip (k_fused): the pre-pass (relative
+// plans: max |S^g| over every frame, as SST_TWO_PASS plans do, since no T
+// exists to settle afterwards), one fused launch over the inverse tiles, and
+// k_finalize.
+static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws, cudaStream_t st) {
+    sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
+    if (s != SST_OK) return s;
+    SST_LAUNCHED_K(PK_FUSED, st,
+                   pl->kt->fused(pl->d, pl->kind_fused, x, ws_scalars(pl, ws), ws_ola(pl, ws), pl->smem_fused, st),
+                   "fused launch");
+    int64_t blocks = (pl->d.n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    SST_LAUNCHED_K(PK_FINALIZE, st,
+                   (k_finalize<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat), cudaGetLastError()),
+                   "finalize launch");
+    return SST_OK;
+}
+
 SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
                                        float *xhat_dev, void *ws, void *stream) {
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
-    if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    if (!tfr_dev) {
+        if (!plan->fused_ok)
+            return fail(SST_EUNSUPPORTED,
+                        "no TFR output needs the fused kernel, whose %zu bytes of shared memory this plan exceeds",
+                        plan->smem_fused);
+        return run_fused(plan, x_dev, xhat_dev, ws, (cudaStream_t)stream);
+    }
     s = run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
     if (s != SST_OK) return s;
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);

@@ -36,6 +36,11 @@ const void *kernel_of(int kind) {
             if (cls == 2) return (const void *)k_inverse<NF, true, CLS2>;
             return (const void *)k_inverse<NF, true>;
         case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
+        case KIND_FUSED:
+            if (cls == 1) return (const void *)k_fused<NF, true, CLS1>;
+            if (cls == 2) return (const void *)k_fused<NF, true, CLS2>;
+            return (const void *)k_fused<NF, true, 0>;
+        case KIND_FUSED_WIDE: return (const void *)k_fused<NF, false, 0>;
         case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
         case KIND_B_FWD: return (const void *)k_forward_batch<NF>;
         case KIND_B_INV: return (const void *)k_inverse_batch<NF, true>;
@@ -105,6 +110,22 @@ cudaError_t inverse(const SstDev &d, int kind, const float2 *T, float *partial, 
     return cudaGetLastError();
 }
 
+cudaError_t fused(const SstDev &d, int kind, const float *x, const SstScalars *sc, float *partial, size_t smem,
+                  cudaStream_t st) {
+    const unsigned grid = (unsigned)d.ntiles;
+    if (kind == kind_cls(KIND_FUSED, 1))
+        k_fused<NF, true, CLS1><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
+    else if (kind == kind_cls(KIND_FUSED, 2))
+        k_fused<NF, true, CLS2><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
+    else if (kind == KIND_FUSED)
+        k_fused<NF, true, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
+    else if (kind == KIND_FUSED_WIDE)
+        k_fused<NF, false, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nitems, int max_nbo, int grid,
                   size_t smem, float *partial, cudaStream_t st) {
     switch (kind) {
@@ -118,7 +139,7 @@ cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nit
 }
 
 const KernelTable table = {NF, C::R1, C::TPF, (size_t)C::BUF * sizeof(float2) + 128, set_smem, occupancy,
-                           absmax, forward, inverse, batch};
+                           absmax, forward, inverse, fused, batch};
 
 }  // namespace
 

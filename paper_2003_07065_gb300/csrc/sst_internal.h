@@ -39,7 +39,7 @@ SST_SHARED cudaError_t launch_gamma(const float *partial, int count, float frac2
     } while (0)
 
 // per-kernel timing (sst_profile_enable): events around each launch
-enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER };
+enum { PK_ABSMAX = 0, PK_GAMMA, PK_FORWARD, PK_STFT, PK_MAP, PK_INVERSE, PK_FINALIZE, PK_OTHER, PK_FUSED };
 SST_SHARED bool profiling_on();
 SST_SHARED void profile_record(int kind, cudaEvent_t a, cudaEvent_t b);
 
@@ -92,6 +92,11 @@ struct sst_plan {
     int kind_fwd_t = sst::KIND_FWD_T;
     int kind_fwd_spec = sst::KIND_FWD_SPEC;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;
+    // fused forward + inverse (sst_forward_inverse without a TFR): kind with
+    // its class, shared memory, and whether it fits this device
+    int kind_fused = sst::KIND_FUSED;
+    size_t smem_fused = 0;
+    bool fused_ok = false;
     size_t ws_bytes = 0, ws_off_partial = 0, ws_off_ola = 0;
     // one-pass relative threshold
     bool spec = false;

@@ -312,6 +312,8 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
 // and S^g' for the band bins, IF estimate, threshold, destination, and the
 // deterministic per-frame accumulation of T in shared memory.
 //   MODE_T   : T rows (F x nbo complex)
+//   MODE_TROW: as MODE_T, the frame's T row written to out0 itself (a
+//              shared-memory row of the fused forward + inverse)
 //   MODE_STFT: S^g, S^g' rows (F x nb complex each), no threshold
 //   MODE_MAP : omega (F x nb float) and dest (F x nb int32)
 // The T sum is exact: every contribution is scaled by the call's power of two
@@ -320,7 +322,7 @@ __global__ void k_absx(const float *__restrict__ x, int64_t n, float *__restrict
 // above 2^-39 of the bound); shared-memory 64-bit integer adds are order
 // independent, so the rounded result does not depend on thread scheduling.
 // ---------------------------------------------------------------------------
-enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2, MODE_SPEC = 3 };
+enum { MODE_T = 0, MODE_STFT = 1, MODE_MAP = 2, MODE_SPEC = 3, MODE_TROW = 4 };
 
 // MODE_SPEC: per-frame shared-memory list of the sources that wait for the
 // exact threshold (beyond it the call falls back to the two-pass path)
@@ -616,8 +618,8 @@ __device__ __forceinline__ void forward_frame(const SstDev &d, const float *__re
     // all band reads and atomics done before the T row is read and the next
     // frame's first pass overwrites buf
     __syncthreads();
-    if (MODE != MODE_T && MODE != MODE_SPEC) return;
-    float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
+    if (MODE != MODE_T && MODE != MODE_SPEC && MODE != MODE_TROW) return;
+    float2 *Trow = MODE == MODE_TROW ? out0 : out0 + (size_t)trow_of(d, m) * d.nbo;
     const int stride = tacc_stride(d.nbo);
     if (MODE == MODE_SPEC) {
         const int nm = *nmarg;
@@ -942,6 +944,193 @@ __device__ __forceinline__ float finalize_value(const SstDev &d, const float *__
 }
 
 __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat);
+
+// ---------------------------------------------------------------------------
+// Fused forward + inverse (sst_forward_inverse without a TFR output): one CTA
+// per inverse tile of B frames.  Per pair of frames (a, b) the forward of each
+// (as k_forward, MODE_TROW) leaves its T row in shared memory, and the pair is
+// inverted from those rows exactly as inverse_tile does from rows staged by
+// its bulk copy (Eq. 25, the z sub-grid IFFTs), then overlap-added into the
+// tile's segment (Eq. 26; k_finalize sums segments and applies 1 / D).  T
+// never reaches global memory.  Shared memory: the frame buffer, the T
+// accumulators (whose first half holds row b while the pair is inverted), row
+// a, the band mirrors (CLS > 0) and the segment.
+// ---------------------------------------------------------------------------
+template <int NF, bool NARROW, int CLS>
+__device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 *__restrict__ rowA,
+                                                  const float2 *__restrict__ rowB, float2 *buf, int tid,
+                                                  const int (&tap)[InvTaps<NARROW>::NACC],
+                                                  float2 (&racc)[InvTaps<NARROW>::NACC]) {
+    using C = Cfg<NF>;
+    using TP = InvTaps<NARROW>;
+    constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
+    const int nq = d.k_hi - d.k_lo + 1;
+    const bool live = (TPF == NS) || tid < NS;
+#pragma unroll
+    for (int i = 0; i < TP::NACC; ++i) racc[i] = make_float2(0.f, 0.f);
+    for (int s = 0; s < d.z; ++s) {
+        const int sb = (s == 0) ? 0 : d.z - s;
+        const int dl = (s == 0) ? 0 : 1;
+        const int nqs = (s == 0) ? nq : nq - 1;
+        const int nqb = (sb == 0) ? nq : nq - 1;
+        // element q of sub-grid s of a row: row[z q + s]
+        const float2 *Ta = rowA + s, *Tam = rowA + sb, *Tb = rowB + s, *Tbm = rowB + sb;
+        constexpr int STEP = NF / C::R1;
+        float2 u[C::PER1][C::R1];
+#pragma unroll
+        for (int bb = 0; bb < C::PER1; ++bb) {
+            const int j = tid + bb * TPF;
+            const bool jok = C::PER1 * TPF == NF / C::R1 || j < NF / C::R1;
+            const int q0 = j - d.k_lo;
+            const int qm0 = NF - dl - j - d.k_lo;
+#pragma unroll
+            for (int r = 0; r < C::R1; ++r) {
+                if (!((band_mask<NF>(CLS) >> r) & 1u)) continue;
+                float2 y = make_float2(0.f, 0.f);
+                const int q = q0 + r * STEP;
+                const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
+                const bool hd = jok && (unsigned)q < (unsigned)nqs;
+                const bool hm = jok && (unsigned)qm < (unsigned)nqb;
+                if (__any_sync(0xffffffffu, hd || hm)) {
+                    if (hd) {
+                        float2 xa = Ta[q * d.z], xb = Tb[q * d.z];
+                        if (s == 0 && (d.k_lo + q == 0 || 2 * (d.k_lo + q) == NF)) {
+                            xa = cscale(xa, 0.5f);
+                            xb = cscale(xb, 0.5f);
+                        }
+                        y.x += xa.x - xb.y;
+                        y.y += xa.y + xb.x;
+                    }
+                    if (hm) {
+                        float2 xa = Tam[qm * d.z], xb = Tbm[qm * d.z];
+                        if (sb == 0 && (d.k_lo + qm == 0 || 2 * (d.k_lo + qm) == NF)) {
+                            xa = cscale(xa, 0.5f);
+                            xb = cscale(xb, 0.5f);
+                        }
+                        y.x += xa.x + xb.y;
+                        y.y += -xa.y + xb.x;
+                    }
+                }
+                u[bb][r] = y;
+            }
+        }
+        fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
+        __syncthreads();
+        fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
+        float2 v[16];
+        fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
+        if (live) {
+            if (s == 0) {
+#pragma unroll
+                for (int i = 0; i < TP::NACC; ++i) racc[i] = cadd(racc[i], v[TP::r_of(i)]);
+            } else {
+                const float2 bs = __ldg(&d.twb[s * NS + tid]);
+#pragma unroll
+                for (int i = 0; i < TP::NACC; ++i) {
+                    if (tap[i] != INT_MIN) {
+                        const float2 w = (i == 16) ? __ldg(&d.twn[s])
+                                                   : cmul(bs, __ldg(&d.twc[(2 * s + (tap[i] < 0)) * 16 + TP::r_of(i)]));
+                        racc[i] = cadd(racc[i], cmul(v[TP::r_of(i)], w));
+                    }
+                }
+            }
+        }
+    }
+}
+
+// bytes of the fused kernel's shared memory (layout in k_fused)
+__host__ __device__ __forceinline__ size_t fused_smem_bytes(size_t smem_frame, int nb, int nbo, int seg_len, int cls) {
+    size_t o = smem_frame;                         // frame buffer (+ slack)
+    o += tacc_bytes(nbo);                          // accumulators; row b in their first half
+    o += ((size_t)8 * nbo + 15) & ~(size_t)15;     // row a
+    if (cls > 0) o += mirror_bytes(nb);            // band mirrors
+    o += (4 * (size_t)seg_len + 15) & ~(size_t)15; // overlap-add segment
+    return o;
+}
+
+template <int NF, bool NARROW, int CLS>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_INV_MINB)
+k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc, float *__restrict__ partial) {
+    using C = Cfg<NF>;
+    using TP = InvTaps<NARROW>;
+    constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
+    extern __shared__ float4 smem4[];
+    const int tid = threadIdx.x;
+    float2 *buf = reinterpret_cast<float2 *>(smem4);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
+    const int stride = tacc_stride(d.nbo);
+    float2 *rowB = reinterpret_cast<float2 *>(acc);   // row b, in the accumulators' first half
+    float2 *rowA = reinterpret_cast<float2 *>(acc + 4 * stride);
+    char *after = reinterpret_cast<char *>(rowA) + ((8 * (size_t)d.nbo + 15) & ~(size_t)15);
+    float2 *mz = reinterpret_cast<float2 *>(after);
+    float *seg = reinterpret_cast<float *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
+    const FwdScale fs = fwd_scale(d, sc, true);
+    const int64_t tile = blockIdx.x;
+    const int64_t m0 = tile * d.B;
+    const float cnorm = 1.0f / (float)NF;
+    const bool live = (TPF == NS) || tid < NS;
+
+    for (int i = tid; i < 4 * stride; i += TPF) acc[i] = 0u;
+    for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
+    // (the first barrier inside the forward orders these before any use)
+
+    for (int pr = 0; pr < d.B / 2; ++pr) {
+        const int64_t a = m0 + 2 * pr, b = a + 1;
+        if (a >= d.F) break;
+        const bool hasb = b < d.F;
+        // forward of a: its row into rowA (the accumulators are cleared on the way)
+        forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, nullptr, nullptr,
+                                          nullptr, mz);
+        // forward of b: its row into the frame buffer (free once the frame's
+        // bins are read), then moved into the accumulators' first half
+        if (hasb) {
+            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, buf, nullptr, b, buf, acc, tid, nullptr, nullptr, nullptr,
+                                              nullptr, mz);
+        } else {
+            __syncthreads();
+            for (int l = tid; l < d.nbo; l += TPF) buf[l] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int l = tid; l < d.nbo; l += TPF) rowB[l] = buf[l];
+        __syncthreads();
+
+        int tap[TP::NACC];
+        float gw[TP::NACC];
+#pragma unroll
+        for (int i = 0; i < TP::NACC; ++i) {
+            const int r = TP::r_of(i);
+            const int q = tid + r * NS;
+            int n;
+            if (i == 16) n = -NF / 2;
+            else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
+            const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
+            tap[i] = ok ? n : INT_MIN;
+            gw[i] = ok ? __ldg(&d.g[n + d.M]) * cnorm : 0.f;
+        }
+        float2 racc[TP::NACC];
+        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, tap, racc);
+        // overlap-add a, then b (ascending frame order at every sample)
+        const int oa = (int)(a - m0) * d.hop + d.M;
+#pragma unroll
+        for (int i = 0; i < TP::NACC; ++i)
+            if (tap[i] != INT_MIN) seg[oa + tap[i]] += gw[i] * racc[i].x;
+        __syncthreads();
+        if (hasb) {
+            const int ob = oa + d.hop;
+#pragma unroll
+            for (int i = 0; i < TP::NACC; ++i)
+                if (tap[i] != INT_MIN) seg[ob + tap[i]] += gw[i] * racc[i].y;
+        }
+        // the accumulators' first half held row b: clear it for the next pair
+        // (ordered before its atomics by the barriers inside the next forward)
+        for (int i = tid; i < 2 * stride; i += TPF) acc[i] = 0u;
+        __syncthreads();
+    }
+    float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
+    for (int i = tid; i < d.seg_len; i += TPF) out[i] = seg[i];
+}
 
 // ---------------------------------------------------------------------------
 // Batched kernels: persistent CTAs walk a table of work items (BatchItem) of

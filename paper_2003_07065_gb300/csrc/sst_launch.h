@@ -10,9 +10,11 @@
 namespace sst {
 
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
-       KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10, KIND_COUNT = 11 };
+       KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10,
+       KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_COUNT = 13 };
 
-// A forward (KIND_FWD_T, KIND_FWD_SPEC) or inverse (KIND_INV) kind may carry a
+// A forward (KIND_FWD_T, KIND_FWD_SPEC), inverse (KIND_INV) or fused
+// forward + inverse (KIND_FUSED) kind may carry a
 // pruning class (band_class, 1 or 2) in the bits from KIND_CLS_SHIFT up;
 // tables whose first radix is not 16 run class 0 for every class.
 constexpr int KIND_CLS_SHIFT = 8;
@@ -33,6 +35,10 @@ struct KernelTable {
                            void *out1, int grid, size_t smem, cudaStream_t st);
     // kind: KIND_INV (window L <= nf/2 + 1) or KIND_INV_WIDE (L <= nf + 1)
     cudaError_t (*inverse)(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st);
+    // fused forward + inverse over the plan's inverse tiles (kind: KIND_FUSED
+    // with its class, or KIND_FUSED_WIDE); partial is the overlap-add buffer
+    cudaError_t (*fused)(const SstDev &d, int kind, const float *x, const SstScalars *sc, float *partial,
+                         size_t smem, cudaStream_t st);
     // batched kernels over a work-item table (kind: KIND_B_*)
     cudaError_t (*batch)(int kind, const BatchChan *ch, const BatchItem *items, int nitems, int max_nbo, int grid,
                          size_t smem, float *partial, cudaStream_t st);

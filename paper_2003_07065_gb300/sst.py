@@ -556,7 +556,7 @@ def sst_launch_count() -> int:
     return int(load().sst_launch_count())
 
 
-PROFILE_KINDS = 8
+PROFILE_KINDS = 9
 
 
 def sst_profile_enable(on: bool = True):
