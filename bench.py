@@ -3,7 +3,9 @@
 One step = sst_forward_inverse over the whole run-up vibration workload
 (N = 2^24 float32 samples at 51.2 kHz, Gaussian window L = 2049, hop 32,
 Nf 4096, band 0-6.4 kHz, subdivision z = 4, gamma = 1e-3 max|V|): threshold
-pre-pass, forward (T written to HBM, 8.6 GB), inverse and overlap-add.
+pre-pass, forward (T written to HBM, 8.6 GB), inverse and overlap-add.  The
+same step without a TFR output (T kept on chip by the fused kernel) is timed
+beside it and reported under "variants".
 Metric: input samples/s.  With --gpus N > 1 (torchrun), every rank runs its
 own replica of the workload on its own GPU (weak scaling, no collective on
 the data path).
@@ -159,6 +161,18 @@ def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
 
 
 # ------------------------------------------------------------------ reference arm
+def plan_supports_fused(sst, plan, x, n, xhat, stream) -> bool:
+    """Whether the plan runs forward + inverse without a TFR output (its
+    fused kernel fits in shared memory)."""
+    try:
+        sst.sst_forward_inverse(plan.handle, x, n, None, xhat, plan.workspace, stream)
+        return True
+    except sst.SstError as e:
+        if e.status == 6:
+            return False
+        raise
+
+
 def max_over_ranks(x: float, dist=None, device="cuda") -> float:
     """The largest x over the ranks of the process group (x itself without
     one): the job's time is its slowest replica's."""
@@ -863,6 +877,33 @@ def main():
     e_s = max_over_ranks(time.perf_counter() - e0, dist)
     e2e = job_rate(world, w.n, args.steps, e_s)
 
+    # ---- the same step without a TFR output (T kept on chip, one fused
+    # kernel per tile; relative threshold from a pre-pass over every frame)
+    fused = None
+    if plan_supports_fused(sst, plan, x, w.n, xhat, stream):
+        for _ in range(2):
+            sst.sst_forward_inverse(plan.handle, x, w.n, None, xhat, plan.workspace, stream)
+        torch.cuda.synchronize()
+        sst.sst_profile_enable(True)
+        sst.sst_profile_collect()
+        fevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            fevs[i][0].record(stream)
+            sst.sst_forward_inverse(plan.handle, x, w.n, None, xhat, plan.workspace, stream)
+            fevs[i][1].record(stream)
+        torch.cuda.synchronize()
+        sst.sst_profile_enable(False)
+        fprof = sst.sst_profile_collect()
+        f_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in fevs), dist)
+        fused = {"value": job_rate(world, w.n, args.steps, f_ms / 1e3), "unit": UNIT,
+                 "ms_per_step": f_ms / args.steps,
+                 "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                             for k, v in fprof.items()}}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -898,6 +939,12 @@ def main():
                 "fused_step": {"algorithmic_flops": step_flops, "achieved": step_flops / (t_ms / args.steps / 1e3) / 1e12,
                                "frac": step_flops / (t_ms / args.steps / 1e3) / 1e12 / peak}}
 
+    if fused is not None and roof is not None:
+        f_s = fused["ms_per_step"] / 1e3
+        fused["fused_step"] = {"algorithmic_flops": step_flops, "achieved": step_flops / f_s / 1e12,
+                               "frac": step_flops / f_s / 1e12 / peak,
+                               "note": "forward + inverse FLOPs as in roofline.fused_step; the pre-pass "
+                                       "over every frame is extra work not counted"}
     kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -924,6 +971,7 @@ def main():
         "gpu_launches_per_step": launches / args.steps,
         "kernels": kern,
         "roofline": roof,
+        "variants": {"no_tfr_output": fused},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n, "d2h_bytes_per_step": 4 * w.n},
         "clocks": clocks,

@@ -647,6 +647,13 @@ class Plan:
         sst_forward_inverse(self.handle, x, self.n, tfr, xhat, self.workspace)
         return tfr, xhat
 
+    def reconstruct(self, x, xhat=None):
+        """Forward + inverse without a TFR output (T stays on chip)."""
+        import torch
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
+        sst_forward_inverse(self.handle, x, self.n, None, xhat, self.workspace)
+        return xhat
+
     def stft(self, x):
         import torch
         V = torch.empty((self.frames, self.nb, 2), dtype=torch.float32, device=self.device)

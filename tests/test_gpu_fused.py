@@ -1,0 +1,116 @@
+"""Forward + inverse without a TFR output (sst_forward_inverse with a NULL
+tfr): T stays in shared memory between the forward and the inverse of each
+pair of frames (Eq. 25 needs only the frame's own column).  The
+reconstruction must carry the same bits as a two-pass plan's forward +
+inverse through a TFR in global memory (same per-frame arithmetic, same
+tiles and overlap-add order), and meet the parity bars against the FP64
+oracle (the inverse end to end, with the moved-source bound, and the SNR)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_07065_gb300 import workloads as W
+
+from parity import check_map, check_xhat_end_to_end, moved_bound, snr_db, SNR_DB
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from test_gpu_parity import EDGE  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_07065_gb300 import build, sst as S
+    build.build()
+    S.load()
+    return S
+
+
+def same_bits_as_two_pass(S, params, x32):
+    x = torch.from_numpy(x32).cuda()
+    two = S.Plan(**params, two_pass=True)
+    _, ref = two.forward_inverse(x)
+    plan = S.Plan(**params)
+    got = torch.full_like(ref, float("nan"))
+    plan.reconstruct(x, got)
+    got2 = plan.reconstruct(x)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref), (got - ref).abs().max().item()
+    assert torch.equal(got, got2)
+    out = got.cpu().numpy().astype(np.float64)
+    _, dest = two.reassign_map(x)
+    dest = dest.cpu().numpy().astype(np.int64)
+    plan.close()
+    two.close()
+    return out, dest
+
+
+def oracle_check(params, x32, xhat, dest, clean=None):
+    p = params
+    r = O.sst(x32.astype(np.float64), p["fs"], p["L"], p["sigma"], p["hop"], p["nfft"], p["f_lo"], p["f_hi"],
+              p["z"], p["gamma"], p["relative"], inverse_range=(0, p["n"]))
+    check_map(dest, r.dest, r.V, r.gamma, r.T.shape[1])
+    g, _ = O.window(p["L"], p["sigma"])
+    bound = moved_bound(r.V, dest, r.dest, r.k_lo, p["nfft"], p["z"], g, p["hop"], p["n"])
+    stats = check_xhat_end_to_end(xhat, r.xhat, bound)
+    if clean is not None:
+        assert abs(snr_db(clean, xhat) - snr_db(clean, r.xhat)) <= SNR_DB
+    return stats
+
+
+@pytest.mark.parametrize("name", ["chirp_fm_64k", "runup_256k"])
+def test_workloads(sst, name):
+    w = W.ALL[name]
+    noisy, clean = w.signal()
+    x32 = noisy.astype(np.float32)
+    xhat, dest = same_bits_as_two_pass(sst, w.params(), x32)
+    print(name, oracle_check(w.params(), x32, xhat, dest, clean))
+
+
+@pytest.mark.parametrize("params", EDGE, ids=[f"n{p['n']}_nf{p['nfft']}_z{p['z']}" for p in EDGE])
+def test_edge_cases(sst, params):
+    gen = np.random.default_rng(params["n"] + 1)
+    t = np.arange(params["n"]) / params["fs"]
+    mid = 0.5 * (params["f_lo"] + params["f_hi"])
+    x32 = (np.cos(2 * np.pi * mid * t + 0.3) + 0.3 * gen.standard_normal(params["n"])).astype(np.float32)
+    try:
+        xhat, dest = same_bits_as_two_pass(sst, params, x32)
+    except sst.SstError as e:
+        assert e.status == 6 and "shared memory" in str(e)
+        pytest.skip("fused kernel does not fit this plan: " + str(e))
+    print(params, oracle_check(params, x32, xhat, dest))
+
+
+def test_runup_16m_full_size(sst):
+    """The benchmark's workload: the same bits as the two-pass path with a TFR."""
+    w = W.RUNUP_16M
+    x32 = w.signal()[0].astype(np.float32)
+    x = torch.from_numpy(x32).cuda()
+    two = sst.Plan(**w.params(), two_pass=True)
+    _, ref = two.forward_inverse(x)
+    two.close()
+    torch.cuda.synchronize()
+    plan = sst.Plan(**w.params())
+    got = plan.reconstruct(x)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    plan.close()
+
+
+def test_unsupported_plan_reported(sst):
+    # Nf 8192 over the whole band with z = 4: accumulators alone exceed shared memory
+    p = dict(n=20000, fs=16000.0, L=4097, sigma=512.0, hop=64, nfft=8192, f_lo=0.0, f_hi=8000.0, z=4,
+             gamma=1e-3, relative=True)
+    try:
+        plan = sst.Plan(**p)
+    except sst.SstError as e:          # the TFR path itself may not fit either
+        assert e.status == 6
+        return
+    x = torch.zeros(p["n"], device="cuda")
+    with pytest.raises(sst.SstError) as e:
+        plan.reconstruct(x)
+    assert e.value.status == 6
+    plan.close()
