@@ -453,6 +453,83 @@ def sst2(x, fs: float, L: int, sigma: float, hop: int, nfft: int, f_lo: float, f
     return Result(V, Vd, omega2, dest, T, np.zeros(nm, np.complex128), gam, k_lo, k_hi, m0, xhat)
 
 
+# ------------------------------------------------ one signal split by frames
+# Frames are independent (Sec. 2.1, Eq. 7-9); only the overlap-add of Eq. 26
+# couples neighbouring frames, and a relative threshold needs the maximum of
+# |V| over every frame.  So a long signal splits into contiguous frame ranges:
+# each part reads its frames' samples (a read-only halo of M samples beyond
+# its own), one max-reduction gives the threshold, and each part sends its
+# overlap-add numerator on a neighbour's samples to that neighbour.
+def frame_ranges(F: int, parts: int, align: int = 1):
+    """Contiguous frame ranges [m_b, m_e) of `parts` parts, as equal as
+    multiples of `align` frames allow."""
+    units = -(-F // align)
+    out = []
+    for r in range(parts):
+        ub, ue = units * r // parts, units * (r + 1) // parts
+        out.append((min(F, ub * align), min(F, ue * align)))
+    return out
+
+
+def part_input_range(m_b: int, m_e: int, hop: int, L: int, n: int):
+    """Samples [x_b, x_e) that frames [m_b, m_e) read (Eq. 7-8)."""
+    M = (L - 1) // 2
+    return max(0, m_b * hop - M), min(n, (m_e - 1) * hop + M + 1)
+
+
+def part_output_range(m_b: int, m_e: int, hop: int, n: int, last: bool):
+    """Output samples [p_b, p_e) a part finalises: from its first frame's
+    centre to the next part's (to n for the last part)."""
+    return min(n, m_b * hop), (n if last else min(n, m_e * hop))
+
+
+def _embed(x_part, x_b, n):
+    xl = np.zeros(n)
+    xl[x_b:x_b + len(x_part)] = x_part
+    return xl
+
+
+def part_max_abs_v(x_part, x_b: int, n: int, L: int, sigma: float, hop: int, nfft: int,
+                   k_lo: int, k_hi: int, m_b: int, m_e: int) -> float:
+    """max |V| over the part's frames and the in-band bins, from its input
+    samples only (the part's contribution to the max-reduction of a relative
+    threshold)."""
+    if m_e <= m_b:
+        return 0.0
+    g, dg = window(L, sigma)
+    V, _ = stft(_embed(x_part, x_b, n), g, dg, hop, nfft, k_lo, k_hi, m_b, m_e - m_b)
+    return float(np.abs(V).max())
+
+
+def part_numerator(x_part, x_b: int, n: int, L: int, sigma: float, hop: int, nfft: int, k_lo: int,
+                   k_hi: int, z: int, gam: float, m_b: int, m_e: int):
+    """The part's STFT, reassignment (threshold gam, Eq. 13, 27-29) and
+    overlap-add numerator sum_m g[p - m hop] r~[m, p - m hop] over its frames
+    (Eq. 25-26 before the division by D), on the samples its frames touch.
+    Returns (numerator, first sample, T of the part's frames)."""
+    M = (L - 1) // 2
+    g, dg = window(L, sigma)
+    V, Vd = stft(_embed(x_part, x_b, n), g, dg, hop, nfft, k_lo, k_hi, m_b, m_e - m_b)
+    _, _, T, _ = reassign(V, Vd, k_lo, k_hi, nfft, z, gam)
+    q_b = max(0, m_b * hop - M)
+    q_e = min(n, (m_e - 1) * hop + M + 1)
+    num = inverse(T, k_lo, nfft, z, g, hop, n, q_b, q_e - q_b, mt0=m_b, mode=2)
+    return num, q_b, T
+
+
+def part_finalise(shares, p_b: int, p_e: int, L: int, sigma: float, hop: int, n: int) -> np.ndarray:
+    """x^ on [p_b, p_e) from the numerator shares (array, first sample) of the
+    parts whose frames touch it, added in the order given (ascending parts),
+    divided by the Eq. 26 normaliser D."""
+    num = np.zeros(p_e - p_b)
+    for arr, q_b in shares:
+        lo, hi = max(p_b, q_b), min(p_e, q_b + len(arr))
+        if hi > lo:
+            num[lo - p_b:hi - p_b] += arr[lo - q_b:hi - q_b]
+    g, _ = window(L, sigma)
+    return num / normaliser(g, hop, n, p_b, p_e - p_b)
+
+
 def global_max_abs_v(x, g, dg, hop, nfft, k_lo, k_hi, chunk: int = 4096) -> float:
     """max over every frame and in-band bin of |V| (the relative-threshold base)."""
     n = len(x)

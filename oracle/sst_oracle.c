@@ -271,7 +271,10 @@ int oro_normaliser(const double *g, int L, int hop, int64_t F, int64_t p0, int64
 /*   overlap-add  num[p] = sum_m g[t] r~[m,t],  xhat[p] = num[p] / D[p] (R6).  */
 /* Output samples p in [p0, p0+np).  T holds frames [mt0, mt0+ntf), which     */
 /* must cover every frame that touches the output range.                     */
-/* mode 0 = Eq. 26 normaliser, mode 1 = Eq. 11 WOLA normaliser (Sum g^2).     */
+/* mode 0 = Eq. 26 normaliser, mode 1 = Eq. 11 WOLA normaliser (Sum g^2),     */
+/* mode 2 = the overlap-add numerator of the frames T holds alone, not divided */
+/* (the share of one contiguous range of frames, for a signal split by frame */
+/* ranges; T then need not cover every frame touching the output range).     */
 /* ------------------------------------------------------------------------ */
 /* r~[m, t] for t in [0, L) of one frame (Eq. 25 on the zero-padded z Nf grid),
  * from its T row; re, im are G = z Nf doubles of scratch. */
@@ -308,7 +311,12 @@ int oro_inverse(const double *T, int64_t mt0, int64_t ntf, int k_lo, int nbo, in
     int64_t mlo = (p0 - M > 0) ? (p0 - M + hop - 1) / hop : 0;
     int64_t mhi = (pend + M) / hop;
     if (mhi > F - 1) mhi = F - 1;
-    if (mlo < mt0 || mhi > mt0 + ntf - 1) return -3;  /* T does not cover the range */
+    if (mode == 2) {                                   /* the given frames only */
+        if (mlo < mt0) mlo = mt0;
+        if (mhi > mt0 + ntf - 1) mhi = mt0 + ntf - 1;
+    } else if (mlo < mt0 || mhi > mt0 + ntf - 1) {
+        return -3;                                     /* T does not cover the range */
+    }
 
     /* Frames are taken in chunks: the r~ of a chunk's frames are independent
      * (Eq. 25) and computed in parallel; they are then overlap-added one frame
@@ -348,10 +356,8 @@ int oro_inverse(const double *T, int64_t mt0, int64_t ntf, int k_lo, int nbo, in
         }
     }
     if (failed) { free(num); free(seg); return -2; }
-    for (int64_t i = 0; i < np; ++i) {
-        double D = normaliser(g, L, hop, F, p0 + i, mode);
-        xhat[i] = num[i] / D;
-    }
+    for (int64_t i = 0; i < np; ++i)
+        xhat[i] = (mode == 2) ? num[i] : num[i] / normaliser(g, L, hop, F, p0 + i, mode);
     free(num); free(seg);
     return 0;
 }
