@@ -267,6 +267,52 @@ sst_status sst_check(sst_plan_t plan, const void *workspace, void *stream);
  * SST_ETIMEOUT.  Nothing faults or hangs. */
 sst_status sst_test_withhold_row_copy(sst_plan_t plan);
 
+/* ---- One signal split by frame ranges, e.g. over several GPUs (one plan
+ * per GPU, all with the same parameters).  Frames are independent (Sec. 2.1,
+ * Eq. 7-9) and only the overlap-add of Eq. 26 couples neighbouring ones, so
+ * part p of P takes a contiguous range of the plan's inverse tiles (tiles of
+ * B frames) and reads only its frames' samples, a read-only halo of M
+ * samples beyond them.  A relative threshold needs max |S^g| over every
+ * frame: each part computes its own maximum (sst_part_prepass) and the
+ * caller reduces them (a max over the parts, e.g. one all-reduce).  Each part
+ * then runs the fused forward + inverse of its tiles (T stays on chip), which
+ * leaves one overlap-add segment per tile in the workspace; the caller moves
+ * the segments of tiles [need_begin, tile_begin) and [tile_end, need_end)
+ * from the parts that computed them into the same places of this part's
+ * workspace (sst_part_segments gives where), and sst_part_finalize divides
+ * by D on the part's output samples.  The parts' outputs, concatenated,
+ * carry the same bits as the unsplit sst_forward_inverse with a NULL tfr. */
+typedef struct {
+    int64_t tile_begin, tile_end;    /* the part's inverse tiles */
+    int64_t frame_begin, frame_end;  /* its frames, [tile_begin B, min(tile_end B, F)) */
+    int64_t x_begin, x_end;          /* the input samples it reads: its frames' windows, widened to
+                                        whole groups of four frames (the pre-pass packs four) */
+    int64_t out_begin, out_end;      /* the output samples it finalises */
+    int64_t need_begin, need_end;    /* the tiles whose segments those samples need */
+} sst_part;
+/* The layout of part `part` of `parts` (host arithmetic; SST_EINVAL for a
+ * part outside [0, parts)).  Parts tile the frames and the output samples. */
+sst_status sst_part_layout(sst_plan_t plan, int32_t part, int32_t parts, sst_part *out);
+/* Where the overlap-add segments live: tile t's seg_len floats start at byte
+ * ola_offset + 4 seg_len t of the workspace; `tiles` tiles in all. */
+sst_status sst_part_segments(sst_plan_t plan, size_t *ola_offset, int32_t *seg_len, int64_t *tiles);
+/* The part's pre-pass maximum, one float written to r_dev: max |S^g|^2 over
+ * its frames and the in-band bins (relative plans), or max |x| over its input
+ * samples (absolute plans, the scale of the exact sums).  x_dev holds samples
+ * [x_begin, x_end) of the signal. */
+sst_status sst_part_prepass(sst_plan_t plan, const sst_part *part, const float *x_dev, float *r_dev,
+                            void *workspace_dev, void *stream);
+/* The part's forward + inverse, given r_dev = the maximum of every part's
+ * pre-pass value: the overlap-add segments of tiles [tile_begin, tile_end)
+ * in the workspace.  SST_EUNSUPPORTED where the plan's fused kernel does not
+ * fit (see sst_forward_inverse). */
+sst_status sst_part_forward_inverse(sst_plan_t plan, const sst_part *part, const float *x_dev, const float *r_dev,
+                                    void *workspace_dev, void *stream);
+/* x^ on the part's output samples into xhat_dev (out_end - out_begin floats),
+ * from the segments of tiles [need_begin, need_end) in the workspace. */
+sst_status sst_part_finalize(sst_plan_t plan, const sst_part *part, void *workspace_dev, float *xhat_dev,
+                             void *stream);
+
 /* Forward SST (as sst_forward) that allocates nothing and takes no
  * workspace.  The paper has no counterpart: this exists for callers that
  * cannot call cudaMalloc at the point where they run the transform, e.g. a

@@ -199,6 +199,28 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
         xhat[p] = finalize_value(d, partial, p);
 }
 
+// xhat[p - p0] for p in [p0, p1) (one part of a split signal)
+__global__ void k_finalize_range(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat, int64_t p0,
+                                 int64_t p1) {
+    for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x)
+        xhat[p - p0] = finalize_value(d, partial, p);
+}
+
+// the largest of count pre-pass partial maxima
+__global__ void k_reduce_max(const float *__restrict__ partial, int count, float *__restrict__ out) {
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmaxf(v, partial[i]);
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+        *out = r;
+    }
+}
+
 }  // namespace sst
 
 using namespace sst;
@@ -888,6 +910,146 @@ SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n,
                                                plan->d.log2_nb, ws_scalars(plan, ws), maxv_dev, nullptr),
                     cudaGetLastError()),
                    "gamma launch");
+    return SST_OK;
+}
+
+// ------------------------------------------------------------ split by frame ranges
+// One signal over several GPUs (Sec. 2.1: frames are independent; Eq. 26's
+// overlap-add couples neighbouring frames only): each part takes a contiguous
+// range of inverse tiles and reads its frames' samples with an M-sample halo.
+static sst_status part_check(sst_plan_t plan, const sst_part *part, const void *ws) {
+    if (!plan || !part) return fail(SST_EINVAL, "plan or part is NULL");
+    if (!ws) return fail(SST_EINVAL, "workspace is NULL");
+    if (((uintptr_t)ws) & 255) return fail(SST_EINVAL, "workspace must be 256-byte aligned");
+    const SstDev &d = plan->d;
+    if (part->tile_begin < 0 || part->tile_end < part->tile_begin || part->tile_end > d.ntiles)
+        return fail(SST_EINVAL, "tile range [%lld, %lld) outside [0, %lld)", (long long)part->tile_begin,
+                    (long long)part->tile_end, (long long)d.ntiles);
+    int dev = -1;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != plan->device) return fail(SST_EINVAL, "plan was created on device %d, current is %d", plan->device, dev);
+    return SST_OK;
+}
+
+SST_API sst_status sst_part_layout(sst_plan_t plan, int32_t part, int32_t parts, sst_part *out) {
+    if (!plan || !out) return fail(SST_EINVAL, "plan or out is NULL");
+    if (parts < 1 || part < 0 || part >= parts) return fail(SST_EINVAL, "part %d of %d", part, parts);
+    const SstDev &d = plan->d;
+    sst_part r;
+    memset(&r, 0, sizeof r);
+    r.tile_begin = d.ntiles * part / parts;
+    r.tile_end = d.ntiles * (part + 1) / parts;
+    r.frame_begin = std::min<int64_t>(d.F, r.tile_begin * d.B);
+    r.frame_end = std::min<int64_t>(d.F, r.tile_end * d.B);
+    if (r.frame_end > r.frame_begin) {
+        // the pre-pass packs frames in groups of four (k_absmax): a part reads
+        // whole groups, so every frame's |S^g| comes out of the same packing
+        // as in the unsplit pre-pass
+        const int64_t q_lo = r.frame_begin / 4 * 4, q_hi = std::min<int64_t>(d.F, (r.frame_end + 3) / 4 * 4);
+        r.x_begin = std::max<int64_t>(0, q_lo * d.hop - d.M);
+        r.x_end = std::min<int64_t>(d.n, (q_hi - 1) * d.hop + d.M + 1);
+    } else {
+        r.x_begin = r.x_end = std::min<int64_t>(d.n, r.frame_begin * d.hop);
+    }
+    r.out_begin = part == 0 ? 0 : std::min<int64_t>(d.n, r.frame_begin * d.hop);
+    r.out_end = part == parts - 1 ? d.n : std::min<int64_t>(d.n, r.frame_end * d.hop);
+    // tiles whose overlap-add segments cover the part's output samples
+    const int64_t BH = (int64_t)d.B * d.hop;
+    if (r.out_end > r.out_begin) {
+        const int64_t num = r.out_begin + d.M - d.seg_len + 1;
+        r.need_begin = num <= 0 ? 0 : (num + BH - 1) / BH;
+        r.need_end = std::min<int64_t>(d.ntiles, (r.out_end - 1 + d.M) / BH + 1);
+    } else {
+        r.need_begin = r.need_end = r.tile_begin;
+    }
+    *out = r;
+    return SST_OK;
+}
+
+SST_API sst_status sst_part_segments(sst_plan_t plan, size_t *ola_offset, int32_t *seg_len, int64_t *tiles) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    if (ola_offset) *ola_offset = plan->ws_off_ola;
+    if (seg_len) *seg_len = plan->d.seg_len;
+    if (tiles) *tiles = plan->d.ntiles;
+    return SST_OK;
+}
+
+SST_API sst_status sst_part_prepass(sst_plan_t plan, const sst_part *part, const float *x_dev, float *r_dev,
+                                    void *ws, void *stream) {
+    sst_status s = part_check(plan, part, ws);
+    if (s != SST_OK) return s;
+    if (!r_dev) return fail(SST_EINVAL, "output pointer is NULL");
+    if (!x_dev && part->x_end > part->x_begin) return fail(SST_EINVAL, "input pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *partial = ws_partial(plan, ws);
+    SstDev d = plan->d;
+    d.xoff = part->x_begin;
+    int count = 0;
+    if (part->frame_end <= part->frame_begin) {
+        SST_CU(cudaMemsetAsync(r_dev, 0, sizeof(float), st), "empty part");
+        return SST_OK;
+    }
+    if (d.relative) {
+        // whole groups of four frames (see sst_part_layout)
+        d.frame_lo = part->frame_begin / 4 * 4;
+        d.frame_hi = std::min<int64_t>(d.F, (part->frame_end + 3) / 4 * 4);
+        const int64_t quads = (d.frame_hi + 3) / 4 - d.frame_lo / 4;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(plan->grid_absmax, quads));
+        SST_LAUNCHED_K(PK_ABSMAX, st, plan->kt->absmax(d, x_dev, partial, grid, plan->smem_absmax, st),
+                       "part pre-pass launch");
+        count = grid;
+    } else {
+        const int64_t len = part->x_end - part->x_begin;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((len + 255) / 256, plan->grid_absmax));
+        SST_LAUNCHED_K(PK_ABSMAX, st, launch_absx(x_dev, len, partial, grid, st), "part max |x| launch");
+        count = grid;
+    }
+    SST_LAUNCHED_K(PK_GAMMA, st, (k_reduce_max<<<1, 256, 0, st>>>(partial, count, r_dev), cudaGetLastError()),
+                   "part reduce launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_part_forward_inverse(sst_plan_t plan, const sst_part *part, const float *x_dev,
+                                            const float *r_dev, void *ws, void *stream) {
+    sst_status s = part_check(plan, part, ws);
+    if (s != SST_OK) return s;
+    if (!r_dev) return fail(SST_EINVAL, "pre-pass maximum pointer is NULL");
+    if (!x_dev && part->x_end > part->x_begin) return fail(SST_EINVAL, "input pointer is NULL");
+    if (!plan->fused_ok)
+        return fail(SST_EUNSUPPORTED, "a split signal needs the fused kernel, whose %zu bytes of shared memory "
+                    "this plan exceeds", plan->smem_fused);
+    if (part->tile_end <= part->tile_begin) return SST_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SstScalars *sc = ws_scalars(plan, ws);
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   launch_gamma(r_dev, 1, plan->gamma_frac2, plan->d.relative ? 0 : 1, plan->sum_abs_g,
+                                plan->d.log2_nb, sc, nullptr, nullptr, st),
+                   "part scalars launch");
+    SstDev d = plan->d;
+    d.xoff = part->x_begin;
+    d.tile0 = part->tile_begin;
+    d.ntiles = part->tile_end - part->tile_begin;   // the launch's grid
+    SST_LAUNCHED_K(PK_FUSED, st, plan->kt->fused(d, plan->kind_fused, x_dev, sc, ws_ola(plan, ws), plan->smem_fused, st),
+                   "part fused launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_part_finalize(sst_plan_t plan, const sst_part *part, void *ws, float *xhat_dev,
+                                     void *stream) {
+    sst_status s = part_check(plan, part, ws);
+    if (s != SST_OK) return s;
+    if (part->out_end < part->out_begin || part->out_begin < 0 || part->out_end > plan->d.n)
+        return fail(SST_EINVAL, "output range outside the signal");
+    if (part->out_end == part->out_begin) return SST_OK;
+    if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t len = part->out_end - part->out_begin;
+    const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 4096);
+    SST_LAUNCHED_K(PK_FINALIZE, st,
+                   (k_finalize_range<<<blocks, 256, 0, st>>>(plan->d, ws_ola(plan, ws), xhat_dev, part->out_begin,
+                                                             part->out_end),
+                    cudaGetLastError()),
+                   "part finalize launch");
     return SST_OK;
 }
 

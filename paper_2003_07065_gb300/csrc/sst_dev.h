@@ -74,6 +74,11 @@ struct SstDev {
     unsigned *status;
     // test hook: CTA 0 does not issue its first row copy, so that wait expires
     int test_withhold;
+    // one part of a signal split by frame ranges (sst_part_*): the pre-pass
+    // takes only frames [frame_lo, frame_hi) (frame_hi = 0: every frame), and
+    // the fused kernel's CTA b works on inverse tile tile0 + b
+    int64_t frame_lo, frame_hi;
+    int64_t tile0;
 };
 #define SST_DEV_WAIT_EXPIRED 0x1u
 #define SST_DEV_COPY_LOST 0x2u

@@ -219,7 +219,8 @@ __device__ __forceinline__ float absmax_quad(const SstDev &d, const float *__res
 #pragma unroll
     for (int f = 0; f < NB; ++f) {
         const int64_t a = 4 * qq + 2 * f;
-        const bool hasa = a < d.F, hasb = a + 1 < d.F;
+        const int64_t flo = d.frame_lo, fhi = d.frame_hi ? d.frame_hi : d.F;
+        const bool hasa = a >= flo && a < fhi, hasb = a + 1 >= flo && a + 1 < fhi;
         const int64_t ca = hasa ? a * d.hop : -(int64_t)4 * NF - d.n;   // absent frame: all taps outside [0, n)
         gather_first<NF, true>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
     }
@@ -257,10 +258,11 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     float *red = reinterpret_cast<float *>(buf + 2 * C::BUF);
     const int tid = threadIdx.x;
     if (d.gate && *d.gate == 0u) return;
-    const int64_t nquads = (d.F + 3) / 4;
+    // quads of frames [frame_lo, frame_hi) (every frame when frame_hi = 0)
+    const int64_t q_lo = d.frame_lo / 4, nquads = ((d.frame_hi ? d.frame_hi : d.F) + 3) / 4;
     const int64_t step = d.sample_stride > 1 ? d.sample_stride : 1;
     float best = 0.f;
-    for (int64_t qq = blockIdx.x * step; qq < nquads; qq += gridDim.x * step)
+    for (int64_t qq = q_lo + blockIdx.x * step; qq < nquads; qq += gridDim.x * step)
         best = absmax_quad<NF>(d, x, qq, buf, tid, best);
     best = block_max<C::NWARP>(best, red, tid);
     if (tid == 0) partial[blockIdx.x] = best;
@@ -1067,7 +1069,7 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     float2 *mz = reinterpret_cast<float2 *>(after);
     float *seg = reinterpret_cast<float *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
     const FwdScale fs = fwd_scale(d, sc, true);
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = d.tile0 + blockIdx.x;
     const int64_t m0 = tile * d.B;
     const float cnorm = 1.0f / (float)NF;
     const bool live = (TPF == NS) || tid < NS;

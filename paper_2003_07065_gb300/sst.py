@@ -44,6 +44,14 @@ class sst_param_report(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class sst_part(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("tile_begin", "tile_end", "frame_begin", "frame_end", "x_begin",
+                                               "x_end", "out_begin", "out_end", "need_begin", "need_end")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 SST_GUARD_EQ38 = 0x1
 SST_GUARD_EQ46 = 0x2
 
@@ -87,6 +95,12 @@ def load():
         "sst_params_check": ([ctypes.POINTER(sst_params), ctypes.POINTER(sst_param_report)], ctypes.c_int),
         "sst_plan_check": ([_vp, ctypes.POINTER(sst_param_report)], ctypes.c_int),
         "sst_forward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_part_layout": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(sst_part)], ctypes.c_int),
+        "sst_part_segments": ([_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(_i64)], ctypes.c_int),
+        "sst_part_prepass": ([_vp, ctypes.POINTER(sst_part), _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_part_forward_inverse": ([_vp, ctypes.POINTER(sst_part), _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_part_finalize": ([_vp, ctypes.POINTER(sst_part), _vp, _vp, _vp], ctypes.c_int),
         "sst_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_inverse": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_inverse_zone": ([_vp, _vp, _i64, _vp, ctypes.c_int32, _vp, _vp, _vp], ctypes.c_int),
@@ -267,6 +281,32 @@ def sst_plan_check(plan: int) -> dict:
     r = sst_param_report()
     _check(load().sst_plan_check(plan, ctypes.byref(r)))
     return _report(r)
+
+
+def sst_part_layout(plan, part: int, parts: int) -> sst_part:
+    out = sst_part()
+    _check(load().sst_part_layout(plan, part, parts, ctypes.byref(out)))
+    return out
+
+
+def sst_part_segments(plan) -> tuple:
+    """(byte offset of tile 0's segment in the workspace, floats per segment, tiles)."""
+    off, sl, nt = ctypes.c_size_t(), ctypes.c_int32(), _i64()
+    _check(load().sst_part_segments(plan, ctypes.byref(off), ctypes.byref(sl), ctypes.byref(nt)))
+    return off.value, sl.value, nt.value
+
+
+def sst_part_prepass(plan, part, x, r, workspace, stream=None):
+    _check(load().sst_part_prepass(plan, ctypes.byref(part), _ptr(x), _ptr(r), _ptr(workspace), _stream(stream)))
+
+
+def sst_part_forward_inverse(plan, part, x, r, workspace, stream=None):
+    _check(load().sst_part_forward_inverse(plan, ctypes.byref(part), _ptr(x), _ptr(r), _ptr(workspace),
+                                           _stream(stream)))
+
+
+def sst_part_finalize(plan, part, workspace, xhat, stream=None):
+    _check(load().sst_part_finalize(plan, ctypes.byref(part), _ptr(workspace), _ptr(xhat), _stream(stream)))
 
 
 def sst_plan_destroy(plan: int) -> None:
