@@ -255,9 +255,17 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ batched workload
-def run_batch(args):
+def params_flops(p: dict) -> dict:
+    """flops_per_frame for a plan's parameter dict."""
+    import types
+    return flops_per_frame(types.SimpleNamespace(**p))
+
+
+def batch_leg(args) -> dict:
     """256 mixed channels in one captured CUDA graph (per-NF persistent
-    launches over a work-item table), autotuned; reports tuned vs untuned."""
+    launches over a work-item table), autotuned; tuned vs untuned time, the
+    timed rate and the FP32 roofline fraction of the batch's algorithmic
+    FLOPs (pre-pass, forward, inverse of every channel)."""
     import torch
     from paper_2003_07065_gb300 import build, sst
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -266,12 +274,15 @@ def run_batch(args):
     chans = W.batch_channels(256)
     plans, items, keep = [], [], []
     tfr_bytes = 0
+    flops = 0.0
     for params, x in chans:
         pl = sst.Plan(**params)
         xd = torch.from_numpy(x).cuda()
         t = pl.new_tfr()
         xh = torch.empty(pl.n, dtype=torch.float32, device="cuda")
         tfr_bytes += t.numel() * 4
+        fl = params_flops(params)
+        flops += pl.frames * (fl["forward"] + fl["inverse"] + (fl["absmax"] / 2 if params["relative"] else 0.0))
         plans.append(pl)
         keep.append((xd, t, xh))
         items.append((pl.handle, xd, pl.n, t, xh))
@@ -300,21 +311,40 @@ def run_batch(args):
     launches = sst.sst_launch_count() - l0
     clocks = sampler.stop()
     t_ms = sum(a.elapsed_time(c) for a, c in evs)
-    line = {
-        "metric": METRIC, "value": total * args.steps / (t_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch256", "channels": len(chans), "total_samples": total,
-                   "tfr_bytes": tfr_bytes, "lengths": "log-uniform [2^14, 2^22]",
-                   "nfft": "512..8192", "hop": "8..64", "z": "1,2,4", "graph": True,
-                   "l2": "flushed before each timed step"},
+    peak = sst.sst_fp32_peak(stream)
+    step_s = t_ms / args.steps / 1e3
+    out = {
+        "value": total * args.steps / (t_ms / 1e3), "unit": UNIT, "steps": args.steps,
+        "ms_per_step": t_ms / args.steps, "total_samples": total, "tfr_bytes": tfr_bytes,
         "autotune": {"untuned_ms": untuned_ms, "tuned_ms": tuned_ms, "knobs": knobs},
+        "roofline": {"bound": "alu", "achieved": flops / step_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / step_s / 1e12 / peak, "algorithmic_flops": flops,
+                     "note": "pre-pass (half a packed FFT per frame), forward and inverse of every channel, "
+                             "conventional 5 N log2 N per complex FFT; peak as sst_fp32_peak"},
         "gpu_launches": launches, "clocks": clocks,
     }
-    print(json.dumps(line))
     sst.sst_batch_destroy(b)
     for pl in plans:
         pl.close()
+    del keep, flush, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    leg = batch_leg(args)
+    line = {
+        "metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": leg["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch256", "channels": 256, "total_samples": leg["total_samples"],
+                   "tfr_bytes": leg["tfr_bytes"], "lengths": "log-uniform [2^14, 2^22]",
+                   "nfft": "512..8192", "hop": "8..64", "z": "1,2,4", "graph": True,
+                   "l2": "flushed before each timed step"},
+        "autotune": leg["autotune"], "roofline": leg["roofline"],
+        "gpu_launches": leg["gpu_launches"], "clocks": leg["clocks"],
+    }
+    print(json.dumps(line))
     return 0
 
 
@@ -385,15 +415,13 @@ def tensor_forms(args, w, params, x, clean, stream, flush, bf16_peak):
     return forms, bins
 
 
-def run_tensor(args):
+def tensor_leg(args) -> dict:
     """Precision workload (Nf 4096, L 2049, hop 16; the 0-6.4 kHz band at
     25.6 kHz = 1025 bins): one step = forward (the FFT form, or the tcgen05
     contraction in one of its three operand forms) + the shared direct inverse.
-    Every form's time and reconstruction SNR (against the clean signal) is
-    reported; the headline is the BF16 tensor form.  The same is timed on the
-    literal 512-bin shape (k = 0..511).  The roofline is the contraction's,
-    against the measured dense BF16 tensor peak (TF32 at the nominal TF32 /
-    BF16 ratio)."""
+    Every form's time and reconstruction SNR (against the clean signal); the
+    same on the literal 512-bin shape (k = 0..511).  Single GPU only: it loads
+    the tensor-form library."""
     import dataclasses
     import torch
     from paper_2003_07065_gb300 import build, sst
@@ -416,31 +444,53 @@ def run_tensor(args):
     launches = sst.sst_launch_count() - l0
     clocks = sampler.stop()
     head = forms["bf16"]
+    best = max((f for f in forms if f != "fft" and abs(forms[f]["snr_db"] - forms["fft"]["snr_db"]) <= 0.1),
+               key=lambda f: forms[f]["samples_per_s"], default="bf16")
+    del flush
+    return {
+        "w": w, "bins": bins, "head": head, "forms": forms, "forms512": forms512, "bins512": bins512, "w512": w512,
+        "vs_fft_form": head["samples_per_s"] / forms["fft"]["samples_per_s"],
+        "snr_gap_db": head["snr_db"] - forms["fft"]["snr_db"],
+        "best_form_at_equal_snr": {"form": best, "vs_fft_form": forms[best]["samples_per_s"] /
+                                   forms["fft"]["samples_per_s"],
+                                   "snr_gap_db": forms[best]["snr_db"] - forms["fft"]["snr_db"]},
+        "bf16_peak": bf16_peak, "gpu_launches": launches, "clocks": clocks,
+    }
+
+
+def run_tensor(args):
+    """The tensor-form leg as its own JSON line; the headline is the BF16
+    tensor form, its roofline the contraction's against the measured dense
+    BF16 tensor peak (TF32 at the nominal TF32 / BF16 ratio)."""
+    leg = tensor_leg(args)
+    w, head, forms = leg["w"], leg["head"], leg["forms"]
     line = {
         "metric": METRIC, "value": head["samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "fs": w.fs, "nfft": w.nfft, "hop": w.hop, "L": w.L,
-                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "bins": bins,
+                   "sigma": w.sigma, "z": w.z, "band_hz": [w.f_lo, w.f_hi], "bins": leg["bins"],
                    "form": "bf16 tcgen05 contraction + FP32 inverse", "l2": "flushed before each timed step"},
-        "vs_fft_form": head["samples_per_s"] / forms["fft"]["samples_per_s"],
-        "snr_gap_db": head["snr_db"] - forms["fft"]["snr_db"],
+        "vs_fft_form": leg["vs_fft_form"],
+        "snr_gap_db": leg["snr_gap_db"],
+        "best_form_at_equal_snr": leg["best_form_at_equal_snr"],
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm", "achieved": head["contraction"]["tflops"],
-                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": head["contraction"]["frac"], "traffic": None,
-                     "peak_note": "measured dense BF16 burst (MEASURED_PEAKS.json)"},
+                     "peak": leg["bf16_peak"], "unit": "TFLOP/s", "frac": head["contraction"]["frac"],
+                     "traffic": None, "peak_note": "measured dense BF16 burst (MEASURED_PEAKS.json)"},
         "forms": forms,
-        "literal_512_bins": {"band_hz": [w512.f_lo, w512.f_hi], "bins": bins512, "forms": forms512},
-        "gpu_launches": launches, "clocks": clocks,
+        "literal_512_bins": {"band_hz": [leg["w512"].f_lo, leg["w512"].f_hi], "bins": leg["bins512"],
+                             "forms": leg["forms512"]},
+        "gpu_launches": leg["gpu_launches"], "clocks": leg["clocks"],
     }
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------ streaming workload
-def run_stream(args):
+def stream_leg(args, dur: float, overload_s: float = 3.0) -> dict:
     """64 sensor streams at 25.6 kHz pushing 8192-sample chunks with Poisson
     arrivals (2 chunks/s per stream; bursts of 1 s at 5x the rate starting as
-    a 0.1/s Poisson process), served in real time for --seconds: p50/p99
+    a 0.1/s Poisson process), served in real time for `dur` seconds: p50/p99
     latency (tick completion minus scheduled arrival).  Then an overload phase
     (every stream's queue kept full) gives the sustained samples/s."""
     import torch
@@ -450,7 +500,6 @@ def run_stream(args):
     sst.load()
     nstreams, fs, chunk = 64, 25600.0, 8192
     P = dict(fs=fs, L=1025, sigma=128.0, hop=16, nfft=2048, f_lo=0.0, f_hi=8000.0, z=2)
-    dur = args.seconds
     # arrival schedules
     sched = []
     for i in range(nstreams):
@@ -513,8 +562,8 @@ def run_stream(args):
                 time.sleep(min(wait, 0.002))
     wall = time.monotonic() - t0
     p50, p99, nlat = sst.sst_service_latency(svc, reset=True)
-    # overload phase: keep every queue full for ~3 s
-    def overload(svc, ids, pos, seconds=3.0):
+    # overload phase: keep every queue full for overload_s seconds
+    def overload(svc, ids, pos, seconds=overload_s):
         t1 = time.monotonic()
         processed = 0
         while time.monotonic() - t1 < seconds:
@@ -546,10 +595,8 @@ def run_stream(args):
     sst.sst_service_destroy(svc2)
     launches = sst.sst_launch_count() - l0
     sst.sst_service_destroy(svc)
-    line = {
-        "metric": "p50/p99 stream latency; sustained input samples/s", "value": sustained, "unit": "samples/s",
-        "n_gpus": 1, "steps": ticks, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+    return {
+        "value": sustained, "unit": "samples/s", "ticks": ticks, "seconds": dur,
         "config": {"workload": "stream64", "streams": nstreams, "chunk": chunk, "fs": fs, "hop": 16, "nfft": 2048,
                    "L": 1025, "band_hz": [0.0, 8000.0], "z": 2, "arrivals": "Poisson 2/s, 1 s bursts x5 at 0.1/s",
                    "seconds": dur},
@@ -560,6 +607,18 @@ def run_stream(args):
                            "and x-hat delivered to the host"),
         "sustained_xhat_only": {"value": sustained_x, "unit": "samples/s", "p50": x50, "p99": x99},
         "gpu_launches": launches,
+    }
+
+
+def run_stream(args):
+    leg = stream_leg(args, args.seconds)
+    line = {
+        "metric": "p50/p99 stream latency; sustained input samples/s", "value": leg["value"], "unit": "samples/s",
+        "n_gpus": 1, "steps": leg["ticks"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": leg["config"],
+        "latency_s": leg["latency_s"], "overload_latency_s": leg["overload_latency_s"],
+        "sustained_note": leg["sustained_note"], "sustained_xhat_only": leg["sustained_xhat_only"],
+        "gpu_launches": leg["gpu_launches"],
     }
     print(json.dumps(line))
     return 0
@@ -788,6 +847,7 @@ def main():
                                              "runup_4m_post"])
     ap.add_argument("--seconds", type=float, default=12.0, help="stream64: simulated real-time seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the tensor-form, stream and batch legs")
     args = ap.parse_args()
     if args.workload == "batch256":
         return run_batch(args)
@@ -958,6 +1018,15 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
                "seconds": el, "cpu_model": cpu_model(),
                "single_thread": {"value": v1, "sample": sample1, "seconds": el1}}
+    legs = None
+    if world == 1 and not args.no_legs:
+        # the rest of the metric, after the headline's timed region: the
+        # tensor form against the FFT form, the streaming service's latency,
+        # the batch's tuned time (the main workload's buffers freed first)
+        plan.close()
+        del tfr, xhat, flush, x
+        torch.cuda.empty_cache()
+        legs = run_legs(args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -972,6 +1041,7 @@ def main():
         "kernels": kern,
         "roofline": roof,
         "variants": {"no_tfr_output": fused},
+        "legs": legs,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n, "d2h_bytes_per_step": 4 * w.n},
         "clocks": clocks,
@@ -982,6 +1052,41 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_legs(args) -> dict:
+    """Short runs of the other workloads for the headline line (one GPU)."""
+    import types
+    out = {}
+    k = types.SimpleNamespace(steps=max(3, min(args.steps, 5)), warmup=3)
+    try:
+        t = tensor_leg(k)
+        out["precision64k_tc"] = {
+            "bf16_vs_fft_form": t["vs_fft_form"], "bf16_snr_gap_db": t["snr_gap_db"],
+            "best_form_at_equal_snr": t["best_form_at_equal_snr"],
+            "forms": {f: {"ms_per_step": v["ms_per_step"], "snr_db": v["snr_db"],
+                          "contraction_frac": v.get("contraction", {}).get("frac")} for f, v in t["forms"].items()},
+            "bf16_peak_tflops": t["bf16_peak"]}
+    except Exception as e:   # reported, never fatal to the headline
+        out["precision64k_tc"] = {"error": repr(e)}
+    try:
+        st = stream_leg(k, dur=4.0, overload_s=2.0)
+        out["stream64"] = {"p50_s": st["latency_s"]["p50"], "p99_s": st["latency_s"]["p99"],
+                           "chunks": st["latency_s"]["chunks"], "dropped": st["latency_s"]["dropped_chunks"],
+                           "offered_samples_per_s": st["latency_s"]["offered_samples_per_s"],
+                           "sustained_samples_per_s": st["value"],
+                           "sustained_xhat_only_samples_per_s": st["sustained_xhat_only"]["value"],
+                           "seconds": st["seconds"]}
+    except Exception as e:
+        out["stream64"] = {"error": repr(e)}
+    try:
+        b = batch_leg(k)
+        out["batch256"] = {"samples_per_s": b["value"], "ms_per_step": b["ms_per_step"],
+                           "untuned_ms": b["autotune"]["untuned_ms"], "tuned_ms": b["autotune"]["tuned_ms"],
+                           "roofline_frac": b["roofline"]["frac"], "total_samples": b["total_samples"]}
+    except Exception as e:
+        out["batch256"] = {"error": repr(e)}
+    return out
 
 
 if __name__ == "__main__":
