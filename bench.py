@@ -476,7 +476,10 @@ def run_tensor(args):
         "best_form_at_equal_snr": leg["best_form_at_equal_snr"],
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm", "achieved": head["contraction"]["tflops"],
                      "peak": leg["bf16_peak"], "unit": "TFLOP/s", "frac": head["contraction"]["frac"],
-                     "traffic": None, "peak_note": "measured dense BF16 burst (MEASURED_PEAKS.json)"},
+                     "traffic": None,
+                     "peak_note": ("of measured: dense BF16 burst (MEASURED_PEAKS.json)" if measured_peaks().get(
+                         "bf16_tflops") else f"of fallback: {FALLBACK_BF16_TFLOPS} TFLOP/s dense BF16 (no "
+                         "MEASURED_PEAKS.json on this machine)")},
         "forms": forms,
         "literal_512_bins": {"band_hz": [leg["w512"].f_lo, leg["w512"].f_hi], "bins": leg["bins512"],
                              "forms": leg["forms512"]},
@@ -1066,7 +1069,8 @@ def run_legs(args) -> dict:
             "best_form_at_equal_snr": t["best_form_at_equal_snr"],
             "forms": {f: {"ms_per_step": v["ms_per_step"], "snr_db": v["snr_db"],
                           "contraction_frac": v.get("contraction", {}).get("frac")} for f, v in t["forms"].items()},
-            "bf16_peak_tflops": t["bf16_peak"]}
+            "bf16_peak_tflops": t["bf16_peak"],
+            "bf16_peak_source": "measured" if measured_peaks().get("bf16_tflops") else "fallback"}
     except Exception as e:   # reported, never fatal to the headline
         out["precision64k_tc"] = {"error": repr(e)}
     try:
