@@ -63,10 +63,6 @@ typedef enum {
  * of max|V| (the FP32 STFT of two different FFT packings); batch results are
  * bit-identical to single-plan results of plans with this flag. */
 #define SST_TWO_PASS 0x2u
-/* Run the forward one frame at a time instead of two at a time (the default
- * wherever the two-frame kernel's shared memory fits).  Results are the same;
- * the flag exists for comparisons and for devices short of shared memory. */
-#define SST_FORWARD_SINGLE 0x4u
 
 typedef struct sst_plan *sst_plan_t;
 

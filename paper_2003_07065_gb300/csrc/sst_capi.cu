@@ -293,8 +293,7 @@ static sst_status validate(const sst_params *p) {
     if (!(p->gamma >= 0.0) || !std::isfinite(p->gamma)) return fail(SST_EINVAL, "gamma must be finite and >= 0");
     if ((p->g == nullptr) != (p->dg == nullptr)) return fail(SST_EINVAL, "give both g and dg, or neither");
     if (!p->g && !(p->sigma > 0.0)) return fail(SST_EINVAL, "sigma must be > 0 when g is not given");
-    if (p->flags & ~(SST_GAMMA_RELATIVE | SST_TWO_PASS | SST_FORWARD_SINGLE))
-        return fail(SST_EINVAL, "unknown flags 0x%x", p->flags);
+    if (p->flags & ~(SST_GAMMA_RELATIVE | SST_TWO_PASS)) return fail(SST_EINVAL, "unknown flags 0x%x", p->flags);
     return SST_OK;
 }
 
@@ -534,39 +533,15 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 3) / 4);
     pl->grid_fwd = grid_for(pl->kind_fwd_t, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
-    // the forward two frames at a time where its shared memory fits (unless
-    // SST_FORWARD_SINGLE): same results, half the barriers per frame
-    const int fwd_cls = half_window ? bcls : 0;
-    const int frame_buf = (int)((kt->smem_frame - 128) / sizeof(float2));
-    const bool two_frames = !(p.flags & SST_FORWARD_SINGLE);
-    if (two_frames) {
-        const size_t b2 = forward2_smem_bytes(frame_buf, nb, nbo, fwd_cls, false);
-        const int k2 = kind_cls(KIND_FWD_T2, fwd_cls);
-        if (b2 <= smax && raise_smem(kt, k2, b2) == cudaSuccess) {
-            pl->kind_fwd_t = k2;
-            pl->smem_fwd_t = b2;
-            pl->grid_fwd = grid_for(k2, b2, (F + 1) / 2);
-        }
-    }
 
     // ---- one-pass relative threshold (default for relative plans)
-    // (the one-frame forward's size: the two-frame kind replaces it below where it fits)
-    pl->smem_fwd_spec = kt->smem_frame + tacc_bytes(nbo) + ((half_window && bcls > 0) ? mirror_bytes(nb) : 0) +
-                        (spec_in_frame(nb, nbo, frame_buf) ? 0 : spec_smem_bytes(nbo));
+    pl->smem_fwd_spec = pl->smem_fwd_t +
+                        (spec_in_frame(nb, nbo, (int)((kt->smem_frame - 128) / sizeof(float2))) ? 0 : spec_smem_bytes(nbo));
     pl->spec = d.relative && !(p.flags & SST_TWO_PASS) && pl->smem_fwd_spec <= smax;
     if (pl->spec) {
         ce = raise_smem(kt, pl->kind_fwd_spec, pl->smem_fwd_spec);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
         pl->grid_fwd_spec = grid_for(pl->kind_fwd_spec, pl->smem_fwd_spec, F);
-        if (two_frames) {
-            const size_t b2 = forward2_smem_bytes(frame_buf, nb, nbo, fwd_cls, true);
-            const int k2 = kind_cls(KIND_FWD_SPEC2, fwd_cls);
-            if (b2 <= smax && raise_smem(kt, k2, b2) == cudaSuccess) {
-                pl->kind_fwd_spec = k2;
-                pl->smem_fwd_spec = b2;
-                pl->grid_fwd_spec = grid_for(k2, b2, (F + 1) / 2);
-            }
-        }
         // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
         pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop + 1));
         // records: 1/64 of the sources, plus the chunk tails each CTA may leave unused

@@ -23,12 +23,6 @@ template <int MODE> const void *forward_kernel(int cls) {
     return (const void *)k_forward<NF, MODE, 0>;
 }
 
-template <int MODE> const void *forward2_kernel(int cls) {
-    if (cls == 1) return (const void *)k_forward2<NF, MODE, CLS1>;
-    if (cls == 2) return (const void *)k_forward2<NF, MODE, CLS2>;
-    return (const void *)k_forward2<NF, MODE, 0>;
-}
-
 const void *kernel_of(int kind) {
     const int cls = cls_of(kind);
     switch (kind & ((1 << KIND_CLS_SHIFT) - 1)) {
@@ -37,8 +31,6 @@ const void *kernel_of(int kind) {
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
         case KIND_FWD_SPEC: return forward_kernel<MODE_SPEC>(cls);
-        case KIND_FWD_T2: return forward2_kernel<MODE_T>(cls);
-        case KIND_FWD_SPEC2: return forward2_kernel<MODE_SPEC>(cls);
         case KIND_INV:
             if (cls == 1) return (const void *)k_inverse<NF, true, CLS1>;
             if (cls == 2) return (const void *)k_inverse<NF, true, CLS2>;
@@ -82,14 +74,6 @@ void launch_forward(int cls, const SstDev &d, const float *x, const SstScalars *
     else k_forward<NF, MODE, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
 }
 
-template <int MODE>
-void launch_forward2(int cls, const SstDev &d, const float *x, const SstScalars *sc, void *out0, void *out1, int grid,
-                     size_t smem, cudaStream_t st) {
-    if (cls == 1) k_forward2<NF, MODE, CLS1><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
-    else if (cls == 2) k_forward2<NF, MODE, CLS2><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
-    else k_forward2<NF, MODE, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
-}
-
 cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0, void *out1,
                     int grid, size_t smem, cudaStream_t st) {
     const int cls = cls_of(kind);
@@ -105,12 +89,6 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
             break;
         case KIND_FWD_SPEC:
             launch_forward<MODE_SPEC>(cls, d, x, sc, out0, out1, grid, smem, st);
-            break;
-        case KIND_FWD_T2:
-            launch_forward2<MODE_T>(cls, d, x, sc, out0, out1, grid, smem, st);
-            break;
-        case KIND_FWD_SPEC2:
-            launch_forward2<MODE_SPEC>(cls, d, x, sc, out0, out1, grid, smem, st);
             break;
         default: return cudaErrorInvalidValue;
     }

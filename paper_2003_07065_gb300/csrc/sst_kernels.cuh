@@ -580,20 +580,25 @@ __device__ __forceinline__ void frame_bin(const SstDev &d, const FwdScale &fs, f
 // X[k] stay in the registers of the thread that computed them and only the
 // mirrors X[NF - k] pass through mz (nb float2 outside the frame buffer), so
 // the last FFT pass needs no barrier of its own.
-// The epilogue of one frame m after its FFT: every band bin through frame_bin
-// (REG: X[k] from the registers v of the last pass, mirrors from mz; else
-// both from zc, zm), a barrier, the MODE_SPEC records, and the read-out of
-// the frame's T row (clearing the accumulators).
-template <int NF, int MODE, int CLS>
-__device__ __forceinline__ void frame_epilogue(const SstDev &d, const FwdScale &fs, float2 *__restrict__ out0,
-                                               void *__restrict__ out1, int64_t m, const float2 (&v)[16],
-                                               const float2 *zc, const float2 *zm, const float2 *mz, uint32_t *acc,
-                                               int tid, SpecFrame *sf, int *nmarg, float *vmax, SpecCursor *cur) {
+template <int NF, int MODE, int CLS = 0>
+__device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
+                                              float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
+                                              float2 *buf, uint32_t *acc, int tid, SpecFrame *sf = nullptr,
+                                              int *nmarg = nullptr, float *vmax = nullptr,
+                                              SpecCursor *cur = nullptr, float2 *mz = nullptr) {
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
     constexpr bool REG = CLS > 0;
     constexpr unsigned OMASK = band_mask<NF>(CLS);
+    float2 v[16];
+    forward_fft<NF, false, window_mask<NF>(CLS), !REG>(buf, d, x, m * d.hop, 0, false, tid, v);
+    float2 *zc = buf, *zm = buf + d.nb;
+    if constexpr (REG) store_mirror<NF, OMASK>(mz, d, tid, v);
+    else scatter_band<NF, OMASK>(zc, zm, d, tid, v);
+    if (MODE == MODE_SPEC && tid == 0) *nmarg = 0;
+    __syncthreads();
+
     if constexpr (REG) {
         if (TPF == NS || tid < NS) {
             const unsigned span = (unsigned)(d.k_hi - d.k_lo);
@@ -626,83 +631,8 @@ __device__ __forceinline__ void frame_epilogue(const SstDev &d, const FwdScale &
         }
     }
     for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
-}
-
-template <int NF, int MODE, int CLS = 0>
-__device__ __forceinline__ void forward_frame(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
-                                              float2 *__restrict__ out0, void *__restrict__ out1, int64_t m,
-                                              float2 *buf, uint32_t *acc, int tid, SpecFrame *sf = nullptr,
-                                              int *nmarg = nullptr, float *vmax = nullptr,
-                                              SpecCursor *cur = nullptr, float2 *mz = nullptr) {
-    constexpr bool REG = CLS > 0;
-    constexpr unsigned OMASK = band_mask<NF>(CLS);
-    float2 v[16];
-    forward_fft<NF, false, window_mask<NF>(CLS), !REG>(buf, d, x, m * d.hop, 0, false, tid, v);
-    float2 *zc = buf, *zm = buf + d.nb;
-    if constexpr (REG) store_mirror<NF, OMASK>(mz, d, tid, v);
-    else scatter_band<NF, OMASK>(zc, zm, d, tid, v);
-    if (MODE == MODE_SPEC && tid == 0) *nmarg = 0;
-    __syncthreads();
-    frame_epilogue<NF, MODE, CLS>(d, fs, out0, out1, m, v, zc, zm, mz, acc, tid, sf, nmarg, vmax, cur);
-    // the zeroing of the accumulators is ordered before the next frame's
-    // atomics by the __syncthreads inside the next frame's FFT
-}
-
-// Two frames m and m + 1 (the second absent when !hasb): both FFTs run
-// through the passes together (half the barriers per frame, twice the
-// independent work between them), then the epilogues follow one after the
-// other through the one set of accumulators.  buf holds two frame buffers
-// BUF float2 apart; sf[f], nmarg[f], mz[f] are frame f's.
-template <int NF, int MODE, int CLS>
-__device__ __forceinline__ void forward_pair(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
-                                             float2 *__restrict__ out0, void *__restrict__ out1, int64_t m, bool hasb,
-                                             float2 *buf, uint32_t *acc, int tid, SpecFrame *sf0, SpecFrame *sf1,
-                                             int *nmarg, float *vmax, SpecCursor *cur, float2 *mz0, float2 *mz1) {
-    using C = Cfg<NF>;
-    constexpr int TPF = C::TPF;
-    constexpr int BS = C::BUF;
-    constexpr bool REG = CLS > 0;
-    constexpr unsigned OMASK = band_mask<NF>(CLS), WMASK = window_mask<NF>(CLS);
-    float2 v[2][16];
-    {
-        float2 u[C::PER1][C::R1];
-        gather_first<NF, false, WMASK>(u, d, x, m * d.hop, 0, false, tid);
-        fft_first_from_regs<NF, TPF, false, WMASK>(buf, u, tid);
-        // an absent second frame: every tap outside [0, n), so its input is zero
-        const int64_t cb = hasb ? (m + 1) * d.hop : -(int64_t)4 * NF - d.n;
-        gather_first<NF, false, WMASK>(u, d, x, cb, 0, false, tid);
-        fft_first_from_regs<NF, TPF, false, WMASK>(buf + BS, u, tid);
-    }
-    __syncthreads();
-    fft_middle_multi<NF, TPF, C::R1, false, 2, BS>(buf, d.tw, tid);
-    fft_last_multi<NF, TPF, false, 2, BS>(buf, d.tw, tid, v);   // ends with a barrier
-    float2 *zc0 = buf, *zm0 = buf + d.nb, *zc1 = buf + BS, *zm1 = buf + BS + d.nb;
-    if constexpr (REG) {
-        store_mirror<NF, OMASK>(mz0, d, tid, v[0]);
-        store_mirror<NF, OMASK>(mz1, d, tid, v[1]);
-    } else {
-        scatter_band<NF, OMASK>(zc0, zm0, d, tid, v[0]);
-        scatter_band<NF, OMASK>(zc1, zm1, d, tid, v[1]);
-    }
-    if (MODE == MODE_SPEC && tid == 0) {
-        nmarg[0] = 0;
-        nmarg[1] = 0;
-    }
-    __syncthreads();
-    frame_epilogue<NF, MODE, CLS>(d, fs, out0, out1, m, v[0], zc0, zm0, mz0, acc, tid, sf0, nmarg, vmax, cur);
-    if (hasb) {
-        __syncthreads();   // frame m's read-out cleared the accumulators
-        frame_epilogue<NF, MODE, CLS>(d, fs, out0, out1, m + 1, v[1], zc1, zm1, mz1, acc, tid, sf1, nmarg + 1, vmax,
-                                      cur);
-    }
-}
-
-// bytes of the two-frame forward's shared memory (layout in k_forward2)
-__host__ __device__ __forceinline__ size_t forward2_smem_bytes(int nf_buf, int nb, int nbo, int cls, bool spec) {
-    size_t o = 2 * 8 * (size_t)nf_buf + 128 + tacc_bytes(nbo);
-    if (cls > 0) o += 2 * mirror_bytes(nb);
-    if (spec && !spec_in_frame(nb, nbo, nf_buf)) o += 2 * ((spec_smem_bytes(nbo) + 15) & ~(size_t)15);
-    return o;
+    // the zeroing above is ordered before the next frame's atomics by the
+    // __syncthreads inside the next frame's FFT
 }
 
 template <int NF, int MODE, int CLS = 0>
@@ -741,61 +671,6 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
     // (the first __syncthreads in forward_frame orders this before any atomic)
     for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
         forward_frame<NF, MODE, CLS>(d, x, fs, out0, out1, m, buf, acc, tid, sf, nmarg, &vmax, &cur, mz);
-    if (MODE == MODE_SPEC) {
-        vmax = warp_max(vmax);
-        if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
-        if (tid == 0) {
-            spec_drop_src(d.spec, cur.src_cur, cur.src_end);
-            spec_drop_bin(d.spec, cur.bin_cur, cur.bin_end);
-        }
-    }
-}
-
-#define SST_FWD2_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : ((512 / Cfg<NF>::TPF > 8) ? 8 : 512 / Cfg<NF>::TPF))
-
-// The forward two frames at a time (forward_pair): frames 2 p, 2 p + 1 for
-// p = blockIdx.x, blockIdx.x + gridDim.x, ...  Shared memory: two frame
-// buffers, 128 bytes of slack (the two MODE_SPEC counters), the accumulators,
-// the two frames' band mirrors (CLS > 0), and their MODE_SPEC lists when
-// those do not fit in the frame buffers.  Same results as k_forward.
-template <int NF, int MODE, int CLS = 0>
-__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_FWD2_MINB)
-k_forward2(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
-           float2 *__restrict__ out0, void *__restrict__ out1) {
-    using C = Cfg<NF>;
-    extern __shared__ float4 smem4[];
-    float2 *buf = reinterpret_cast<float2 *>(smem4);
-    int *nmarg = reinterpret_cast<int *>(buf + 2 * C::BUF);
-    uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 4 * C::BUF + 32;
-    const int tid = threadIdx.x;
-    if (d.gate && *d.gate == 0u) return;
-    FwdScale fs = fwd_scale(d, sc, MODE == MODE_T || MODE == MODE_SPEC);
-    if (MODE == MODE_SPEC) {
-        fs.gamma2 = sc->g_lb2;
-        fs.g_ub2 = sc->g_ub2;
-    }
-    const int stride = tacc_stride(d.nbo);
-    char *after = reinterpret_cast<char *>(acc + 4 * stride);
-    float2 *mz0 = reinterpret_cast<float2 *>(after);
-    float2 *mz1 = reinterpret_cast<float2 *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
-    after += CLS > 0 ? 2 * mirror_bytes(d.nb) : 0;
-    const size_t band_bytes = (16 * (size_t)d.nb + 15) & ~(size_t)15;
-    SpecFrame *sf0, *sf1;
-    if (spec_in_frame(d.nb, d.nbo, C::BUF)) {
-        sf0 = reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(buf) + band_bytes);
-        sf1 = reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(buf + C::BUF) + band_bytes);
-    } else {
-        sf0 = reinterpret_cast<SpecFrame *>(after);
-        sf1 = reinterpret_cast<SpecFrame *>(after + ((spec_smem_bytes(d.nbo) + 15) & ~(size_t)15));
-    }
-    if (MODE == MODE_T || MODE == MODE_SPEC)
-        for (int i = tid; i < 4 * stride; i += C::TPF) acc[i] = 0u;
-    float vmax = 0.f;
-    SpecCursor cur = {0u, 0u, 0u, 0u};
-    // (the first __syncthreads in forward_pair orders this before any atomic)
-    for (int64_t m = 2 * (int64_t)blockIdx.x; m < d.F; m += 2 * (int64_t)gridDim.x)
-        forward_pair<NF, MODE, CLS>(d, x, fs, out0, out1, m, m + 1 < d.F, buf, acc, tid, sf0, sf1, nmarg, &vmax, &cur,
-                                    mz0, mz1);
     if (MODE == MODE_SPEC) {
         vmax = warp_max(vmax);
         if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));

@@ -11,10 +11,9 @@ namespace sst {
 
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
        KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10,
-       KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_FWD_T2 = 13, KIND_FWD_SPEC2 = 14, KIND_COUNT = 15 };
+       KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_COUNT = 13 };
 
-// KIND_FWD_T2 / KIND_FWD_SPEC2: the forward two frames at a time (k_forward2).
-// A forward (KIND_FWD_T, KIND_FWD_SPEC and their two-frame kinds), inverse (KIND_INV) or fused
+// A forward (KIND_FWD_T, KIND_FWD_SPEC), inverse (KIND_INV) or fused
 // forward + inverse (KIND_FUSED) kind may carry a
 // pruning class (band_class, 1 or 2) in the bits from KIND_CLS_SHIFT up;
 // tables whose first radix is not 16 run class 0 for every class.

@@ -17,7 +17,6 @@ from . import build as _build
 
 SST_GAMMA_RELATIVE = 0x1
 SST_TWO_PASS = 0x2
-SST_FORWARD_SINGLE = 0x4
 SST_STREAM_XHAT_ONLY = 0x100
 STATUS = {0: "SST_OK", 1: "SST_EINVAL", 2: "SST_ENOMEM", 3: "SST_ECUDA", 4: "SST_EBUSY",
           5: "SST_ETIMEOUT", 6: "SST_EUNSUPPORTED", 7: "SST_EINTERNAL"}
@@ -227,8 +226,7 @@ def _stream(stream) -> int | None:
 
 
 # ------------------------------------------------------------------ C names
-def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass=False,
-            forward_single=False):
+def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass=False):
     p = sst_params()
     p.n, p.fs, p.L = int(n), float(fs), int(L)
     p.sigma = float(sigma) if sigma is not None else 0.0
@@ -243,19 +241,17 @@ def _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, t
     p.hop, p.nfft = int(hop), int(nfft)
     p.f_lo, p.f_hi, p.z = float(f_lo), float(f_hi), int(z)
     p.gamma = float(gamma)
-    p.flags = ((SST_GAMMA_RELATIVE if relative else 0) | (SST_TWO_PASS if two_pass else 0) |
-               (SST_FORWARD_SINGLE if forward_single else 0))
+    p.flags = (SST_GAMMA_RELATIVE if relative else 0) | (SST_TWO_PASS if two_pass else 0)
     return p, keep
 
 
 def sst_plan_create(n: int, fs: float, L: int, hop: int, nfft: int, f_lo: float, f_hi: float,
                     z: int = 1, gamma: float = 1e-3, relative: bool = True, sigma: float | None = None,
-                    g=None, dg=None, two_pass: bool = False, forward_single: bool = False) -> int:
+                    g=None, dg=None, two_pass: bool = False) -> int:
     """Returns an opaque plan handle (int).  g, dg: optional FP64 numpy windows;
-    two_pass: SST_TWO_PASS (separate max|V| pre-pass for relative thresholds);
-    forward_single: SST_FORWARD_SINGLE (the one-frame forward kernel)."""
+    two_pass: SST_TWO_PASS (separate max|V| pre-pass for relative thresholds)."""
     lib = load()
-    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass, forward_single)
+    p, keep = _params(n, fs, L, hop, nfft, f_lo, f_hi, z, gamma, relative, sigma, g, dg, two_pass)
     out = _vp()
     _check(lib.sst_plan_create(ctypes.byref(p), ctypes.byref(out)))
     del keep

@@ -179,29 +179,3 @@ def test_plan_check_matches_params_check(sst):
     assert a == b
     assert a["hf"] == p["n"] / p["nfft"]
     plan.close()
-
-
-SAME_BITS = [W.ALL["chirp_fm_64k"].params(), W.ALL["runup_256k"].params()] + EDGE
-
-
-@pytest.mark.parametrize("two_pass", [False, True], ids=["one_pass", "two_pass"])
-@pytest.mark.parametrize("params", SAME_BITS, ids=[f"n{p['n']}_nf{p['nfft']}_z{p['z']}" for p in SAME_BITS])
-def test_two_frame_forward_same_bits(sst, params, two_pass):
-    """The forward two frames at a time (the default) and one frame at a time
-    (SST_FORWARD_SINGLE) give the same TFR and reconstruction bit for bit:
-    the same per-frame arithmetic and exact sums, only the schedule differs
-    (odd frame counts leave the last pair's second frame absent)."""
-    gen = np.random.default_rng(params["n"] + 7)
-    t = np.arange(params["n"]) / params["fs"]
-    mid = 0.5 * (params["f_lo"] + params["f_hi"])
-    x = torch.from_numpy((np.cos(2 * np.pi * mid * t) + 0.3 * gen.standard_normal(params["n"]))
-                         .astype(np.float32)).cuda()
-    a = sst.Plan(**params, two_pass=two_pass)
-    b = sst.Plan(**params, two_pass=two_pass, forward_single=True)
-    ta, xa = a.forward_inverse(x)
-    tb, xb = b.forward_inverse(x)
-    torch.cuda.synchronize()
-    assert torch.equal(ta, tb)
-    assert torch.equal(xa, xb)
-    a.close()
-    b.close()
