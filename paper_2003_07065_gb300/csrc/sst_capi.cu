@@ -534,6 +534,13 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->grid_fwd = grid_for(pl->kind_fwd_t, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
 
+    // Forwards of class 1 or 2 keep their band values in registers, so the
+    // frame buffer is free between the last FFT pass and the next frame: the
+    // T accumulators go there (k_forward_alias), a third of the shared memory
+    // and four CTAs per SM instead of three, where they fit in the buffer.
+    const int frame_buf = (int)((kt->smem_frame - 128) / sizeof(float2));
+    const bool fwd_alias = half_window && bcls > 0 && kt->r1 == 16 && tacc_fits_frame(nbo, frame_buf);
+
     // ---- one-pass relative threshold (default for relative plans)
     pl->smem_fwd_spec = pl->smem_fwd_t +
                         (spec_in_frame(nb, nbo, (int)((kt->smem_frame - 128) / sizeof(float2))) ? 0 : spec_smem_bytes(nbo));
@@ -542,12 +549,31 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         ce = raise_smem(kt, pl->kind_fwd_spec, pl->smem_fwd_spec);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
         pl->grid_fwd_spec = grid_for(pl->kind_fwd_spec, pl->smem_fwd_spec, F);
+        if (fwd_alias) {   // (see below)
+            const int ka = kind_cls(KIND_FWD_SPECA, bcls);
+            const size_t ba = forward_alias_smem_bytes(frame_buf, nb, true);
+            if (ba <= smax && raise_smem(kt, ka, ba) == cudaSuccess) {
+                pl->kind_fwd_spec = ka;
+                pl->smem_fwd_spec = ba;
+                pl->grid_fwd_spec = grid_for(ka, ba, F);
+            }
+        }
         // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
         pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop + 1));
         // records: 1/64 of the sources, plus the chunk tails each CTA may leave unused
         pl->spec_cap = (int)std::min<int64_t>(std::max<int64_t>(4096, F * (int64_t)nb / 64) +
                                                   (int64_t)SPEC_CHUNK * pl->grid_fwd_spec,
                                               (int64_t)1 << 28);
+    }
+
+    if (fwd_alias) {
+        const int ka = kind_cls(KIND_FWD_TA, bcls);
+        const size_t ba = forward_alias_smem_bytes(frame_buf, nb, false);
+        if (ba <= smax && raise_smem(kt, ka, ba) == cudaSuccess) {
+            pl->kind_fwd_t = ka;
+            pl->smem_fwd_t = ba;
+            pl->grid_fwd = grid_for(ka, ba, F);
+        }
     }
 
     // ---- workspace: [scalars 256 B][absmax partials][overlap-add partials]

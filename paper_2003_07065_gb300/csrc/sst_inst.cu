@@ -17,6 +17,31 @@ constexpr int CLS1 = cls_for<NF>(1), CLS2 = cls_for<NF>(2);
 
 int cls_of(int kind) { return kind >> KIND_CLS_SHIFT; }
 
+// the forward with aliased accumulators exists for classes 1 and 2 only
+template <int MODE> const void *forward_alias_kernel(int cls) {
+    if constexpr (CLS1 > 0 && CLS2 > 0) {
+        if (cls == 1) return (const void *)k_forward_alias<NF, MODE, CLS1>;
+        if (cls == 2) return (const void *)k_forward_alias<NF, MODE, CLS2>;
+    }
+    return nullptr;
+}
+
+template <int MODE>
+bool launch_forward_alias(int cls, const SstDev &d, const float *x, const SstScalars *sc, void *out0, int grid,
+                          size_t smem, cudaStream_t st) {
+    if constexpr (CLS1 > 0 && CLS2 > 0) {
+        if (cls == 1) {
+            k_forward_alias<NF, MODE, CLS1><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, nullptr);
+            return true;
+        }
+        if (cls == 2) {
+            k_forward_alias<NF, MODE, CLS2><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, nullptr);
+            return true;
+        }
+    }
+    return false;
+}
+
 template <int MODE> const void *forward_kernel(int cls) {
     if (cls == 1) return (const void *)k_forward<NF, MODE, CLS1>;
     if (cls == 2) return (const void *)k_forward<NF, MODE, CLS2>;
@@ -31,6 +56,8 @@ const void *kernel_of(int kind) {
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
         case KIND_FWD_SPEC: return forward_kernel<MODE_SPEC>(cls);
+        case KIND_FWD_TA: return forward_alias_kernel<MODE_T>(cls);
+        case KIND_FWD_SPECA: return forward_alias_kernel<MODE_SPEC>(cls);
         case KIND_INV:
             if (cls == 1) return (const void *)k_inverse<NF, true, CLS1>;
             if (cls == 2) return (const void *)k_inverse<NF, true, CLS2>;
@@ -89,6 +116,12 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
             break;
         case KIND_FWD_SPEC:
             launch_forward<MODE_SPEC>(cls, d, x, sc, out0, out1, grid, smem, st);
+            break;
+        case KIND_FWD_TA:
+            if (!launch_forward_alias<MODE_T>(cls, d, x, sc, out0, grid, smem, st)) return cudaErrorInvalidValue;
+            break;
+        case KIND_FWD_SPECA:
+            if (!launch_forward_alias<MODE_SPEC>(cls, d, x, sc, out0, grid, smem, st)) return cudaErrorInvalidValue;
             break;
         default: return cudaErrorInvalidValue;
     }

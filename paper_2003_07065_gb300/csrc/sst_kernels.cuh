@@ -682,6 +682,100 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// The forward of a pruning class > 0 with the T accumulators in the frame
+// buffer.  Such a forward keeps the band values in registers after the last
+// FFT pass and the mirrors outside the frame buffer, so the buffer is free
+// from the end of the last pass until the next frame's first pass: the
+// accumulators (cleared there each frame) take its place, which more than
+// halves the shared memory of a CTA and lets four CTAs (32 warps) share an
+// SM instead of three.  Same arithmetic as k_forward; two more barriers per
+// frame.  Shared memory: the frame buffer (BUF float2; the accumulators
+// alias its start), 128 bytes of slack (the MODE_SPEC counter), the band
+// mirrors, and the MODE_SPEC list.
+// ---------------------------------------------------------------------------
+#define SST_FWDA_MINB ((1024 / Cfg<NF>::TPF < 1) ? 1 : ((1024 / Cfg<NF>::TPF > 8) ? 8 : 1024 / Cfg<NF>::TPF))
+
+__host__ __device__ constexpr size_t forward_alias_smem_bytes(int nf_buf, int nb, bool spec) {
+    return 8 * (size_t)nf_buf + 128 + mirror_bytes(nb) + (spec ? ((sizeof(SpecFrame) + 15) & ~(size_t)15) : 0);
+}
+// whether the accumulators of nbo fine bins fit in a frame buffer of nf_buf float2
+__host__ __device__ inline bool tacc_fits_frame(int nbo, int nf_buf) { return tacc_bytes(nbo) <= 8 * (size_t)nf_buf; }
+
+template <int NF, int MODE, int CLS>
+__device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
+                                                    float2 *__restrict__ out0, int64_t m, float2 *buf, int tid,
+                                                    SpecFrame *sf, int *nmarg, float *vmax, SpecCursor *cur,
+                                                    float2 *mz) {
+    static_assert(CLS > 0, "the band values must stay in registers");
+    using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
+    constexpr unsigned OMASK = band_mask<NF>(CLS);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(buf);
+    const int stride = tacc_stride(d.nbo);
+    float2 v[16];
+    forward_fft<NF, false, window_mask<NF>(CLS), true>(buf, d, x, m * d.hop, 0, false, tid, v);  // ends with a barrier
+    store_mirror<NF, OMASK>(mz, d, tid, v);
+    uint4 *a4 = reinterpret_cast<uint4 *>(acc);
+    for (int i = tid; i < stride; i += TPF) a4[i] = make_uint4(0u, 0u, 0u, 0u);   // 4 stride words
+    if (MODE == MODE_SPEC && tid == 0) *nmarg = 0;
+    __syncthreads();
+    if (TPF == NS || tid < NS) {
+        const unsigned span = (unsigned)(d.k_hi - d.k_lo);
+        const int kb0 = tid - d.k_lo;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (!((OMASK >> r) & 1u)) continue;
+            const int kk = kb0 + r * NS;
+            if ((unsigned)kk <= span) frame_bin<MODE>(d, fs, out0, nullptr, m, kk, v[r], mz[kk], acc, sf, nmarg, vmax);
+        }
+    }
+    __syncthreads();
+    float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
+    if (MODE == MODE_SPEC) {
+        const int nm = *nmarg;
+        if (nm > 0) {   // (block-uniform)
+            if (tid < 32) spec_records(d, sf, nm, acc, m, tid, cur);
+            __syncthreads();
+        }
+    }
+    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
+    // the read-out done before the next frame's first pass overwrites the buffer
+    __syncthreads();
+}
+
+template <int NF, int MODE, int CLS>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_FWDA_MINB)
+k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
+                float2 *__restrict__ out0, void *__restrict__ out1) {
+    using C = Cfg<NF>;
+    extern __shared__ float4 smem4[];
+    float2 *buf = reinterpret_cast<float2 *>(smem4);
+    int *nmarg = reinterpret_cast<int *>(buf + C::BUF);
+    float2 *mz = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem4) + 8 * (size_t)C::BUF + 128);
+    SpecFrame *sf = reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(mz) + mirror_bytes(d.nb));
+    const int tid = threadIdx.x;
+    if (d.gate && *d.gate == 0u) return;
+    FwdScale fs = fwd_scale(d, sc, true);
+    if (MODE == MODE_SPEC) {
+        fs.gamma2 = sc->g_lb2;
+        fs.g_ub2 = sc->g_ub2;
+    }
+    float vmax = 0.f;
+    SpecCursor cur = {0u, 0u, 0u, 0u};
+    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
+        forward_frame_alias<NF, MODE, CLS>(d, x, fs, out0, m, buf, tid, sf, nmarg, &vmax, &cur, mz);
+    if (MODE == MODE_SPEC) {
+        vmax = warp_max(vmax);
+        if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
+        if (tid == 0) {
+            spec_drop_src(d.spec, cur.src_cur, cur.src_end);
+            spec_drop_bin(d.spec, cur.bin_cur, cur.bin_end);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Inverse, one CTA per tile of B consecutive frames (B even), frames taken in
 // pairs (a, b = a + 1).  r_a + i r_b comes out of z complex inverse FFTs of
 // length NF: sub-grid s (fine bins l = z q + s) is placed at coarse bin
