@@ -149,12 +149,22 @@ sst_status build_items(sst_batch *b) {
         b->groups.push_back(std::move(g));
     }
     b->total_parts = part;
-    // forward groups
-    for (auto &kv : by_nf) {
+    // forward and inverse groups by (nf, pruning class): a channel with a
+    // half-length window and a band of class 1 or 2 runs the pruned kernels
+    auto class_of = [](const SstDev &d, const KernelTable *kt) {
+        return d.L <= d.nf / 2 + 1 ? band_class(d.nf, kt->r1, d.k_hi) : 0;
+    };
+    std::map<std::pair<int, int>, std::vector<int>> by_fwd;
+    for (int c = 0; c < nch; ++c) {
+        const SstDev &d = b->ch[c].d;
+        by_fwd[{d.nf, class_of(d, table_for_nf(d.nf))}].push_back(c);
+    }
+    for (auto &kv : by_fwd) {
         Group g;
-        g.kind = KIND_B_FWD;
-        g.nf = kv.first;
-        g.kt = table_for_nf(kv.first);
+        const int cls = kv.first.second;
+        g.kind = kind_cls(KIND_B_FWD, cls);
+        g.nf = kv.first.first;
+        g.kt = table_for_nf(g.nf);
         // interleave the channels' chunks so long channels do not end last
         std::vector<std::vector<BatchItem>> per;
         for (int c : kv.second) {
@@ -170,14 +180,15 @@ sst_status build_items(sst_batch *b) {
                 if (r < v.size()) { g.items.push_back(v[r]); any = true; }
             if (!any) break;
         }
-        g.smem = g.kt->smem_frame + tacc_bytes(g.max_nbo);
+        g.smem = g.kt->smem_frame + tacc_bytes(g.max_nbo) + (cls > 0 ? mirror_bytes(g.max_nbo) : 0);
         b->groups.push_back(std::move(g));
     }
-    // inverse groups, by (nf, window class)
+    // inverse groups, by (nf, window and pruning class)
     std::map<std::pair<int, int>, std::vector<int>> by_inv;
     for (int c = 0; c < nch; ++c) {
         const SstDev &d = b->ch[c].d;
-        by_inv[{d.nf, d.L <= d.nf / 2 + 1 ? KIND_B_INV : KIND_B_INV_WIDE}].push_back(c);
+        by_inv[{d.nf, d.L <= d.nf / 2 + 1 ? kind_cls(KIND_B_INV, class_of(d, table_for_nf(d.nf)))
+                                          : KIND_B_INV_WIDE}].push_back(c);
     }
     for (auto &kv : by_inv) {
         Group g;
@@ -271,19 +282,22 @@ sst_status enqueue_phase(sst_batch *b, cudaStream_t st, float *part, bool count,
     for (auto &g : b->groups)
         if (pred(g.kind)) gs.push_back(&g);
     if (gs.empty()) return SST_OK;
-    // fork: side streams wait for the main stream
+    // fork: side streams wait for the main stream (more groups than streams
+    // share them round-robin)
+    const size_t nstreams = std::min(gs.size(), b->side.size() + 1);
     SST_CU(cudaEventRecord(b->ev[0], st), "batch fork");
-    for (size_t i = 1; i < gs.size(); ++i) SST_CU(cudaStreamWaitEvent(b->side[i - 1], b->ev[0], 0), "batch fork");
+    for (size_t i = 1; i < nstreams; ++i) SST_CU(cudaStreamWaitEvent(b->side[i - 1], b->ev[0], 0), "batch fork");
     for (size_t i = 0; i < gs.size(); ++i) {
         Group &g = *gs[i];
-        cudaStream_t s = i == 0 ? st : b->side[i - 1];
+        const size_t k = i % nstreams;
+        cudaStream_t s = k == 0 ? st : b->side[k - 1];
         cudaError_t e = g.kt->batch(g.kind, b->d_ch, g.d_items, (int)g.items.size(), g.max_nbo, g.grid, g.smem,
                                     part + g.part_off, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
         if (count) count_launch();
     }
     // join
-    for (size_t i = 1; i < gs.size(); ++i) {
+    for (size_t i = 1; i < nstreams; ++i) {
         SST_CU(cudaEventRecord(b->ev[i], b->side[i - 1]), "batch join");
         SST_CU(cudaStreamWaitEvent(st, b->ev[i], 0), "batch join");
     }
@@ -298,9 +312,12 @@ sst_status enqueue_all(sst_batch *b, void *ws, cudaStream_t st, bool count) {
     k_gamma_batch<<<(unsigned)b->ch.size(), 256, 0, st>>>(b->d_ch, (int)b->ch.size(), part);
     SST_CU(cudaGetLastError(), "batch gamma launch");
     if (count) count_launch();
-    s = enqueue_phase(b, st, part, count, [](int k) { return k == KIND_B_FWD; });
+    s = enqueue_phase(b, st, part, count, [](int k) { return (k & ((1 << KIND_CLS_SHIFT) - 1)) == KIND_B_FWD; });
     if (s != SST_OK) return s;
-    s = enqueue_phase(b, st, part, count, [](int k) { return k == KIND_B_INV || k == KIND_B_INV_WIDE; });
+    s = enqueue_phase(b, st, part, count, [](int k) {
+        const int base = k & ((1 << KIND_CLS_SHIFT) - 1);
+        return base == KIND_B_INV || base == KIND_B_INV_WIDE;
+    });
     if (s != SST_OK) return s;
     const int grid = (int)std::min<size_t>(std::max<size_t>(b->fin.size(), 1), (size_t)b->nsm * 8);
     k_finalize_batch<<<grid, 256, 0, st>>>(b->d_ch, b->d_fin, (int)b->fin.size());

@@ -69,8 +69,14 @@ const void *kernel_of(int kind) {
             return (const void *)k_fused<NF, true, 0>;
         case KIND_FUSED_WIDE: return (const void *)k_fused<NF, false, 0>;
         case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
-        case KIND_B_FWD: return (const void *)k_forward_batch<NF>;
-        case KIND_B_INV: return (const void *)k_inverse_batch<NF, true>;
+        case KIND_B_FWD:
+            if (cls == 1) return (const void *)k_forward_batch<NF, CLS1>;
+            if (cls == 2) return (const void *)k_forward_batch<NF, CLS2>;
+            return (const void *)k_forward_batch<NF>;
+        case KIND_B_INV:
+            if (cls == 1) return (const void *)k_inverse_batch<NF, true, CLS1>;
+            if (cls == 2) return (const void *)k_inverse_batch<NF, true, CLS2>;
+            return (const void *)k_inverse_batch<NF, true>;
         case KIND_B_INV_WIDE: return (const void *)k_inverse_batch<NF, false>;
     }
     return nullptr;
@@ -161,10 +167,19 @@ cudaError_t fused(const SstDev &d, int kind, const float *x, const SstScalars *s
 
 cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nitems, int max_nbo, int grid,
                   size_t smem, float *partial, cudaStream_t st) {
-    switch (kind) {
+    const int cls = cls_of(kind);
+    switch (kind & ((1 << KIND_CLS_SHIFT) - 1)) {
         case KIND_B_ABSMAX: k_absmax_batch<NF><<<grid, C::TPF, smem, st>>>(ch, items, nitems, partial); break;
-        case KIND_B_FWD: k_forward_batch<NF><<<grid, C::TPF, smem, st>>>(ch, items, nitems, max_nbo); break;
-        case KIND_B_INV: k_inverse_batch<NF, true><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
+        case KIND_B_FWD:
+            if (cls == 1) k_forward_batch<NF, CLS1><<<grid, C::TPF, smem, st>>>(ch, items, nitems, max_nbo);
+            else if (cls == 2) k_forward_batch<NF, CLS2><<<grid, C::TPF, smem, st>>>(ch, items, nitems, max_nbo);
+            else k_forward_batch<NF><<<grid, C::TPF, smem, st>>>(ch, items, nitems, max_nbo);
+            break;
+        case KIND_B_INV:
+            if (cls == 1) k_inverse_batch<NF, true, CLS1><<<grid, C::TPF, smem, st>>>(ch, items, nitems);
+            else if (cls == 2) k_inverse_batch<NF, true, CLS2><<<grid, C::TPF, smem, st>>>(ch, items, nitems);
+            else k_inverse_batch<NF, true><<<grid, C::TPF, smem, st>>>(ch, items, nitems);
+            break;
         case KIND_B_INV_WIDE: k_inverse_batch<NF, false><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
         default: return cudaErrorInvalidValue;
     }

@@ -1273,7 +1273,20 @@ k_absmax_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ i
     }
 }
 
-template <int NF>
+// a channel the kernels of pruning class CLS may run: a half-length window
+// and a band of class 1 .. CLS (class 1's positions are a subset of class 2's)
+template <int NF, int CLS> __device__ __forceinline__ bool class_ok(const SstDev &d) {
+    if constexpr (CLS == 0) {
+        return true;
+    } else {
+        const int c = band_class(NF, FftPlan<NF>::R1, d.k_hi);
+        return d.L <= NF / 2 + 1 && c >= 1 && c <= CLS;
+    }
+}
+
+// CLS: the pruning class of every channel in the group (the band mirrors
+// then follow the accumulators, sized for max_nbo bins)
+template <int NF, int CLS = 0>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, Cfg<NF>::MINB)
 k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems, int max_nbo) {
     using C = Cfg<NF>;
@@ -1281,6 +1294,7 @@ k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
+    float2 *mz = reinterpret_cast<float2 *>(acc + 4 * tacc_stride(max_nbo));
     const int tid = threadIdx.x;
     for (int i = tid; i < 4 * tacc_stride(max_nbo); i += C::TPF) acc[i] = 0u;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -1289,14 +1303,15 @@ k_forward_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
         load_chan(sd, ch, w.chan, tid, C::TPF);
         __syncthreads();
         const BatchChan &c = ch[w.chan];
-        if (!chan_ok<NF>(sd) || sd.nbo > max_nbo || w.end > sd.F) continue;
+        if (!chan_ok<NF>(sd) || sd.nbo > max_nbo || w.end > sd.F || !class_ok<NF, CLS>(sd)) continue;
         const FwdScale fs = fwd_scale(sd, c.sc, true);
         for (int64_t m = w.begin; m < w.end; ++m)
-            forward_frame<NF, MODE_T>(sd, c.x, fs, c.T, nullptr, m, buf, acc, tid);
+            forward_frame<NF, MODE_T, CLS>(sd, c.x, fs, c.T, nullptr, m, buf, acc, tid, nullptr, nullptr, nullptr,
+                                           nullptr, mz);
     }
 }
 
-template <int NF, bool NARROW>
+template <int NF, bool NARROW, int CLS = 0>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, SST_INV_MINB)
 k_inverse_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ items, int nitems) {
     using C = Cfg<NF>;
@@ -1308,8 +1323,8 @@ k_inverse_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
         __syncthreads();   // previous tile's segment written out, sd free
         load_chan(sd, ch, w.chan, tid, C::TPF);
         __syncthreads();
-        if (!chan_ok<NF>(sd) || w.begin >= sd.ntiles) continue;
-        inverse_tile<NF, NARROW>(sd, ch[w.chan].T, ch[w.chan].ola, w.begin, smem4, tid);
+        if (!chan_ok<NF>(sd) || w.begin >= sd.ntiles || !class_ok<NF, CLS>(sd)) continue;
+        inverse_tile<NF, NARROW, CLS>(sd, ch[w.chan].T, ch[w.chan].ola, w.begin, smem4, tid);
     }
 }
 
