@@ -233,6 +233,26 @@ sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, float *V_dev
 sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
                             int32_t *dest_dev, void *workspace_dev, void *stream);
 
+/* ---- Second-order synchrosqueezing (the extension named in Sec. 6).  The
+ * IF estimate of Eq. 13 is exact for a tone but biased off the ridge of a
+ * chirp; the second-order estimate corrects it with the chirp rate, from the
+ * STFTs with windows g, g', g'', t g and t g' (Eq. 8-9 conventions, t and
+ * frequencies in samples and rad/sample):
+ *   w~ = w + i S^{g'} / S^g,  q~ = i ((S^{g'})^2 - S^{g''} S^g) / (S^{tg} S^{g'} - S^{tg'} S^g),
+ *   w2 = Re(w~ - q~ S^{tg} / S^g)   where |S^{tg} S^{g'} - S^{tg'} S^g| > 1e-3 |S^g|^2, else Re w~
+ * (exact for linear chirps).  Threshold, grid and exact sums as sst_forward;
+ * a relative threshold takes max|S^g| from a pre-pass over every frame.
+ * Three packed FFTs per frame.  Needs the built-in Gaussian window
+ * (SST_EUNSUPPORTED for a supplied one, or where the kernel's shared memory,
+ * the frame buffer plus 16 bytes per fine bin plus 48 bytes per band bin,
+ * exceeds the device's).  T from sst_forward2 inverts with sst_inverse. */
+sst_status sst_forward2(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *workspace_dev,
+                        void *stream);
+/* The map of sst_forward2: omega2_dev = the second-order IF in coarse bins
+ * (NaN where S^g = 0), dest_dev as in sst_reassign_map.  F x nb each. */
+sst_status sst_reassign_map2(sst_plan_t plan, const float *x_dev, int64_t n, float *omega2_dev,
+                             int32_t *dest_dev, void *workspace_dev, void *stream);
+
 /* max |S^g| over all frames and in-band bins (the base of a relative
  * threshold), written as one float to maxv_dev. */
 sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev,

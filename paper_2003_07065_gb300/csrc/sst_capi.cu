@@ -390,6 +390,37 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->g64 = g;
     pl->dgs64.resize(L);
     for (int i = 0; i < L; ++i) pl->dgs64[i] = dg[i] * dsc;
+    // second-order IF windows (built-in Gaussian only): g'' = (j^2 / sigma^4 -
+    // 1 / sigma^2) g, t g = j g, t g' = j g', each scaled by a power of two
+    // to the norm of g (undone exactly in the kernel)
+    std::vector<float2> win2(L), win3(L);
+    double s2 = 1.0, s3 = 1.0, s4 = 1.0;
+    const bool so_ok = params->g == nullptr;
+    if (so_ok) {
+        std::vector<double> d2g(L), tg(L), tdg(L);
+        double n2 = 0.0, n3 = 0.0, n4 = 0.0;
+        const double sg2 = p.sigma * p.sigma;
+        for (int i = 0; i < L; ++i) {
+            const double j = (double)(i - M);
+            d2g[i] = (j * j / (sg2 * sg2) - 1.0 / sg2) * g[i];
+            tg[i] = j * g[i];
+            tdg[i] = j * dg[i];
+            n2 += d2g[i] * d2g[i];
+            n3 += tg[i] * tg[i];
+            n4 += tdg[i] * tdg[i];
+        }
+        auto eq = [&](double nh) {
+            int e = nh > 0.0 ? (int)std::lround(0.5 * std::log2(ng / nh)) : 0;
+            return std::ldexp(1.0, std::max(-60, std::min(60, e)));
+        };
+        s2 = eq(n2);
+        s3 = eq(n3);
+        s4 = eq(n4);
+        for (int i = 0; i < L; ++i) {
+            win2[i] = make_float2((float)(d2g[i] * s2), (float)(tg[i] * s3));
+            win3[i] = make_float2((float)(tdg[i] * s4), 0.f);
+        }
+    }
     // Stockham twiddles, per radix-16 pass of span Ns (Ns = R1, 16 R1, ..., nf/16): rows
     // m = 1, 2, 4, 8 of exp(-2 pi i m k / (16 Ns)), k in [0, Ns), from entry 4 (Ns - R1) / 15
     int lg2 = 0;
@@ -428,7 +459,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
                  o_tw = take(sizeof(float2) * tw.size()), o_twb = take(sizeof(float2) * twb.size()),
                  o_twc = take(sizeof(float2) * twc.size()), o_twn = take(sizeof(float2) * z),
                  o_rl = take(sizeof(float) * rDl.size()),
-                 o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop);
+                 o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop),
+                 o_w2 = take(sizeof(float2) * L), o_w3 = take(sizeof(float2) * L);
     cudaError_t ce = cudaMalloc(&pl->dmem, off);
     if (ce != cudaSuccess) { delete pl; return fail(SST_ENOMEM, "cudaMalloc of %zu table bytes failed", off); }
     char *base = (char *)pl->dmem;
@@ -442,6 +474,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     memcpy(host.data() + o_rl, rDl.data(), sizeof(float) * rDl.size());
     memcpy(host.data() + o_rr, rDr.data(), sizeof(float) * rDr.size());
     memcpy(host.data() + o_rp, rDp.data(), sizeof(float) * hop);
+    memcpy(host.data() + o_w2, win2.data(), sizeof(float2) * L);
+    memcpy(host.data() + o_w3, win3.data(), sizeof(float2) * L);
     ce = cudaMemcpy(base, host.data(), off, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "table upload"); }
 
@@ -473,6 +507,12 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     d.log2_nb = lg;
     d.c_if = (float)((double)nf / (2.0 * M_PI) / dsc);
     d.dscale = (float)(1.0 / dsc);
+    d.win2 = so_ok ? (const float2 *)(base + o_w2) : nullptr;
+    d.win3 = so_ok ? (const float2 *)(base + o_w3) : nullptr;
+    d.r2 = (float)(1.0 / s2);
+    d.r3 = (float)(1.0 / s3);
+    d.r4 = (float)(1.0 / s4);
+    d.c_so = (float)((double)nf / (2.0 * M_PI));
     d.relative = (p.flags & SST_GAMMA_RELATIVE) ? 1 : 0;
     d.gamma2_abs = d.relative ? 0.f : (float)(p.gamma * p.gamma);
     pl->gamma_frac2 = (float)(p.gamma * p.gamma);
@@ -920,6 +960,51 @@ SST_API sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t
                                      plan->grid_fwd_x, plan->smem_fwd_x, st),
                    "map launch");
     return SST_OK;
+}
+
+// ------------------------------------------------------------ second-order IF
+// The forward with the second-order IF estimate (k_forward_so): the
+// threshold's pre-pass as for sst_forward on a SST_TWO_PASS plan, then one
+// launch of three packed FFTs per frame.
+static sst_status run_forward_so(sst_plan_t pl, int kind, const float *x, void *out0, void *out1, void *ws,
+                                 cudaStream_t st) {
+    if (!pl->d.win2) return fail(SST_EUNSUPPORTED, "the second-order IF needs the built-in Gaussian window");
+    const size_t smem = forward_so_smem_bytes(pl->kt->smem_frame, pl->d.nb, pl->d.nbo);
+    int dev = 0;
+    SST_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    int smax = 0;
+    SST_CU(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device attributes");
+    if (smem > (size_t)smax)
+        return fail(SST_EUNSUPPORTED, "the second-order forward needs %zu bytes of shared memory (%d available)",
+                    smem, smax);
+    SST_CU(raise_smem(pl->kt, kind, smem), "cudaFuncSetAttribute");
+    if (pl->d.relative || kind == KIND_FWD_SO_T) {
+        sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
+        if (s != SST_OK) return s;
+    }
+    int occ = 1;
+    if (pl->kt->occupancy(kind, smem, &occ) != cudaSuccess || occ < 1) occ = 1;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * pl->num_sms * 2, pl->d.F));
+    SST_LAUNCHED_K(kind == KIND_FWD_SO_T ? PK_FORWARD : PK_MAP, st,
+                   pl->kt->forward(pl->d, kind, x, ws_scalars(pl, ws), out0, out1, grid, smem, st),
+                   "second-order forward launch");
+    return SST_OK;
+}
+
+SST_API sst_status sst_forward2(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *ws,
+                                void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
+    return run_forward_so(plan, KIND_FWD_SO_T, x_dev, tfr_dev, nullptr, ws, (cudaStream_t)stream);
+}
+
+SST_API sst_status sst_reassign_map2(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
+                                     int32_t *dest_dev, void *ws, void *stream) {
+    sst_status s = check_call(plan, x_dev, n, ws);
+    if (s != SST_OK) return s;
+    if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
+    return run_forward_so(plan, KIND_FWD_SO_MAP, x_dev, omega_dev, dest_dev, ws, (cudaStream_t)stream);
 }
 
 SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev, void *ws,

@@ -48,6 +48,12 @@ struct SstDev {
     int log2_nb;        // ceil(log2(nb))
     float c_if;         // nf / (2 pi s): IF offset factor for the packed, scaled S^g'
     float dscale;       // 1 / s: the packed imaginary part carries s g' (s a power of two)
+    // second-order IF (sst_forward2): windows (s2 g'', s3 t g) and (s4 t g', 0),
+    // L entries each (null when the plan's window is not the built-in
+    // Gaussian), and the exact inverse scales 1 / s2, 1 / s3, 1 / s4
+    const float2 *win2, *win3;
+    float r2, r3, r4;
+    float c_so;         // nf / (2 pi): rad/sample -> bins
     float gamma2_abs;   // absolute threshold squared
     int relative;       // threshold from the pre-pass
     int B;              // frames per inverse tile (even)

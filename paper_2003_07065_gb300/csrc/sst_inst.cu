@@ -56,6 +56,8 @@ const void *kernel_of(int kind) {
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
         case KIND_FWD_SPEC: return forward_kernel<MODE_SPEC>(cls);
+        case KIND_FWD_SO_T: return (const void *)k_forward_so<NF, MODE_T>;
+        case KIND_FWD_SO_MAP: return (const void *)k_forward_so<NF, MODE_MAP>;
         case KIND_FWD_TA: return forward_alias_kernel<MODE_T>(cls);
         case KIND_FWD_SPECA: return forward_alias_kernel<MODE_SPEC>(cls);
         case KIND_INV:
@@ -122,6 +124,12 @@ cudaError_t forward(const SstDev &d, int kind, const float *x, const SstScalars 
             break;
         case KIND_FWD_SPEC:
             launch_forward<MODE_SPEC>(cls, d, x, sc, out0, out1, grid, smem, st);
+            break;
+        case KIND_FWD_SO_T:
+            k_forward_so<NF, MODE_T><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
+            break;
+        case KIND_FWD_SO_MAP:
+            k_forward_so<NF, MODE_MAP><<<grid, C::TPF, smem, st>>>(d, x, sc, (float2 *)out0, out1);
             break;
         case KIND_FWD_TA:
             if (!launch_forward_alias<MODE_T>(cls, d, x, sc, out0, grid, smem, st)) return cudaErrorInvalidValue;

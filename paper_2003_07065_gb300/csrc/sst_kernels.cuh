@@ -682,6 +682,124 @@ k_forward(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Second-order synchrosqueezing (the extension Sec. 6 names): the IF estimate
+// of a frame's bin corrected for the chirp rate.  From the STFTs with windows
+// g, g', g'', t g and t g' (in samples; Eq. 8-9 conventions), with w the
+// bin's frequency in rad/sample:
+//   complex IF    w~ = w + i V^{g'} / V                 (Re: Eq. 13)
+//   chirp rate    q~ = i ((V^{g'})^2 - V^{g''} V) / (V^{tg} V^{g'} - V^{tg'} V)
+//   second order  w2 = Re(w~ - q~ V^{tg} / V),  where |V^{tg} V^{g'} - V^{tg'} V| > 1e-3 |V|^2
+//                 (else the chirp rate is ill-conditioned: w2 = Re w~)
+// The five STFTs come from three packed FFTs per frame: x (g + i s1 g'),
+// x (s2 g'' + i s3 t g) and x s4 t g' (each s a power of two equalising
+// norms, undone exactly).  Reassignment, threshold and the exact sums are
+// those of the first-order forward.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cdiv_scaled(float2 a, float2 b) {
+    // a / b with both scaled by 1 / max(|b.x|, |b.y|) (no overflow of |b|^2)
+    const float m = fmaxf(fabsf(b.x), fabsf(b.y));
+    const float s = 1.0f / m;
+    const float2 bs = make_float2(b.x * s, b.y * s), as = make_float2(a.x * s, a.y * s);
+    const float den = bs.x * bs.x + bs.y * bs.y;
+    return make_float2((as.x * bs.x + as.y * bs.y) / den, (as.y * bs.x - as.x * bs.y) / den);
+}
+
+// Band bin kk of frame m from the three packed FFTs' band values (zc, zm
+// layout of scatter_band for each): MODE_MAP writes the second-order IF (bins)
+// and the destination, MODE_T adds the source to the T accumulators.
+template <int MODE>
+__device__ __forceinline__ void frame_bin_so(const SstDev &d, const FwdScale &fs, float2 *__restrict__ out0,
+                                             void *__restrict__ out1, int64_t m, int kk, const float2 *A,
+                                             const float2 *B, const float2 *C, uint32_t *acc) {
+    const int k = d.k_lo + kk, nb = d.nb;
+    float2 zk = A[kk], zn = A[nb + kk];
+    const float2 V = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+    const float2 Vd = make_float2(0.5f * (zk.y + zn.y) * d.dscale, 0.5f * (zn.x - zk.x) * d.dscale);
+    zk = B[kk];
+    zn = B[nb + kk];
+    const float2 V2 = make_float2(0.5f * (zk.x + zn.x) * d.r2, 0.5f * (zk.y - zn.y) * d.r2);
+    const float2 Vt = make_float2(0.5f * (zk.y + zn.y) * d.r3, 0.5f * (zn.x - zk.x) * d.r3);
+    zk = C[kk];
+    zn = C[nb + kk];
+    const float2 Vtd = make_float2(0.5f * (zk.x + zn.x) * d.r4, 0.5f * (zk.y - zn.y) * d.r4);
+    const float mag2 = V.x * V.x + V.y * V.y;
+    float delta = __int_as_float(0x7fc00000);
+    if (mag2 > 0.f) {
+        const float c = d.c_so;                     // Nf / (2 pi): rad/sample -> bins
+        const float2 ratio = cdiv_scaled(Vd, V);    // V^{g'} / V
+        delta = -c * ratio.y;                       // Re(i ratio) in bins: the first-order offset
+        const float2 den = csub(cmul(Vt, Vd), cmul(Vtd, V));
+        if (hypotf(den.x, den.y) > 1e-3f * mag2) {
+            const float2 num = csub(cmul(Vd, Vd), cmul(V2, V));
+            const float2 qq = cdiv_scaled(num, den);            // q~ / i
+            const float2 q = make_float2(-qq.y, qq.x);          // q~
+            const float2 corr = cmul(q, cdiv_scaled(Vt, V));    // q~ V^{tg} / V
+            delta -= c * corr.x;
+        }
+    }
+    int l = -1;
+    if (mag2 > fs.gamma2) {
+        const float f = floorf(fmaf((float)d.z, delta, 0.5f));
+        l = -2;
+        if (f > -1073741824.f && f < 1073741824.f) {
+            const int lc = d.z * (k - d.k_lo) + (int)f;
+            if (lc >= 0 && lc < d.nbo) l = lc;
+        }
+    }
+    if (MODE == MODE_MAP) {
+        const size_t o = (size_t)m * d.nb + kk;
+        reinterpret_cast<float *>(out0)[o] = (mag2 > 0.f) ? (float)k + delta : __int_as_float(0x7fc00000);
+        reinterpret_cast<int32_t *>(out1)[o] = l;
+        return;
+    }
+    if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
+}
+
+// bytes of k_forward_so's shared memory: the frame buffer (+ slack), the T
+// accumulators, and the band values of the three FFTs (2 nb float2 each)
+__host__ __device__ inline size_t forward_so_smem_bytes(size_t smem_frame, int nb, int nbo) {
+    return smem_frame + tacc_bytes(nbo) + 6 * 8 * (size_t)nb;
+}
+
+#define SST_SO_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
+
+template <int NF, int MODE>
+__global__ void __launch_bounds__(Cfg<NF>::TPF, SST_SO_MINB)
+k_forward_so(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc, float2 *__restrict__ out0,
+             void *__restrict__ out1) {
+    using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    extern __shared__ float4 smem4[];
+    float2 *buf = reinterpret_cast<float2 *>(smem4);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem4) + 2 * C::BUF + 32;
+    const int stride = tacc_stride(d.nbo);
+    float2 *band = reinterpret_cast<float2 *>(acc + 4 * stride);
+    float2 *bA = band, *bB = band + 2 * d.nb, *bC = band + 4 * d.nb;
+    const int tid = threadIdx.x;
+    const FwdScale fs = fwd_scale(d, sc, MODE == MODE_T);
+    for (int i = tid; i < 4 * stride; i += TPF) acc[i] = 0u;
+    SstDev d2 = d, d3 = d;
+    d2.win = d.win2;
+    d3.win = d.win3;
+    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x) {
+        float2 v[16];
+        forward_fft<NF, false>(buf, d, x, m * d.hop, 0, false, tid, v);     // ends with a barrier
+        scatter_band<NF>(bA, bA + d.nb, d, tid, v);
+        forward_fft<NF, false>(buf, d2, x, m * d.hop, 0, false, tid, v);
+        scatter_band<NF>(bB, bB + d.nb, d, tid, v);
+        forward_fft<NF, false>(buf, d3, x, m * d.hop, 0, false, tid, v);
+        scatter_band<NF>(bC, bC + d.nb, d, tid, v);
+        __syncthreads();
+        for (int kk = tid; kk < d.nb; kk += TPF) frame_bin_so<MODE>(d, fs, out0, out1, m, kk, bA, bB, bC, acc);
+        __syncthreads();   // the bins read and the atomics done before the read-out and the next frame
+        if (MODE == MODE_T) {
+            float2 *Trow = out0 + (size_t)trow_of(d, m) * d.nbo;
+            for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The forward of a pruning class > 0 with the T accumulators in the frame
 // buffer.  Such a forward keeps the band values in registers after the last
 // FFT pass and the mirrors outside the frame buffer, so the buffer is free

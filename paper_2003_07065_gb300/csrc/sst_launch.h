@@ -11,7 +11,9 @@ namespace sst {
 
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
        KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10,
-       KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_FWD_TA = 13, KIND_FWD_SPECA = 14, KIND_COUNT = 15 };
+       KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_FWD_TA = 13, KIND_FWD_SPECA = 14, KIND_FWD_SO_T = 15,
+       KIND_FWD_SO_MAP = 16, KIND_COUNT = 17 };
+// KIND_FWD_SO_T / KIND_FWD_SO_MAP: the second-order forward (k_forward_so).
 // KIND_FWD_TA / KIND_FWD_SPECA: the forward with its accumulators in the frame
 // buffer (k_forward_alias), pruning classes 1 and 2 only.
 

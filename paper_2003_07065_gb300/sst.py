@@ -112,6 +112,8 @@ def load():
         "sst_forward_inverse_host": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_stft": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_reassign_map": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sst_forward2": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+        "sst_reassign_map2": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sst_max_abs_v": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
         "sst_forward_static": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
         "sst_fp32_peak": ([ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
@@ -367,6 +369,14 @@ def sst_stft(plan, x, n, V, Vd, workspace, stream=None):
 def sst_reassign_map(plan, x, n, omega, dest, workspace, stream=None):
     _check(load().sst_reassign_map(plan, _ptr(x), n, _ptr(omega), _ptr(dest), _ptr(workspace),
                                    _stream(stream)))
+
+
+def sst_forward2(plan, x, n, tfr, workspace, stream=None):
+    _check(load().sst_forward2(plan, _ptr(x), n, _ptr(tfr), _ptr(workspace), _stream(stream)))
+
+
+def sst_reassign_map2(plan, x, n, omega2, dest, workspace, stream=None):
+    _check(load().sst_reassign_map2(plan, _ptr(x), n, _ptr(omega2), _ptr(dest), _ptr(workspace), _stream(stream)))
 
 
 def sst_max_abs_v(plan, x, n, maxv, workspace, stream=None):
@@ -706,6 +716,19 @@ class Plan:
         om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
         de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
         sst_reassign_map(self.handle, x, self.n, om, de, self.workspace)
+        return om, de
+
+    def forward2(self, x, tfr=None):
+        """Second-order forward (sst_forward2)."""
+        tfr = self.new_tfr() if tfr is None else tfr
+        sst_forward2(self.handle, x, self.n, tfr, self.workspace)
+        return tfr
+
+    def reassign_map2(self, x):
+        import torch
+        om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
+        de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
+        sst_reassign_map2(self.handle, x, self.n, om, de, self.workspace)
         return om, de
 
     def max_abs_v(self, x):
