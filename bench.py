@@ -1057,6 +1057,44 @@ def main():
     return 0
 
 
+def second_order_leg(args) -> dict:
+    """The second-order IF variant (sst_forward2, three packed FFTs per frame,
+    + sst_inverse) on the run-up recipe at 2^22 samples: samples/s, beside
+    the first-order forward + inverse of the same plan."""
+    import torch
+    from paper_2003_07065_gb300 import sst
+    w = W.ALL["runup_4m"]
+    x = torch.from_numpy(w.signal()[0].astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    tfr = plan.new_tfr()
+    xhat = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, fwd in (("second_order", lambda: sst.sst_forward2(plan.handle, x, w.n, tfr, plan.workspace, stream)),
+                      ("first_order", lambda: sst.sst_forward(plan.handle, x, w.n, tfr, plan.workspace, stream))):
+        def step():
+            fwd()
+            sst.sst_inverse(plan.handle, tfr, w.n, xhat, plan.workspace, stream)
+        for _ in range(args.warmup):
+            step()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        res[name] = {"ms_per_step": ms, "samples_per_s": w.n / (ms / 1e3)}
+    plan.close()
+    del tfr, flush
+    torch.cuda.empty_cache()
+    res["workload"] = w.name
+    return res
+
+
 def run_legs(args) -> dict:
     """Short runs of the other workloads for the headline line (one GPU)."""
     import types
@@ -1083,6 +1121,10 @@ def run_legs(args) -> dict:
                            "seconds": st["seconds"]}
     except Exception as e:
         out["stream64"] = {"error": repr(e)}
+    try:
+        out["runup_4m_second_order"] = second_order_leg(k)
+    except Exception as e:
+        out["runup_4m_second_order"] = {"error": repr(e)}
     try:
         b = batch_leg(k)
         out["batch256"] = {"samples_per_s": b["value"], "ms_per_step": b["ms_per_step"],
