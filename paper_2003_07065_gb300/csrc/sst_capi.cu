@@ -580,6 +580,11 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     // and four CTAs per SM instead of three, where they fit in the buffer.
     const int frame_buf = (int)((kt->smem_frame - 128) / sizeof(float2));
     const bool fwd_alias = half_window && bcls > 0 && kt->r1 == 16 && tacc_fits_frame(nbo, frame_buf);
+    // its chunks of consecutive frames (staged samples): up to 16 frames, at
+    // least about eight chunks per CTA
+    d.fwd_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, F / (8LL * pl->num_sms)));
+    const int seg_floats = fwd_seg_floats(d.fwd_chunk, hop, L);
+    const int64_t fwd_chunks = (F + d.fwd_chunk - 1) / d.fwd_chunk;
 
     // ---- one-pass relative threshold (default for relative plans)
     pl->smem_fwd_spec = pl->smem_fwd_t +
@@ -591,11 +596,11 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         pl->grid_fwd_spec = grid_for(pl->kind_fwd_spec, pl->smem_fwd_spec, F);
         if (fwd_alias) {   // (see below)
             const int ka = kind_cls(KIND_FWD_SPECA, bcls);
-            const size_t ba = forward_alias_smem_bytes(frame_buf, nb, true);
+            const size_t ba = forward_alias_smem_bytes(frame_buf, nb, true, seg_floats);
             if (ba <= smax && raise_smem(kt, ka, ba) == cudaSuccess) {
                 pl->kind_fwd_spec = ka;
                 pl->smem_fwd_spec = ba;
-                pl->grid_fwd_spec = grid_for(ka, ba, F);
+                pl->grid_fwd_spec = grid_for(ka, ba, fwd_chunks);
             }
         }
         // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
@@ -608,11 +613,11 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
 
     if (fwd_alias) {
         const int ka = kind_cls(KIND_FWD_TA, bcls);
-        const size_t ba = forward_alias_smem_bytes(frame_buf, nb, false);
+        const size_t ba = forward_alias_smem_bytes(frame_buf, nb, false, seg_floats);
         if (ba <= smax && raise_smem(kt, ka, ba) == cudaSuccess) {
             pl->kind_fwd_t = ka;
             pl->smem_fwd_t = ba;
-            pl->grid_fwd = grid_for(ka, ba, F);
+            pl->grid_fwd = grid_for(ka, ba, fwd_chunks);
         }
     }
 

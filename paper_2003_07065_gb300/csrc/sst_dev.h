@@ -85,6 +85,9 @@ struct SstDev {
     // the fused kernel's CTA b works on inverse tile tile0 + b
     int64_t frame_lo, frame_hi;
     int64_t tile0;
+    // k_forward_alias: consecutive frames per chunk, whose samples are staged
+    // in shared memory by one bulk copy (0: one frame per chunk)
+    int fwd_chunk;
 };
 #define SST_DEV_WAIT_EXPIRED 0x1u
 #define SST_DEV_COPY_LOST 0x2u

@@ -807,20 +807,61 @@ k_forward_so(SstDev d, const float *__restrict__ x, const SstScalars *__restrict
 // accumulators (cleared there each frame) take its place, which more than
 // halves the shared memory of a CTA and lets four CTAs (32 warps) share an
 // SM instead of three.  Same arithmetic as k_forward; two more barriers per
-// frame.  Shared memory: the frame buffer (BUF float2; the accumulators
-// alias its start), 128 bytes of slack (the MODE_SPEC counter), the band
-// mirrors, and the MODE_SPEC list.
+// frame.  A CTA takes chunks of d.fwd_chunk consecutive frames; the chunk's
+// samples ((chunk - 1) hop + L of them, zero outside [0, n)) are staged in
+// shared memory by one bulk copy where the range is 16-byte aligned and
+// inside the signal, else by plain loads, and every frame of the chunk
+// gathers its windowed taps from there.  Shared memory: the frame buffer
+// (BUF float2; the accumulators alias its start), 128 bytes of slack (the
+// MODE_SPEC counter), the band mirrors, the MODE_SPEC list, the chunk's
+// samples and the copy's mbarrier.
 // ---------------------------------------------------------------------------
 #define SST_FWDA_MINB ((1024 / Cfg<NF>::TPF < 1) ? 1 : ((1024 / Cfg<NF>::TPF > 8) ? 8 : 1024 / Cfg<NF>::TPF))
 
-__host__ __device__ constexpr size_t forward_alias_smem_bytes(int nf_buf, int nb, bool spec) {
-    return 8 * (size_t)nf_buf + 128 + mirror_bytes(nb) + (spec ? ((sizeof(SpecFrame) + 15) & ~(size_t)15) : 0);
+// floats of the staged samples of a chunk (rounded up so the copy's length
+// is a multiple of 16 bytes, plus that rounding's slack)
+__host__ __device__ constexpr int fwd_seg_floats(int chunk, int hop, int L) {
+    return (((chunk - 1) * hop + L + 3) & ~3) + 4;
+}
+__host__ __device__ constexpr size_t forward_alias_smem_bytes(int nf_buf, int nb, bool spec, int seg_floats) {
+    return 8 * (size_t)nf_buf + 128 + mirror_bytes(nb) + (spec ? ((sizeof(SpecFrame) + 15) & ~(size_t)15) : 0) +
+           4 * (size_t)seg_floats + 16;
 }
 // whether the accumulators of nbo fine bins fit in a frame buffer of nf_buf float2
 __host__ __device__ inline bool tacc_fits_frame(int nbo, int nf_buf) { return tacc_bytes(nbo) <= 8 * (size_t)nf_buf; }
 
+// First-pass inputs of one frame from staged samples: seg[off + j] is the
+// sample at the frame's centre + j (zero outside the signal), taps j with
+// |j| <= M, at most one per position (L <= NF).  The same products as
+// gather_first's interior path.
+template <int NF, unsigned WMASK>
+__device__ __forceinline__ void gather_staged(float2 (&u)[Cfg<NF>::PER1][Cfg<NF>::R1], const SstDev &d,
+                                              const float *seg, int off, int tid) {
+    using C = Cfg<NF>;
+    const float2 *w = d.win + d.M;
+    const float *xs = seg + off;
+#pragma unroll
+    for (int b = 0; b < C::PER1; ++b) {
+        const int j = tid + b * C::TPF;
+#pragma unroll
+        for (int r = 0; r < C::R1; ++r) {
+            if (!((WMASK >> r) & 1u)) continue;
+            const int p = j + r * (NF / C::R1);
+            const bool lo = p <= d.M, hi = p >= NF - d.M;
+            const int jj = lo ? p : p - NF;
+            float2 val = make_float2(0.f, 0.f);
+            if ((C::PER1 * C::TPF == NF / C::R1 || j < NF / C::R1) && (lo || hi)) {
+                const float2 wv = __ldg(&w[jj]);
+                const float a = xs[jj];
+                val = make_float2(a * wv.x, a * wv.y);
+            }
+            u[b][r] = val;
+        }
+    }
+}
+
 template <int NF, int MODE, int CLS>
-__device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float *__restrict__ x, const FwdScale &fs,
+__device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float *seg, int off, const FwdScale &fs,
                                                     float2 *__restrict__ out0, int64_t m, float2 *buf, int tid,
                                                     SpecFrame *sf, int *nmarg, float *vmax, SpecCursor *cur,
                                                     float2 *mz) {
@@ -828,11 +869,18 @@ __device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float
     using C = Cfg<NF>;
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
-    constexpr unsigned OMASK = band_mask<NF>(CLS);
+    constexpr unsigned OMASK = band_mask<NF>(CLS), WMASK = window_mask<NF>(CLS);
     uint32_t *acc = reinterpret_cast<uint32_t *>(buf);
     const int stride = tacc_stride(d.nbo);
     float2 v[16];
-    forward_fft<NF, false, window_mask<NF>(CLS), true>(buf, d, x, m * d.hop, 0, false, tid, v);  // ends with a barrier
+    {
+        float2 u[C::PER1][C::R1];
+        gather_staged<NF, WMASK>(u, d, seg, off, tid);
+        fft_first_from_regs<NF, TPF, false, WMASK>(buf, u, tid);
+    }
+    __syncthreads();
+    fft_middle<NF, TPF, C::R1, false>(buf, d.tw, tid);
+    fft_last_to_regs<NF, TPF, false, true>(buf, d.tw, tid, v);   // ends with a barrier
     store_mirror<NF, OMASK>(mz, d, tid, v);
     uint4 *a4 = reinterpret_cast<uint4 *>(acc);
     for (int i = tid; i < stride; i += TPF) a4[i] = make_uint4(0u, 0u, 0u, 0u);   // 4 stride words
@@ -858,7 +906,8 @@ __device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float
         }
     }
     for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
-    // the read-out done before the next frame's first pass overwrites the buffer
+    // the read-out (and this frame's reads of the staged samples) done before
+    // the next frame's first pass overwrites the buffer, or the next chunk's copy the samples
     __syncthreads();
 }
 
@@ -867,11 +916,17 @@ __global__ void __launch_bounds__(Cfg<NF>::TPF, SST_FWDA_MINB)
 k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc,
                 float2 *__restrict__ out0, void *__restrict__ out1) {
     using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
     extern __shared__ float4 smem4[];
     float2 *buf = reinterpret_cast<float2 *>(smem4);
     int *nmarg = reinterpret_cast<int *>(buf + C::BUF);
     float2 *mz = reinterpret_cast<float2 *>(reinterpret_cast<char *>(smem4) + 8 * (size_t)C::BUF + 128);
     SpecFrame *sf = reinterpret_cast<SpecFrame *>(reinterpret_cast<char *>(mz) + mirror_bytes(d.nb));
+    const int chunk = d.fwd_chunk > 0 ? d.fwd_chunk : 1;
+    const int seg_floats = fwd_seg_floats(chunk, d.hop, d.L);
+    float *seg = reinterpret_cast<float *>(reinterpret_cast<char *>(sf) +
+                                           (MODE == MODE_SPEC ? ((sizeof(SpecFrame) + 15) & ~(size_t)15) : 0));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(seg + seg_floats);
     const int tid = threadIdx.x;
     if (d.gate && *d.gate == 0u) return;
     FwdScale fs = fwd_scale(d, sc, true);
@@ -879,10 +934,53 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
         fs.gamma2 = sc->g_lb2;
         fs.g_ub2 = sc->g_ub2;
     }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     float vmax = 0.f;
     SpecCursor cur = {0u, 0u, 0u, 0u};
-    for (int64_t m = blockIdx.x; m < d.F; m += gridDim.x)
-        forward_frame_alias<NF, MODE, CLS>(d, x, fs, out0, m, buf, tid, sf, nmarg, &vmax, &cur, mz);
+    uint32_t phase = 0;
+    bool bulk = true;   // cleared for the rest of the launch should a copy's wait ever expire
+    const int64_t nchunks = (d.F + chunk - 1) / chunk;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int64_t m0 = c * chunk;
+        const int64_t m1 = m0 + chunk < d.F ? m0 + chunk : d.F;
+        const int64_t s0 = m0 * d.hop - d.M;
+        const int len = (int)((m1 - 1 - m0) * d.hop) + d.L;
+        const int len4 = (len + 3) & ~3;
+        const float *src = x + (s0 - d.xoff);
+        // staging: one bulk copy where it may run (16-byte aligned, inside the
+        // signal), with a bounded wait; else, or should the wait expire, loads
+        bool staged = false;
+        if (bulk && s0 >= 0 && s0 + len4 <= d.n && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            int ok = 1;
+            if (tid == 0) {
+                mbar_expect_tx(bar, 4u * (uint32_t)len4);
+                bulk_g2s(seg, src, 4u * (uint32_t)len4, bar);
+                ok = mbar_wait(bar, phase) ? 1 : 0;
+                if (!ok) {
+                    const bool landed = mbar_wait(bar, phase);
+                    if (d.status) atomicOr(d.status, SST_DEV_WAIT_EXPIRED | (landed ? 0u : SST_DEV_COPY_LOST));
+                }
+            }
+            phase ^= 1u;
+            staged = __syncthreads_and(ok) != 0;
+            bulk = staged;
+        }
+        if (!staged) {
+            // (a late copy would write these same values)
+            for (int i = tid; i < len; i += TPF) {
+                const int64_t sp = s0 + i;
+                seg[i] = (sp >= 0 && sp < d.n) ? __ldg(&x[sp - d.xoff]) : 0.f;
+            }
+            __syncthreads();
+        }
+        for (int64_t m = m0; m < m1; ++m)
+            forward_frame_alias<NF, MODE, CLS>(d, seg, (int)((m - m0) * d.hop) + d.M, fs, out0, m, buf, tid, sf,
+                                               nmarg, &vmax, &cur, mz);
+    }
     if (MODE == MODE_SPEC) {
         vmax = warp_max(vmax);
         if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
