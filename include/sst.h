@@ -273,19 +273,24 @@ sst_status sst_fp32_peak(double *tflops, void *stream);
 sst_status sst_threshold_stats(sst_plan_t plan, const void *workspace, int64_t *waiting, int64_t *bins,
                                int32_t *fell_back);
 
-/* Status of the last inverse (sst_inverse, sst_inverse_zone,
- * sst_forward_inverse) that used `workspace`.  The inverse stages each pair
- * of T rows in shared memory with one asynchronous bulk copy and waits for
- * it with a bounded wait (about a second).  Should a wait ever give up, the
- * tile is staged with ordinary loads instead, so the result is still
- * correct, and this call reports SST_ETIMEOUT (with the reason in
- * sst_last_error).  Synchronises `stream`; SST_OK otherwise. */
+/* Status of the last sst_forward, sst_inverse, sst_inverse_zone or
+ * sst_forward_inverse with a TFR output that used `workspace`.  The inverse
+ * stages each pair of T rows in shared memory with one asynchronous bulk
+ * copy, and the forward of pruning classes 1 and 2 each chunk of frames'
+ * samples, each waited for with a bounded wait (about a second).  Should a
+ * wait ever give up, the data are loaded with ordinary loads instead, so the
+ * result is still correct, and this call reports SST_ETIMEOUT (with the
+ * reason in sst_last_error).  Synchronises `stream`; SST_OK otherwise. */
 sst_status sst_check(sst_plan_t plan, const void *workspace, void *stream);
 /* Test hook of that path: in the next inverse of this plan one CTA does not
  * issue its first row copy, so its bounded waits run out (about two
  * seconds), it stages its tile synchronously and the next sst_check reports
  * SST_ETIMEOUT.  Nothing faults or hangs. */
 sst_status sst_test_withhold_row_copy(sst_plan_t plan);
+/* The same for the forward's staged samples: in the next sst_forward of
+ * this plan one CTA does not issue its first sample copy (plans whose
+ * forward stages its samples: pruning class 1 or 2). */
+sst_status sst_test_withhold_sample_copy(sst_plan_t plan);
 
 /* ---- One signal split by frame ranges, e.g. over several GPUs (one plan
  * per GPU, all with the same parameters).  Frames are independent (Sec. 2.1,

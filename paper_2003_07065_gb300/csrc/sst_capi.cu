@@ -720,6 +720,14 @@ static sst_status check_call(sst_plan_t plan, const void *x, int64_t n, const vo
 static SstScalars *ws_scalars(sst_plan_t, void *ws) { return (SstScalars *)ws; }
 static float *ws_partial(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_partial); }
 static float *ws_ola(sst_plan_t pl, void *ws) { return (float *)((char *)ws + pl->ws_off_ola); }
+// the call's status word (SST_DEV_*: a bounded wait of a staged copy gave
+// up), in the workspace's 256-byte header; cleared at the start of every
+// entry point that runs the forward or the inverse, read by sst_check
+static unsigned *ws_status(sst_plan_t, void *ws) { return (unsigned *)((char *)ws + 192); }
+static sst_status clear_status(sst_plan_t pl, void *ws, cudaStream_t st) {
+    SST_CU(cudaMemsetAsync(ws_status(pl, ws), 0, sizeof(unsigned), st), "status reset");
+    return SST_OK;
+}
 
 // The pre-pass of a forward call: for relative plans the max |S^g| pre-pass,
 // for absolute plans a max |x| reduction (only needed for the T scale).
@@ -783,8 +791,8 @@ static SpecBuf ws_spec(sst_plan_t pl, void *ws) {
 // path (up to the rounding of max |S^g|).  If a record buffer overflows, the
 // two-pass kernels, launched behind a device-side gate, redo the forward.
 static constexpr int kSpecStride = 16;
-static sst_status run_forward_spec(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
-    const SstDev &d = pl->d;
+static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *x, float *tfr, void *ws,
+                                   cudaStream_t st) {
     SstScalars *sc = ws_scalars(pl, ws);
     float *partial = ws_partial(pl, ws);
     const SpecBuf sb = ws_spec(pl, ws);
@@ -833,17 +841,18 @@ static sst_status run_forward_spec(sst_plan_t pl, const float *x, float *tfr, vo
 }
 
 static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *ws, cudaStream_t st) {
-    if (pl->spec) return run_forward_spec(pl, x, tfr, ws, st);
+    SstDev d = pl->d;
+    d.status = ws_status(pl, ws);
+    d.test_withhold = pl->test_withhold_fwd.exchange(0) ? 1 : 0;
+    if (pl->spec) return run_forward_spec(pl, d, x, tfr, ws, st);
     sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
     if (s != SST_OK) return s;
     SST_LAUNCHED_K(PK_FORWARD, st,
-                   pl->kt->forward(pl->d, pl->kind_fwd_t, x, ws_scalars(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
+                   pl->kt->forward(d, pl->kind_fwd_t, x, ws_scalars(pl, ws), tfr, nullptr, pl->grid_fwd, pl->smem_fwd_t, st),
                    "forward launch");
     return SST_OK;
 }
 
-// the inverse's status word (SST_DEV_*), in the workspace's 256-byte header
-static unsigned *ws_status(sst_plan_t, void *ws) { return (unsigned *)((char *)ws + 192); }
 
 static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st,
                               const int32_t *zone = nullptr, int zone_hw = 0) {
@@ -851,7 +860,6 @@ static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void
     d.zone = zone;
     d.zone_hw = zone_hw;
     d.status = ws_status(pl, ws);
-    SST_CU(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st), "status reset");
     d.test_withhold = pl->test_withhold.exchange(0) ? 1 : 0;
     SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
                    "inverse launch");
@@ -867,6 +875,8 @@ SST_API sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, f
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
+    s = clear_status(plan, ws, (cudaStream_t)stream);
+    if (s != SST_OK) return s;
     return run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
 }
 
@@ -875,6 +885,8 @@ SST_API sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n,
     sst_status s = check_call(plan, tfr_dev, n, ws);
     if (s != SST_OK) return s;
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
+    s = clear_status(plan, ws, (cudaStream_t)stream);
+    if (s != SST_OK) return s;
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
 }
 
@@ -886,6 +898,8 @@ SST_API sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64
     if (!ridge_dev) return fail(SST_EINVAL, "ridge pointer is NULL");
     if (((uintptr_t)ridge_dev) & 3) return fail(SST_EINVAL, "ridge must be 4-byte aligned");
     if (half_width < 0 || half_width > (1 << 28)) return fail(SST_EINVAL, "half_width = %d out of range", half_width);
+    s = clear_status(plan, ws, (cudaStream_t)stream);
+    if (s != SST_OK) return s;
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream, ridge_dev, half_width);
 }
 
@@ -919,6 +933,8 @@ SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int6
                         plan->smem_fused);
         return run_fused(plan, x_dev, xhat_dev, ws, (cudaStream_t)stream);
     }
+    s = clear_status(plan, ws, (cudaStream_t)stream);
+    if (s != SST_OK) return s;
     s = run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
     if (s != SST_OK) return s;
     return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
@@ -1233,8 +1249,15 @@ SST_API sst_status sst_check(sst_plan_t plan, const void *ws, void *stream) {
     unsigned w = 0;
     SST_CU(cudaMemcpy(&w, (const char *)ws + 192, sizeof w, cudaMemcpyDeviceToHost), "status read");
     if (w & SST_DEV_WAIT_EXPIRED)
-        return fail(SST_ETIMEOUT, "the inverse gave up waiting for a staged T row and staged it synchronously%s",
-                    (w & SST_DEV_COPY_LOST) ? "; the row copy had not landed after a second bounded wait" : "");
+        return fail(SST_ETIMEOUT, "a bounded wait for a staged copy (the forward's samples or the inverse's T rows) "
+                    "gave up and the data were loaded directly instead%s",
+                    (w & SST_DEV_COPY_LOST) ? "; the copy had not landed after a second bounded wait" : "");
+    return SST_OK;
+}
+
+SST_API sst_status sst_test_withhold_sample_copy(sst_plan_t plan) {
+    if (!plan) return fail(SST_EINVAL, "plan is NULL");
+    plan->test_withhold_fwd.store(1);
     return SST_OK;
 }
 

@@ -943,6 +943,7 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
     SpecCursor cur = {0u, 0u, 0u, 0u};
     uint32_t phase = 0;
     bool bulk = true;   // cleared for the rest of the launch should a copy's wait ever expire
+    bool withheld = false;  // (test hook: CTA 0 withholds only its first copy)
     const int64_t nchunks = (d.F + chunk - 1) / chunk;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int64_t m0 = c * chunk;
@@ -958,7 +959,8 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
             int ok = 1;
             if (tid == 0) {
                 mbar_expect_tx(bar, 4u * (uint32_t)len4);
-                bulk_g2s(seg, src, 4u * (uint32_t)len4, bar);
+                // (test hook: CTA 0 does not issue its first copy, so its waits expire)
+                if (!(d.test_withhold && blockIdx.x == 0 && !withheld)) bulk_g2s(seg, src, 4u * (uint32_t)len4, bar);
                 ok = mbar_wait(bar, phase) ? 1 : 0;
                 if (!ok) {
                     const bool landed = mbar_wait(bar, phase);
@@ -966,6 +968,7 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
                 }
             }
             phase ^= 1u;
+            withheld = true;
             staged = __syncthreads_and(ok) != 0;
             bulk = staged;
         }

@@ -120,6 +120,7 @@ def load():
         "sst_check": ([_vp, _vp, _vp], ctypes.c_int),
         "sst_test_static_capacity": ([ctypes.c_size_t], ctypes.c_int),
         "sst_test_withhold_row_copy": ([_vp], ctypes.c_int),
+        "sst_test_withhold_sample_copy": ([_vp], ctypes.c_int),
         "sst_threshold_stats": ([_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sst_batch_create": ([ctypes.POINTER(sst_batch_item), ctypes.c_int32, ctypes.c_uint32,
@@ -461,6 +462,10 @@ def sst_check(plan, workspace, stream=None):
 
 def sst_test_withhold_row_copy(plan):
     _check(load().sst_test_withhold_row_copy(plan))
+
+
+def sst_test_withhold_sample_copy(plan):
+    _check(load().sst_test_withhold_sample_copy(plan))
 
 
 def sst_threshold_stats(plan, workspace) -> dict:

@@ -170,6 +170,28 @@ def test_inverse_wait_expiry_reported(sst):
     plan.close()
 
 
+def test_forward_sample_copy_expiry_reported(sst):
+    """The forward of the run-up class (pruning class 1) stages each chunk's
+    samples with one bulk copy; a copy that never lands (test hook) makes
+    that CTA's waits run out, it loads the samples directly, the TFR keeps
+    its bits and sst_check reports SST_ETIMEOUT; the next call is clean."""
+    w = W.ALL["runup_256k"]
+    x = torch.from_numpy(w.signal()[0].astype(np.float32)).cuda()
+    plan = sst.Plan(**w.params())
+    ref = plan.forward(x)
+    sst.sst_check(plan.handle, plan.workspace)
+    sst.sst_test_withhold_sample_copy(plan.handle)
+    got = plan.forward(x)
+    with pytest.raises(sst.SstError) as e:
+        sst.sst_check(plan.handle, plan.workspace)
+    assert e.value.status == 5
+    assert torch.equal(ref, got)
+    again = plan.forward(x)
+    sst.sst_check(plan.handle, plan.workspace)
+    assert torch.equal(ref, again)
+    plan.close()
+
+
 def test_plan_check_matches_params_check(sst):
     w = W.ALL["runup_256k"]
     p = w.params()
