@@ -553,7 +553,9 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         return fail(SST_EUNSUPPORTED, "shared memory need (%zu / %zu B) exceeds %zu B", pl->smem_fwd_t,
                     pl->smem_inv, smax);
     }
-    struct { int kind; size_t bytes; } kinds[] = {{KIND_ABSMAX, pl->smem_absmax}, {pl->kind_fwd_t, pl->smem_fwd_t},
+    pl->absmax_cls = half_window ? bcls : 0;
+    struct { int kind; size_t bytes; } kinds[] = {{kind_cls(KIND_ABSMAX, pl->absmax_cls), pl->smem_absmax},
+        {pl->kind_fwd_t, pl->smem_fwd_t},
         {KIND_FWD_STFT, pl->smem_fwd_x}, {KIND_FWD_MAP, pl->smem_fwd_x}, {pl->inv_kind, pl->smem_inv}};
     for (auto &k : kinds) {
         ce = raise_smem(kt, k.kind, k.bytes);
@@ -570,7 +572,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->kind_fused = half_window ? kind_cls(KIND_FUSED, bcls) : KIND_FUSED_WIDE;
     pl->smem_fused = fused_smem_bytes(kt->smem_frame, nb, nbo, d.seg_len, half_window ? bcls : 0);
     pl->fused_ok = pl->smem_fused <= smax && raise_smem(kt, pl->kind_fused, pl->smem_fused) == cudaSuccess;
-    pl->grid_absmax = grid_for(KIND_ABSMAX, pl->smem_absmax, (F + 3) / 4);
+    pl->grid_absmax = grid_for(kind_cls(KIND_ABSMAX, pl->absmax_cls), pl->smem_absmax, (F + 3) / 4);
     pl->grid_fwd = grid_for(pl->kind_fwd_t, pl->smem_fwd_t, F);
     pl->grid_fwd_x = grid_for(KIND_FWD_STFT, pl->smem_fwd_x, F);
 
@@ -737,10 +739,10 @@ static sst_status run_prepass(sst_plan_t pl, const float *x, SstScalars *sc, flo
     if (pl->d.relative) {
         cudaError_t e;
         if (profile) {
-            SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(pl->d, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+            SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(pl->d, pl->absmax_cls, x, partial, pl->grid_absmax, pl->smem_absmax, st),
                            "absmax launch");
         } else {
-            e = pl->kt->absmax(pl->d, x, partial, pl->grid_absmax, pl->smem_absmax, st);
+            e = pl->kt->absmax(pl->d, pl->absmax_cls, x, partial, pl->grid_absmax, pl->smem_absmax, st);
             if (e != cudaSuccess) return cuda_fail(e, "absmax launch");
             count_launch();
         }
@@ -807,7 +809,7 @@ static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *
     }
     SstDev ds = d;
     ds.sample_stride = kSpecStride;
-    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(ds, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(ds, pl->absmax_cls, x, partial, pl->grid_absmax, pl->smem_absmax, st),
                    "sampled pre-pass launch");
     SST_LAUNCHED_K(PK_GAMMA, st,
                    (k_spec_scalars<<<1, 256, 0, st>>>(partial, pl->grid_absmax, sb.ctl, pl->gamma_frac2, d.log2_nb,
@@ -827,7 +829,7 @@ static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *
     // the two-pass path, run only if a record buffer overflowed
     SstDev dg = d;
     dg.gate = sb.ctl + 3;
-    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(dg, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(dg, pl->absmax_cls, x, partial, pl->grid_absmax, pl->smem_absmax, st),
                    "absmax launch");
     SST_LAUNCHED_K(PK_GAMMA, st,
                    (k_gamma<<<1, 256, 0, st>>>(partial, pl->grid_absmax, pl->gamma_frac2, 0, 1.f, d.log2_nb, sc,
@@ -1035,7 +1037,7 @@ SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n,
     if (!maxv_dev) return fail(SST_EINVAL, "output pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     SST_LAUNCHED_K(PK_ABSMAX, st,
-                   plan->kt->absmax(plan->d, x_dev, ws_partial(plan, ws), plan->grid_absmax, plan->smem_absmax, st),
+                   plan->kt->absmax(plan->d, plan->absmax_cls, x_dev, ws_partial(plan, ws), plan->grid_absmax, plan->smem_absmax, st),
                    "absmax launch");
     SST_LAUNCHED_K(PK_GAMMA, st,
                    (k_gamma<<<1, 256, 0, st>>>(ws_partial(plan, ws), plan->grid_absmax, plan->gamma_frac2, 0, 1.f,
@@ -1127,7 +1129,7 @@ SST_API sst_status sst_part_prepass(sst_plan_t plan, const sst_part *part, const
         d.frame_hi = std::min<int64_t>(d.F, (part->frame_end + 3) / 4 * 4);
         const int64_t quads = (d.frame_hi + 3) / 4 - d.frame_lo / 4;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(plan->grid_absmax, quads));
-        SST_LAUNCHED_K(PK_ABSMAX, st, plan->kt->absmax(d, x_dev, partial, grid, plan->smem_absmax, st),
+        SST_LAUNCHED_K(PK_ABSMAX, st, plan->kt->absmax(d, plan->absmax_cls, x_dev, partial, grid, plan->smem_absmax, st),
                        "part pre-pass launch");
         count = grid;
     } else {

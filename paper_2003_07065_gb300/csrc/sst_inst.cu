@@ -51,7 +51,10 @@ template <int MODE> const void *forward_kernel(int cls) {
 const void *kernel_of(int kind) {
     const int cls = cls_of(kind);
     switch (kind & ((1 << KIND_CLS_SHIFT) - 1)) {
-        case KIND_ABSMAX: return (const void *)k_absmax<NF>;
+        case KIND_ABSMAX:
+            if (cls == 1) return (const void *)k_absmax<NF, CLS1>;
+            if (cls == 2) return (const void *)k_absmax<NF, CLS2>;
+            return (const void *)k_absmax<NF>;
         case KIND_FWD_T: return forward_kernel<MODE_T>(cls);
         case KIND_FWD_STFT: return (const void *)k_forward<NF, MODE_STFT>;
         case KIND_FWD_MAP: return (const void *)k_forward<NF, MODE_MAP>;
@@ -96,8 +99,10 @@ cudaError_t occupancy(int kind, size_t bytes, int *blocks) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, C::TPF, bytes);
 }
 
-cudaError_t absmax(const SstDev &d, const float *x, float *partial, int grid, size_t smem, cudaStream_t st) {
-    k_absmax<NF><<<grid, C::TPF, smem, st>>>(d, x, partial);
+cudaError_t absmax(const SstDev &d, int cls, const float *x, float *partial, int grid, size_t smem, cudaStream_t st) {
+    if (cls == 1) k_absmax<NF, CLS1><<<grid, C::TPF, smem, st>>>(d, x, partial);
+    else if (cls == 2) k_absmax<NF, CLS2><<<grid, C::TPF, smem, st>>>(d, x, partial);
+    else k_absmax<NF><<<grid, C::TPF, smem, st>>>(d, x, partial);
     return cudaGetLastError();
 }
 

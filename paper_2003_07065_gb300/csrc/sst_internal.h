@@ -89,6 +89,7 @@ struct sst_plan {
     float sum_abs_g = 0.f;   // bound factor |S^g| <= max|x| sum|g| (rounded up)
     size_t smem_fwd_t = 0, smem_fwd_x = 0, smem_absmax = 0, smem_inv = 0;
     int inv_kind = sst::KIND_INV;            // with its pruning class (kind_cls)
+    int absmax_cls = 0;                      // pruning class of the max |S^g| pre-pass
     int kind_fwd_t = sst::KIND_FWD_T;
     int kind_fwd_spec = sst::KIND_FWD_SPEC;
     int grid_absmax = 0, grid_fwd = 0, grid_fwd_x = 0;

@@ -207,7 +207,11 @@ __device__ __forceinline__ void store_mirror(float2 *mz, const SstDev &d, int ti
 // such FFTs at once (four frames per CTA iteration) to hide latency.  One
 // partial max per CTA.
 // ---------------------------------------------------------------------------
-template <int NF>
+// CLS > 0 (a half-length window and a band of that pruning class): the first
+// pass leaves out the inputs the window leaves zero and the scatter the
+// positions no band bin occupies (the same values: only operations on exact
+// zeros are left out)
+template <int NF, int CLS = 0>
 __device__ __forceinline__ float absmax_quad(const SstDev &d, const float *__restrict__ x, int64_t qq, float2 *buf,
                                              int tid, float best) {
     using C = Cfg<NF>;
@@ -222,16 +226,16 @@ __device__ __forceinline__ float absmax_quad(const SstDev &d, const float *__res
         const int64_t flo = d.frame_lo, fhi = d.frame_hi ? d.frame_hi : d.F;
         const bool hasa = a >= flo && a < fhi, hasb = a + 1 >= flo && a + 1 < fhi;
         const int64_t ca = hasa ? a * d.hop : -(int64_t)4 * NF - d.n;   // absent frame: all taps outside [0, n)
-        gather_first<NF, true>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
+        gather_first<NF, true, window_mask<NF>(CLS)>(u[f], d, x, ca, (a + 1) * d.hop, hasb, tid);
     }
 #pragma unroll
-    for (int f = 0; f < NB; ++f) fft_first_from_regs<NF, TPF, false>(buf + f * BS, u[f], tid);
+    for (int f = 0; f < NB; ++f) fft_first_from_regs<NF, TPF, false, window_mask<NF>(CLS)>(buf + f * BS, u[f], tid);
     __syncthreads();
     fft_middle_multi<NF, TPF, C::R1, false, NB, BS>(buf, d.tw, tid);
     float2 v[NB][16];
     fft_last_multi<NF, TPF, false, NB, BS>(buf, d.tw, tid, v);
 #pragma unroll
-    for (int f = 0; f < NB; ++f) scatter_band<NF>(buf + f * BS, buf + f * BS + d.nb, d, tid, v[f]);
+    for (int f = 0; f < NB; ++f) scatter_band<NF, band_mask<NF>(CLS)>(buf + f * BS, buf + f * BS + d.nb, d, tid, v[f]);
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NB; ++f) {
@@ -249,7 +253,7 @@ __device__ __forceinline__ float absmax_quad(const SstDev &d, const float *__res
 
 #define SST_ABSMAX_MINB ((512 / Cfg<NF>::TPF < 1) ? 1 : 512 / Cfg<NF>::TPF)
 
-template <int NF>
+template <int NF, int CLS = 0>
 __global__ void __launch_bounds__(Cfg<NF>::TPF, SST_ABSMAX_MINB)
 k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     using C = Cfg<NF>;
@@ -263,7 +267,7 @@ k_absmax(SstDev d, const float *__restrict__ x, float *__restrict__ partial) {
     const int64_t step = d.sample_stride > 1 ? d.sample_stride : 1;
     float best = 0.f;
     for (int64_t qq = q_lo + blockIdx.x * step; qq < nquads; qq += gridDim.x * step)
-        best = absmax_quad<NF>(d, x, qq, buf, tid, best);
+        best = absmax_quad<NF, CLS>(d, x, qq, buf, tid, best);
     best = block_max<C::NWARP>(best, red, tid);
     if (tid == 0) partial[blockIdx.x] = best;
 }

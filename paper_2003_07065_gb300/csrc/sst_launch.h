@@ -33,7 +33,8 @@ struct KernelTable {
     cudaError_t (*set_smem)(int kind, size_t bytes);
     // resident CTAs per SM for a kernel kind at a dynamic shared-memory size
     cudaError_t (*occupancy)(int kind, size_t bytes, int *blocks);
-    cudaError_t (*absmax)(const SstDev &d, const float *x, float *partial, int grid, size_t smem,
+    // the max |S^g|^2 pre-pass; cls: the plan's pruning class (0 for any plan)
+    cudaError_t (*absmax)(const SstDev &d, int cls, const float *x, float *partial, int grid, size_t smem,
                           cudaStream_t st);
     cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0,
                            void *out1, int grid, size_t smem, cudaStream_t st);
