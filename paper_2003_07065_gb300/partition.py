@@ -57,21 +57,37 @@ def segments(workspace, ola_offset: int, seg_len: int, t0: int, t1: int):
 
 
 class DistComm:
-    """The two exchanges over a torch.distributed process group."""
+    """The two exchanges over a torch.distributed process group.  With NCCL
+    the device buffers are sent as they are; with a backend that moves host
+    memory only (gloo), through host copies."""
 
-    def __init__(self, dist):
+    def __init__(self, dist, group=None):
         self.dist = dist
+        self.group = group
+        self.host = dist.get_backend(group) == "gloo"
+
+    def _stage(self, t):
+        return t.cpu() if (self.host and t.is_cuda) else t
 
     def allreduce_max(self, t):
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        h = self._stage(t)
+        self.dist.all_reduce(h, op=self.dist.ReduceOp.MAX, group=self.group)
+        if h is not t:
+            t.copy_(h)
 
     def exchange(self, sends, recvs):
         """sends / recvs: (peer rank, tensor) pairs; all posted, then awaited."""
-        ops = [self.dist.P2POp(self.dist.isend, t, peer) for peer, t in sends]
-        ops += [self.dist.P2POp(self.dist.irecv, t, peer) for peer, t in recvs]
+        hs = [(peer, self._stage(t)) for peer, t in sends]
+        hr = [(peer, self._stage(t) if not self.host else t.new_empty(t.shape, device="cpu"), t)
+              for peer, t in recvs]
+        ops = [self.dist.P2POp(self.dist.isend, h, peer, group=self.group) for peer, h in hs]
+        ops += [self.dist.P2POp(self.dist.irecv, h, peer, group=self.group) for peer, h, _ in hr]
         if ops:
             for req in self.dist.batch_isend_irecv(ops):
                 req.wait()
+        for _, h, t in hr:
+            if h is not t:
+                t.copy_(h)
 
 
 def run(plan, x_part, rank: int, parts: int, comm, lays=None):
