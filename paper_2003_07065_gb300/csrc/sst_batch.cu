@@ -201,8 +201,7 @@ sst_status build_items(sst_batch *b) {
             std::vector<BatchItem> v;
             for (int64_t t = 0; t < d.ntiles; ++t) v.push_back({c, 0, t, t + 1});
             per.push_back(std::move(v));
-            const size_t nq = (size_t)(d.k_hi - d.k_lo + 1);
-            g.smem = std::max(g.smem, g.kt->smem_frame + 16 * (size_t)d.z * nq + 4 * (size_t)d.seg_len);
+            g.smem = std::max(g.smem, inverse_smem_bytes(g.kt->smem_frame, d.z, d.k_hi - d.k_lo + 1, d.seg_len));
         }
         for (size_t r = 0;; ++r) {
             bool any = false;

@@ -537,7 +537,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     pl->smem_fwd_t = kt->smem_frame + tacc_bytes(nbo);
     pl->smem_absmax = kt->smem_frame + sizeof(float2) * (kt->smem_frame - 128) / sizeof(float2);  // two frame buffers
     // inverse: frame buffer, the pair's two T rows regrouped by sub-grid, overlap-add segment
-    pl->smem_inv = kt->smem_frame + 2 * sizeof(float2) * (size_t)z * nb + sizeof(float) * (size_t)d.seg_len;
+    pl->smem_inv = inverse_smem_bytes(kt->smem_frame, z, nb, d.seg_len);
     // pruned kernels where the band (and, for the forward, the window) leaves
     // part of the radix-16 first pass empty
     const int bcls = band_class(nf, kt->r1, (int)k_hi);

@@ -497,17 +497,21 @@ __device__ __forceinline__ float tacc_value(uint32_t lo, uint32_t hi, const FwdS
     return (fmaf((float)h, 2097152.f, (float)r) * fs.r1) * fs.r2;
 }
 
-// Reads fine bins 4 q .. 4 q + 3 (those below nbo) into Trow and clears them.
+// Reads fine bins 4 q .. 4 q + 3 (those below nbo) into Trow and (CLEAR)
+// clears them.
+template <bool CLEAR = true>
 __device__ __forceinline__ void tacc_take4(uint32_t *__restrict__ acc, int stride, int q, int nbo,
                                            float2 *__restrict__ Trow, const FwdScale &fs) {
     uint4 *a4 = reinterpret_cast<uint4 *>(acc);
     const int s4 = stride >> 2;
     const uint4 rl = a4[q], rh = a4[s4 + q], il = a4[2 * s4 + q], ih = a4[3 * s4 + q];
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    a4[q] = z;
-    a4[s4 + q] = z;
-    a4[2 * s4 + q] = z;
-    a4[3 * s4 + q] = z;
+    if (CLEAR) {
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        a4[q] = z;
+        a4[s4 + q] = z;
+        a4[2 * s4 + q] = z;
+        a4[3 * s4 + q] = z;
+    }
     const float2 t0 = make_float2(tacc_value(rl.x, rh.x, fs), tacc_value(il.x, ih.x, fs));
     const float2 t1 = make_float2(tacc_value(rl.y, rh.y, fs), tacc_value(il.y, ih.y, fs));
     const float2 t2 = make_float2(tacc_value(rl.z, rh.z, fs), tacc_value(il.z, ih.z, fs));
@@ -909,7 +913,9 @@ __device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float
             __syncthreads();
         }
     }
-    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4(acc, stride, q, d.nbo, Trow, fs);
+    // (the accumulators live in the frame buffer, which the next frame's FFT
+    // overwrites and which is cleared again after it: no clearing here)
+    for (int q = tid; 4 * q < d.nbo; q += TPF) tacc_take4<false>(acc, stride, q, d.nbo, Trow, fs);
     // the read-out (and this frame's reads of the staged samples) done before
     // the next frame's first pass overwrites the buffer, or the next chunk's copy the samples
     __syncthreads();
@@ -1005,10 +1011,12 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
 // k_lo + q together with the Hermitian image of sub-grid (z - s) mod z, and
 // the result at tap j is multiplied by exp(i 2 pi s j / (z NF)) (Eq. 25, with
 // the zNf-point zero-padded inverse of Sec. 2.5 split into its z interleaved
-// sub-grids).  The pair's two T rows are staged in shared memory by
-// sub-grid; the spectrum build is fused into the first FFT pass and the tap
-// accumulation into the last, whose thread j holds the outputs
-// q = j + r NF/16.  NARROW (L <= NF/2 + 1) keeps the 9 accumulators of
+// sub-grids).  The sub-grids are taken in descending order and their
+// results summed by Horner's rule in omega = exp(i 2 pi j / (z NF)), one
+// complex multiply-add per tap and sub-grid.  The pair's two T rows are
+// staged in shared memory; the spectrum build is fused into the first FFT
+// pass and the tap accumulation into the last, whose thread j holds the
+// outputs q = j + r NF/16.  NARROW (L <= NF/2 + 1) keeps the 9 accumulators of
 // r in [0, 4] and [12, 15]; otherwise all 16 plus the tap -NF/2 (which shares
 // q = NF/2 with +NF/2).  The windowed frames are overlap-added into a
 // shared-memory segment in ascending frame order, written to the partial
@@ -1020,6 +1028,126 @@ template <bool NARROW> struct InvTaps {
     // r of accumulator i (i = 16 is the extra tap -NF/2 at r = 8)
     __host__ __device__ static constexpr int r_of(int i) { return NARROW ? (i <= 4 ? i : i + 7) : (i < 16 ? i : 8); }
 };
+
+// The last-pass taps of thread tid: n_i = q or q - NF (q = tid + r NF/16),
+// INT_MIN where outside the window, and omega_i = exp(2 pi i n_i / (z NF)),
+// the sub-grid twiddle of sub-grid 1, whose powers give the others.
+template <int NF, bool NARROW>
+__device__ __forceinline__ void inverse_taps(const SstDev &d, int tid, int (&tap)[InvTaps<NARROW>::NACC],
+                                             float2 (&om)[InvTaps<NARROW>::NACC]) {
+    using TP = InvTaps<NARROW>;
+    constexpr int NS = NF / 16;
+    const bool live = (Cfg<NF>::TPF == NS) || tid < NS;
+    const float2 b1 = (d.z > 1 && live) ? __ldg(&d.twb[NS + tid]) : make_float2(1.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < TP::NACC; ++i) {
+        const int r = TP::r_of(i);
+        const int q = tid + r * NS;
+        int n;
+        if (i == 16) n = -NF / 2;
+        else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
+        const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
+        tap[i] = ok ? n : INT_MIN;
+        om[i] = make_float2(1.f, 0.f);
+        if (ok && d.z > 1) om[i] = (i == 16) ? __ldg(&d.twn[1]) : cmul(b1, __ldg(&d.twc[(2 + (n < 0)) * 16 + r]));
+    }
+}
+
+// First FFT pass of sub-grid s of a pair of rows (a, b), with the spectrum
+// built in registers: Y_s[k] = X_a,s[k] + conj X_a,sb[-k-dl]
+// + i (X_b,s[k] + conj X_b,sb[-k-dl]), sb = (z - s) mod z, dl = (s > 0).
+// Element q of sub-grid s of row a is Ta[q qstride] (Tam for sub-grid sb;
+// Tb, Tbm for row b).  Input k = j + r NF/R1 reads q = k - k_lo and, for the
+// image, qm = ((NF - k - dl) mod NF) - k_lo = (NF - dl - j - k_lo) - r NF/R1,
+// except at k = 0 with dl = 0 (qm = -k_lo).  The coarse DC and Nyquist bins
+// (k = 0 and NF/2 of sub-grid 0, i.e. j = 0 with r = 0 or R1/2) are their own
+// images: both terms land on the same input, which takes the weight 1/2.
+// The band is a small part of the spectrum, so most r hold nothing for a
+// whole warp: those iterations are skipped on a warp vote.  No barrier inside.
+template <int NF, int CLS>
+__device__ __forceinline__ void inverse_first_pass(const SstDev &d, const float2 *Ta, const float2 *Tam,
+                                                   const float2 *Tb, const float2 *Tbm, int qstride, int s,
+                                                   float2 *buf, int tid) {
+    using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    constexpr int STEP = NF / C::R1;
+    const int nq = d.k_hi - d.k_lo + 1;
+    const int sb = (s == 0) ? 0 : d.z - s;
+    const int dl = (s == 0) ? 0 : 1;
+    const int nqs = (s == 0) ? nq : nq - 1;     // sub-grid s holds q in [0, nqs)
+    const int nqb = (sb == 0) ? nq : nq - 1;
+    float2 u[C::PER1][C::R1];
+#pragma unroll
+    for (int bb = 0; bb < C::PER1; ++bb) {
+        const int j = tid + bb * TPF;
+        const bool jok = C::PER1 * TPF == NF / C::R1 || j < NF / C::R1;
+        const int q0 = j - d.k_lo;
+        const int qm0 = NF - dl - j - d.k_lo;
+#pragma unroll
+        for (int r = 0; r < C::R1; ++r) {
+            if (!((band_mask<NF>(CLS) >> r) & 1u)) continue;
+            float2 y = make_float2(0.f, 0.f);
+            const int q = q0 + r * STEP;
+            const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
+            const bool hd = jok && (unsigned)q < (unsigned)nqs;
+            const bool hm = jok && (unsigned)qm < (unsigned)nqb;
+            if (__any_sync(0xffffffffu, hd || hm)) {
+                if (hd) {
+                    const float2 xa = Ta[q * qstride], xb = Tb[q * qstride];
+                    y.x += xa.x - xb.y;
+                    y.y += xa.y + xb.x;
+                }
+                if (hm) {
+                    const float2 xa = Tam[qm * qstride], xb = Tbm[qm * qstride];
+                    // conj(xa) + i conj(xb)
+                    y.x += xa.x + xb.y;
+                    y.y += -xa.y + xb.x;
+                }
+                if ((r == 0 || r == C::R1 / 2) && s == 0 && j == 0) y = cscale(y, 0.5f);
+            }
+            u[bb][r] = y;
+        }
+    }
+    fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
+}
+
+// shared memory of the inverse: frame buffer, the pair's rows by sub-grid, overlap-add segment
+__host__ __device__ inline size_t inverse_smem_bytes(size_t smem_frame, int z, int nq, int seg_len) {
+    return smem_frame + 16 * (size_t)z * (size_t)nq + 4 * (size_t)seg_len;
+}
+
+// Overlap-add of one frame's taps (the real part: frame a of the pair; the
+// imaginary part: frame b) into the segment at offset o, each weighted by
+// g[n_i] / NF (the inverse DFT's 1 / NF, a power of two, so exact, applied
+// once per tap instead of to every spectrum input).
+template <int NF, bool NARROW, bool IMAG>
+__device__ __forceinline__ void inverse_ola(const SstDev &d, float *seg, int o,
+                                            const int (&tap)[InvTaps<NARROW>::NACC],
+                                            const float2 (&racc)[InvTaps<NARROW>::NACC]) {
+    const float cnorm = 1.0f / (float)NF;
+#pragma unroll
+    for (int i = 0; i < InvTaps<NARROW>::NACC; ++i)
+        if (tap[i] != INT_MIN) seg[o + tap[i]] += (__ldg(&d.g[tap[i] + d.M]) * cnorm) * (IMAG ? racc[i].y : racc[i].x);
+}
+
+// Tap accumulation of sub-grid s, taken in descending order (Horner's rule
+// in omega): racc = sum_s omega^s v_s, i.e. every tap gets the sub-grid
+// twiddle exp(i 2 pi s n / (z NF)) of Eq. 25's zNf-point inverse.
+template <bool NARROW>
+__device__ __forceinline__ void inverse_accumulate(float2 (&racc)[InvTaps<NARROW>::NACC], const float2 (&v)[16],
+                                                   const float2 (&om)[InvTaps<NARROW>::NACC], bool first) {
+    using TP = InvTaps<NARROW>;
+#pragma unroll
+    for (int i = 0; i < TP::NACC; ++i) {
+        const float2 x = v[TP::r_of(i)];
+        if (first) {
+            racc[i] = x;
+        } else {
+            const float2 a = racc[i], w = om[i];
+            racc[i] = make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, x.x)), fmaf(a.x, w.y, fmaf(a.y, w.x, x.y)));
+        }
+    }
+}
 
 // One inverse tile; smem4 is the kernel's dynamic shared memory.  Ends with a
 // barrier-free write of the tile's segment (callers looping over tiles sync
@@ -1033,9 +1161,8 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
     float2 *buf = reinterpret_cast<float2 *>(smem4);
-    // staged rows.  Synchronous staging: Tst[f][s][q] = w T_f[z q + s], q in
-    // [0, nq), nq = N_r + 1 (regrouped by sub-grid, DC / Nyquist weight
-    // applied).  Asynchronous staging (rows of the tile contiguous and 16-byte
+    // staged rows.  Synchronous staging: Tst[f][s][q] = T_f[z q + s], q in
+    // [0, nq), nq = N_r + 1 (regrouped by sub-grid).  Asynchronous staging (rows of the tile contiguous and 16-byte
     // aligned): the pair's two rows as they are in T, raw[f nbo + l], one bulk
     // copy per pair, the next pair's copy issued as soon as the current pair's
     // last spectrum is built, so it lands while that sub-grid's FFT runs.
@@ -1045,28 +1172,14 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     // (the frame buffer's 128 bytes of slack are at the end of the allocation)
     uint64_t *rbar = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(seg + d.seg_len) + 15) & ~(uintptr_t)15);
     const int64_t m0 = tile * d.B;
-    const float cnorm = 1.0f / (float)NF;
     const bool live = (TPF == NS) || tid < NS;
     const uint32_t pair_bytes = 16u * (uint32_t)d.nbo;
     const float2 *tile_rows = T + (size_t)m0 * d.nbo;
     bool async = d.trow_cap == 0 && m0 + d.B <= d.F && (reinterpret_cast<uintptr_t>(tile_rows) & 15) == 0;
 
-    // per-thread taps of the last pass: n_i = q or q - NF, window g[n_i + M]
     int tap[TP::NACC];
-    float gw[TP::NACC];
-#pragma unroll
-    for (int i = 0; i < TP::NACC; ++i) {
-        const int r = TP::r_of(i);
-        const int q = tid + r * NS;
-        int n;
-        if (i == 16) n = -NF / 2;
-        else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
-        const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
-        tap[i] = ok ? n : INT_MIN;
-        // the inverse DFT's 1 / NF (a power of two, so exact) is applied here,
-        // once per tap, instead of to every spectrum input
-        gw[i] = ok ? __ldg(&d.g[n + d.M]) * cnorm : 0.f;
-    }
+    float2 om[TP::NACC];
+    inverse_taps<NF, NARROW>(d, tid, tap, om);
 
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
     if (async && tid == 0) {
@@ -1097,9 +1210,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             ok = __syncthreads_and(ok);
             if (!ok) async = false;
         }
-        // synchronous staging: both rows (contiguous in T), regrouped by
-        // sub-grid, with the 1/2 weight of the DC and Nyquist destinations
-        // (Hermitian completion)
+        // synchronous staging: both rows (contiguous in T), regrouped by sub-grid
         // zone centres of the pair (component recovery only)
         const int za = d.zone ? d.zone[a] : 0;
         const int zb = d.zone ? (hasb ? d.zone[b] : -1) : 0;
@@ -1107,14 +1218,10 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             const float2 *src = T + (size_t)trow_of(d, a + f) * d.nbo;
             const bool have = f == 0 || hasb;
             for (int q = tid; q < nq; q += TPF) {
-                const int k = d.k_lo + q;
-                const float w0 = (k == 0 || 2 * k == NF) ? 0.5f : 1.f;
                 for (int s = 0; s < d.z; ++s) {
                     const int l = d.z * q + s;
                     const bool keep = !d.zone || in_zone(l, f ? zb : za, d.zone_hw);
-                    float2 t = (have && l < d.nbo && keep) ? __ldg(&src[l]) : make_float2(0.f, 0.f);
-                    if (s == 0) t = cscale(t, w0);
-                    Tst[(f * d.z + s) * nq + q] = t;
+                    Tst[(f * d.z + s) * nq + q] = (have && l < d.nbo && keep) ? __ldg(&src[l]) : make_float2(0.f, 0.f);
                 }
             }
         }
@@ -1128,107 +1235,31 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
         }
 
         float2 racc[TP::NACC];
-#pragma unroll
-        for (int i = 0; i < TP::NACC; ++i) racc[i] = make_float2(0.f, 0.f);
-
-        for (int s = 0; s < d.z; ++s) {
+        // sub-grids in descending order, for the Horner accumulation
+        for (int s = d.z - 1; s >= 0; --s) {
             const int sb = (s == 0) ? 0 : d.z - s;
-            const int dl = (s == 0) ? 0 : 1;
-            const int nqs = (s == 0) ? nq : nq - 1;     // sub-grid s holds q in [0, nqs)
-            const int nqb = (sb == 0) ? nq : nq - 1;
             // element q of sub-grid s of row f: staged Tst[(f z + s) nq + q], raw Tst[f nbo + z q + s]
             const int qstride = async ? d.z : 1;
             const float2 *Ta = Tst + (async ? s : s * nq), *Tam = Tst + (async ? sb : sb * nq);
             const float2 *Tb = Tst + (async ? d.nbo + s : (d.z + s) * nq);
             const float2 *Tbm = Tst + (async ? d.nbo + sb : (d.z + sb) * nq);
-            // first pass with the spectrum built in registers (the 1/NF is in gw):
-            // Y_s[k] = X_a,s[k] + conj X_a,sb[-k-dl] + i (X_b,s[k] + conj X_b,sb[-k-dl])
-            // Input k = j + r NF/R1 reads q = k - k_lo and, for the image,
-            // qm = ((NF - k - dl) mod NF) - k_lo = (NF - dl - j - k_lo) - r NF/R1,
-            // except at k = 0 with dl = 0 (qm = -k_lo).  The band is a small part
-            // of the spectrum, so most r hold nothing for a whole warp: those
-            // iterations are skipped on a warp vote.
-            constexpr int STEP = NF / C::R1;
-            float2 u[C::PER1][C::R1];
-#pragma unroll
-            for (int bb = 0; bb < C::PER1; ++bb) {
-                const int j = tid + bb * TPF;
-                const bool jok = C::PER1 * TPF == NF / C::R1 || j < NF / C::R1;
-                const int q0 = j - d.k_lo;
-                const int qm0 = NF - dl - j - d.k_lo;
-#pragma unroll
-                for (int r = 0; r < C::R1; ++r) {
-                    if (!((band_mask<NF>(CLS) >> r) & 1u)) continue;
-                    float2 y = make_float2(0.f, 0.f);
-                    const int q = q0 + r * STEP;
-                    const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
-                    const bool hd = jok && (unsigned)q < (unsigned)nqs;
-                    const bool hm = jok && (unsigned)qm < (unsigned)nqb;
-                    if (__any_sync(0xffffffffu, hd || hm)) {
-                        if (hd) {
-                            float2 xa = Ta[q * qstride], xb = Tb[q * qstride];
-                            if (async && s == 0 && (d.k_lo + q == 0 || 2 * (d.k_lo + q) == NF)) {
-                                xa = cscale(xa, 0.5f);
-                                xb = cscale(xb, 0.5f);
-                            }
-                            y.x += xa.x - xb.y;
-                            y.y += xa.y + xb.x;
-                        }
-                        if (hm) {
-                            float2 xa = Tam[qm * qstride], xb = Tbm[qm * qstride];
-                            if (async && sb == 0 && (d.k_lo + qm == 0 || 2 * (d.k_lo + qm) == NF)) {
-                                xa = cscale(xa, 0.5f);
-                                xb = cscale(xb, 0.5f);
-                            }
-                            // conj(xa) + i conj(xb)
-                            y.x += xa.x + xb.y;
-                            y.y += -xa.y + xb.x;
-                        }
-                    }
-                    u[bb][r] = y;
-                }
-            }
-            fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
+            inverse_first_pass<NF, CLS>(d, Ta, Tam, Tb, Tbm, qstride, s, buf, tid);
             __syncthreads();
             // the pair's rows are read for the last time above: fetch the next pair's
-            if (async && s == d.z - 1 && tid == 0 && 2 * (pr + 1) < d.B) {
+            if (async && s == 0 && tid == 0 && 2 * (pr + 1) < d.B) {
                 mbar_expect_tx(rbar, pair_bytes);
                 bulk_g2s(Tst, tile_rows + (size_t)2 * (pr + 1) * d.nbo, pair_bytes, rbar);
             }
             fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
             float2 v[16];
             fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
-            // accumulate the taps, with the sub-grid twiddle exp(i 2 pi s n / (z NF))
-            if (live) {
-                if (s == 0) {
-#pragma unroll
-                    for (int i = 0; i < TP::NACC; ++i) racc[i] = cadd(racc[i], v[TP::r_of(i)]);
-                } else {
-                    // exp(i 2 pi s n / (z NF)) = base_s(j) * c_s(r, wrapped) for n = j + r NF/16 (- NF)
-                    const float2 bs = __ldg(&d.twb[s * NS + tid]);
-#pragma unroll
-                    for (int i = 0; i < TP::NACC; ++i) {
-                        if (tap[i] != INT_MIN) {
-                            const float2 w = (i == 16) ? __ldg(&d.twn[s])
-                                                       : cmul(bs, __ldg(&d.twc[(2 * s + (tap[i] < 0)) * 16 + TP::r_of(i)]));
-                            racc[i] = cadd(racc[i], cmul(v[TP::r_of(i)], w));
-                        }
-                    }
-                }
-            }
+            if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
         }
         // overlap-add a, then b (ascending frame order at every sample)
         const int oa = (int)(a - m0) * d.hop + d.M;
-#pragma unroll
-        for (int i = 0; i < TP::NACC; ++i)
-            if (tap[i] != INT_MIN) seg[oa + tap[i]] += gw[i] * racc[i].x;
+        inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
         __syncthreads();
-        if (hasb) {
-            const int ob = oa + d.hop;
-#pragma unroll
-            for (int i = 0; i < TP::NACC; ++i)
-                if (tap[i] != INT_MIN) seg[ob + tap[i]] += gw[i] * racc[i].y;
-        }
+        if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
         __syncthreads();
     }
     float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
@@ -1278,83 +1309,21 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
 template <int NF, bool NARROW, int CLS>
 __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 *__restrict__ rowA,
                                                   const float2 *__restrict__ rowB, float2 *buf, int tid,
-                                                  const int (&tap)[InvTaps<NARROW>::NACC],
+                                                  const float2 (&om)[InvTaps<NARROW>::NACC],
                                                   float2 (&racc)[InvTaps<NARROW>::NACC]) {
     using C = Cfg<NF>;
-    using TP = InvTaps<NARROW>;
     constexpr int TPF = C::TPF;
     constexpr int NS = NF / 16;
-    const int nq = d.k_hi - d.k_lo + 1;
     const bool live = (TPF == NS) || tid < NS;
-#pragma unroll
-    for (int i = 0; i < TP::NACC; ++i) racc[i] = make_float2(0.f, 0.f);
-    for (int s = 0; s < d.z; ++s) {
+    for (int s = d.z - 1; s >= 0; --s) {
         const int sb = (s == 0) ? 0 : d.z - s;
-        const int dl = (s == 0) ? 0 : 1;
-        const int nqs = (s == 0) ? nq : nq - 1;
-        const int nqb = (sb == 0) ? nq : nq - 1;
         // element q of sub-grid s of a row: row[z q + s]
-        const float2 *Ta = rowA + s, *Tam = rowA + sb, *Tb = rowB + s, *Tbm = rowB + sb;
-        constexpr int STEP = NF / C::R1;
-        float2 u[C::PER1][C::R1];
-#pragma unroll
-        for (int bb = 0; bb < C::PER1; ++bb) {
-            const int j = tid + bb * TPF;
-            const bool jok = C::PER1 * TPF == NF / C::R1 || j < NF / C::R1;
-            const int q0 = j - d.k_lo;
-            const int qm0 = NF - dl - j - d.k_lo;
-#pragma unroll
-            for (int r = 0; r < C::R1; ++r) {
-                if (!((band_mask<NF>(CLS) >> r) & 1u)) continue;
-                float2 y = make_float2(0.f, 0.f);
-                const int q = q0 + r * STEP;
-                const int qm = (r == 0 && j == 0 && dl == 0) ? -d.k_lo : qm0 - r * STEP;
-                const bool hd = jok && (unsigned)q < (unsigned)nqs;
-                const bool hm = jok && (unsigned)qm < (unsigned)nqb;
-                if (__any_sync(0xffffffffu, hd || hm)) {
-                    if (hd) {
-                        float2 xa = Ta[q * d.z], xb = Tb[q * d.z];
-                        if (s == 0 && (d.k_lo + q == 0 || 2 * (d.k_lo + q) == NF)) {
-                            xa = cscale(xa, 0.5f);
-                            xb = cscale(xb, 0.5f);
-                        }
-                        y.x += xa.x - xb.y;
-                        y.y += xa.y + xb.x;
-                    }
-                    if (hm) {
-                        float2 xa = Tam[qm * d.z], xb = Tbm[qm * d.z];
-                        if (sb == 0 && (d.k_lo + qm == 0 || 2 * (d.k_lo + qm) == NF)) {
-                            xa = cscale(xa, 0.5f);
-                            xb = cscale(xb, 0.5f);
-                        }
-                        y.x += xa.x + xb.y;
-                        y.y += -xa.y + xb.x;
-                    }
-                }
-                u[bb][r] = y;
-            }
-        }
-        fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
+        inverse_first_pass<NF, CLS>(d, rowA + s, rowA + sb, rowB + s, rowB + sb, d.z, s, buf, tid);
         __syncthreads();
         fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
         float2 v[16];
         fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
-        if (live) {
-            if (s == 0) {
-#pragma unroll
-                for (int i = 0; i < TP::NACC; ++i) racc[i] = cadd(racc[i], v[TP::r_of(i)]);
-            } else {
-                const float2 bs = __ldg(&d.twb[s * NS + tid]);
-#pragma unroll
-                for (int i = 0; i < TP::NACC; ++i) {
-                    if (tap[i] != INT_MIN) {
-                        const float2 w = (i == 16) ? __ldg(&d.twn[s])
-                                                   : cmul(bs, __ldg(&d.twc[(2 * s + (tap[i] < 0)) * 16 + TP::r_of(i)]));
-                        racc[i] = cadd(racc[i], cmul(v[TP::r_of(i)], w));
-                    }
-                }
-            }
-        }
+        if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
     }
 }
 
@@ -1388,8 +1357,6 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     const FwdScale fs = fwd_scale(d, sc, true);
     const int64_t tile = d.tile0 + blockIdx.x;
     const int64_t m0 = tile * d.B;
-    const float cnorm = 1.0f / (float)NF;
-    const bool live = (TPF == NS) || tid < NS;
 
     for (int i = tid; i < 4 * stride; i += TPF) acc[i] = 0u;
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
@@ -1416,32 +1383,15 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         __syncthreads();
 
         int tap[TP::NACC];
-        float gw[TP::NACC];
-#pragma unroll
-        for (int i = 0; i < TP::NACC; ++i) {
-            const int r = TP::r_of(i);
-            const int q = tid + r * NS;
-            int n;
-            if (i == 16) n = -NF / 2;
-            else n = (r < 8 || (r == 8 && tid == 0)) ? q : q - NF;
-            const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
-            tap[i] = ok ? n : INT_MIN;
-            gw[i] = ok ? __ldg(&d.g[n + d.M]) * cnorm : 0.f;
-        }
+        float2 om[TP::NACC];
+        inverse_taps<NF, NARROW>(d, tid, tap, om);
         float2 racc[TP::NACC];
-        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, tap, racc);
+        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, om, racc);
         // overlap-add a, then b (ascending frame order at every sample)
         const int oa = (int)(a - m0) * d.hop + d.M;
-#pragma unroll
-        for (int i = 0; i < TP::NACC; ++i)
-            if (tap[i] != INT_MIN) seg[oa + tap[i]] += gw[i] * racc[i].x;
+        inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
         __syncthreads();
-        if (hasb) {
-            const int ob = oa + d.hop;
-#pragma unroll
-            for (int i = 0; i < TP::NACC; ++i)
-                if (tap[i] != INT_MIN) seg[ob + tap[i]] += gw[i] * racc[i].y;
-        }
+        if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
         // the accumulators' first half held row b: clear it for the next pair
         // (ordered before its atomics by the barriers inside the next forward)
         for (int i = tid; i < 2 * stride; i += TPF) acc[i] = 0u;

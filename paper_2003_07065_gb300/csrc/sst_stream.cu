@@ -266,7 +266,7 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
     }
     // kernel attributes for this stream's shapes
     const size_t smem_f = plan->kt->smem_frame + tacc_bytes(d.nbo);
-    const size_t smem_i = plan->kt->smem_frame + 16 * (size_t)d.z * (size_t)(d.k_hi - d.k_lo + 1) + 4 * (size_t)d.seg_len;
+    const size_t smem_i = inverse_smem_bytes(plan->kt->smem_frame, d.z, d.k_hi - d.k_lo + 1, d.seg_len);
     const int ik = d.L <= d.nf / 2 + 1 ? KIND_B_INV : KIND_B_INV_WIDE;
     if (raise_smem(plan->kt, KIND_B_FWD, smem_f) != cudaSuccess || raise_smem(plan->kt, ik, smem_i) != cudaSuccess) {
         cudaFree(S.dmem);
@@ -435,8 +435,8 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
             fin.push_back({(int)i, 0, p, std::min<int64_t>(work[i].p_ready, p + 65536)});
         smem_f[nf] = std::max(smem_f[nf], S.plan->kt->smem_frame + tacc_bytes(c.d.nbo));
         maxnbo[nf] = std::max(maxnbo[nf], c.d.nbo);
-        smem_i[nf * 16 + ik] = std::max(smem_i[nf * 16 + ik], S.plan->kt->smem_frame +
-                                        16 * (size_t)c.d.z * (size_t)(c.d.k_hi - c.d.k_lo + 1) + 4 * (size_t)c.d.seg_len);
+        smem_i[nf * 16 + ik] = std::max(smem_i[nf * 16 + ik], inverse_smem_bytes(S.plan->kt->smem_frame, c.d.z,
+                                                                                  c.d.k_hi - c.d.k_lo + 1, c.d.seg_len));
     }
     std::vector<BatchItem> all;
     std::vector<std::pair<size_t, size_t>> spans_f, spans_i;
