@@ -423,6 +423,95 @@ __device__ __forceinline__ void fft_last_to_regs(const float2 *buf, const float2
     if constexpr (SYNC) __syncthreads();
 }
 
+// ---- In-place decimation in frequency, for NF = 16^P (P = 2, 3)
+// Pass p combines the elements at stride ST = NF / 16^p and multiplies
+// output r of butterfly s (its position within the stride) by W_{16 ST}^{s r}
+// (the Stockham table of span ST); every butterfly reads and writes the same
+// sixteen elements, so a pass needs one barrier (after its stores) instead of
+// two.  The spectrum comes out digit-reversed in the buffer: element
+// 256 k0 + 16 k1 + k2 (NF = 4096) holds X[k0 + 16 k1 + 256 k2].  The last
+// pass undoes that by its choice of butterfly: thread t takes the butterfly
+// of the sixteen elements 16 rev(t) .. 16 rev(t) + 15 (rev: the two hex
+// digits of t swapped), whose outputs are X[t + r NF/16], the same registers
+// as the Stockham last pass.  Element i lives at dpad(i) = i + i/16 + i/256,
+// which keeps all three passes' accesses free of bank conflicts.
+template <int NF> __host__ __device__ constexpr bool dif_ok() { return NF == 256 || NF == 4096; }
+__host__ __device__ constexpr int dpad(int i) { return i + (i >> 4) + (i >> 8); }
+template <int NF> __host__ __device__ constexpr int dif_len() { return dif_ok<NF>() ? dpad(NF - 1) + 1 : 0; }
+template <int NF> __device__ __forceinline__ int dif_rev(int t) {
+    if constexpr (NF == 4096) return ((t & 15) << 4) | (t >> 4);
+    else return t;
+}
+
+// first pass from registers: butterfly j = tid (< NF/16) holds x[j + r NF/16]
+// in v[r] (zero where bit r of MASK is clear); no barrier inside
+template <int NF, int TPF, bool INV, unsigned MASK>
+__device__ __forceinline__ void dif_first_from_regs(float2 *buf, float2 (&v)[16], const float2 *__restrict__ tw,
+                                                    int tid) {
+    constexpr int ST = NF / 16;
+    if (TPF == ST || tid < ST) {
+        dft16m<INV, MASK>(v);
+        twiddle16<INV>(v, tw + tw_offset<NF, ST>(), ST, tid);
+        const int b = dpad(tid);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[b + r * dpad(ST)] = v[r];   // dpad(tid + r ST) = dpad(tid) + r dpad(ST)
+    }
+}
+
+// the middle pass (NF = 4096 only: stride 16), ends with a barrier
+template <int NF, int TPF, bool INV>
+__device__ __forceinline__ void dif_middle(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    if constexpr (NF == 4096) {
+        constexpr int ST = 16;
+        if (TPF == NF / 16 || tid < NF / 16) {
+            const int sidx = tid & (ST - 1);
+            const int b = dpad((tid >> 4) * 256 + sidx);   // + 17 r for element + 16 r
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = buf[b + 17 * r];
+            dft16<INV>(v);
+            twiddle16<INV>(v, tw + tw_offset<NF, ST>(), ST, sidx);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) buf[b + 17 * r] = v[r];
+        }
+        __syncthreads();
+    }
+}
+
+// last pass into registers: v[r] = X[tid + r NF/16]; ends with a barrier (SYNC)
+template <int NF, int TPF, bool INV, bool SYNC = true>
+__device__ __forceinline__ void dif_last_to_regs(const float2 *buf, int tid, float2 (&v)[16]) {
+    constexpr int NS = NF / 16;
+    if (TPF == NS || tid < NS) {
+        const int b = dpad(16 * dif_rev<NF>(tid));   // + r for element + r
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = buf[b + r];
+        dft16<INV>(v);
+    }
+    if constexpr (SYNC) __syncthreads();
+}
+
+// ---- The three phases of a frame transform whose input and output are in
+// registers, in the in-place form where NF allows it and the Stockham form
+// otherwise.  fft_in: first pass (the caller syncs after it); fft_mid: the
+// middle passes (each ends with a barrier); fft_out: the last pass.
+template <int NF, int TPF, bool INV, unsigned MASK>
+__device__ __forceinline__ void fft_in(float2 *buf, float2 (*u)[FftPlan<NF>::R1], const float2 *__restrict__ tw,
+                                       int tid) {
+    if constexpr (dif_ok<NF>()) dif_first_from_regs<NF, TPF, INV, MASK>(buf, u[0], tw, tid);
+    else fft_first_from_regs<NF, TPF, INV, MASK>(buf, u, tid);
+}
+template <int NF, int TPF, bool INV>
+__device__ __forceinline__ void fft_mid(float2 *buf, const float2 *__restrict__ tw, int tid) {
+    if constexpr (dif_ok<NF>()) dif_middle<NF, TPF, INV>(buf, tw, tid);
+    else fft_middle<NF, TPF, FftPlan<NF>::R1, INV>(buf, tw, tid);
+}
+template <int NF, int TPF, bool INV, bool SYNC = true>
+__device__ __forceinline__ void fft_out(const float2 *buf, const float2 *__restrict__ tw, int tid, float2 (&v)[16]) {
+    if constexpr (dif_ok<NF>()) dif_last_to_regs<NF, TPF, INV, SYNC>(buf, tid, v);
+    else fft_last_to_regs<NF, TPF, INV, SYNC>(buf, tw, tid, v);
+}
+
 // Whole in-place FFT of buf (natural order in and out), for callers that do
 // not fuse the first or last pass.  Caller syncs after writing buf; ends with
 // a __syncthreads().

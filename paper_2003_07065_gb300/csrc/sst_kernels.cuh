@@ -17,7 +17,8 @@ namespace sst {
 
 template <int NF> struct Cfg {
     static constexpr int TPF = (NF / 16 < 32) ? 32 : NF / 16;  // threads per CTA
-    static constexpr int BUF = padded_len(NF);                    // float2 per frame buffer
+    // float2 per frame buffer (the larger of the two layouts, rounded to 16 bytes)
+    static constexpr int BUF = ((padded_len(NF) > dif_len<NF>() ? padded_len(NF) : dif_len<NF>()) + 1) & ~1;
     static constexpr int R1 = FftPlan<NF>::R1;                    // radix of the first pass
     static constexpr int PER1 = (NF / R1 + TPF - 1) / TPF;        // first-pass butterflies per thread
     static constexpr int NSL = NF / 16;                           // span of the last pass
@@ -148,10 +149,10 @@ __device__ __forceinline__ void forward_fft(float2 *buf, const SstDev &d, const 
     using C = Cfg<NF>;
     float2 u[C::PER1][C::R1];
     gather_first<NF, PAIR, WMASK>(u, d, x, c1, c2, has2, tid);
-    fft_first_from_regs<NF, C::TPF, false, WMASK>(buf, u, tid);
+    fft_in<NF, C::TPF, false, WMASK>(buf, u, d.tw, tid);
     __syncthreads();
-    fft_middle<NF, C::TPF, C::R1, false>(buf, d.tw, tid);
-    fft_last_to_regs<NF, C::TPF, false, SYNC>(buf, d.tw, tid, v);
+    fft_mid<NF, C::TPF, false>(buf, d.tw, tid);
+    fft_out<NF, C::TPF, false, SYNC>(buf, d.tw, tid, v);
 }
 
 // Scatter the last-pass outputs needed by the Hermitian split into buf:
@@ -884,11 +885,11 @@ __device__ __forceinline__ void forward_frame_alias(const SstDev &d, const float
     {
         float2 u[C::PER1][C::R1];
         gather_staged<NF, WMASK>(u, d, seg, off, tid);
-        fft_first_from_regs<NF, TPF, false, WMASK>(buf, u, tid);
+        fft_in<NF, TPF, false, WMASK>(buf, u, d.tw, tid);
     }
     __syncthreads();
-    fft_middle<NF, TPF, C::R1, false>(buf, d.tw, tid);
-    fft_last_to_regs<NF, TPF, false, true>(buf, d.tw, tid, v);   // ends with a barrier
+    fft_mid<NF, TPF, false>(buf, d.tw, tid);
+    fft_out<NF, TPF, false, true>(buf, d.tw, tid, v);   // ends with a barrier
     store_mirror<NF, OMASK>(mz, d, tid, v);
     uint4 *a4 = reinterpret_cast<uint4 *>(acc);
     for (int i = tid; i < stride; i += TPF) a4[i] = make_uint4(0u, 0u, 0u, 0u);   // 4 stride words
@@ -1108,7 +1109,7 @@ __device__ __forceinline__ void inverse_first_pass(const SstDev &d, const float2
             u[bb][r] = y;
         }
     }
-    fft_first_from_regs<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, tid);
+    fft_in<NF, TPF, true, band_mask<NF>(CLS)>(buf, u, d.tw, tid);
 }
 
 // shared memory of the inverse: frame buffer, the pair's rows by sub-grid, overlap-add segment
@@ -1250,9 +1251,9 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
                 mbar_expect_tx(rbar, pair_bytes);
                 bulk_g2s(Tst, tile_rows + (size_t)2 * (pr + 1) * d.nbo, pair_bytes, rbar);
             }
-            fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
+            fft_mid<NF, TPF, true>(buf, d.tw, tid);
             float2 v[16];
-            fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
+            fft_out<NF, TPF, true>(buf, d.tw, tid, v);
             if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
         }
         // overlap-add a, then b (ascending frame order at every sample)
@@ -1320,9 +1321,9 @@ __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 
         // element q of sub-grid s of a row: row[z q + s]
         inverse_first_pass<NF, CLS>(d, rowA + s, rowA + sb, rowB + s, rowB + sb, d.z, s, buf, tid);
         __syncthreads();
-        fft_middle<NF, TPF, C::R1, true>(buf, d.tw, tid);
+        fft_mid<NF, TPF, true>(buf, d.tw, tid);
         float2 v[16];
-        fft_last_to_regs<NF, TPF, true>(buf, d.tw, tid, v);
+        fft_out<NF, TPF, true>(buf, d.tw, tid, v);
         if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
     }
 }
