@@ -97,14 +97,15 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // max over frames of A_m = sum_j |x[m H + j - M]| |g_j|, which bounds |S^g| in
 // every bin of frame m; folded into ctl[4] (float bits).  A CTA takes tiles
-// of tf frames, staging the tile's |x| segment ((tf - 1) H + L floats) in
-// shared memory; a warp sums one frame at a time.
+// of tf frames, staging the tile's |x| segment in shared memory ((tf + 2) H + L
+// floats: a warp sums four consecutive frames at a time, and those past the
+// tile's last read samples that are staged but not counted).
 __global__ void k_frame_absmax(SstDev d, const float *__restrict__ x, int tf, unsigned *__restrict__ ctl) {
     extern __shared__ float seg[];
     __shared__ float red[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int64_t tiles = (d.F + tf - 1) / tf;
-    const int len = (tf - 1) * d.hop + d.L;
+    const int len = (tf + 2) * d.hop + d.L;   // the tile's frames and three beyond (see below)
     float best = 0.f;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t m0 = t * tf;
@@ -115,11 +116,29 @@ __global__ void k_frame_absmax(SstDev d, const float *__restrict__ x, int tf, un
             seg[i] = (p >= 0 && p < d.n) ? fabsf(x[p]) : 0.f;
         }
         __syncthreads();
-        for (int f = warp; f < tf && m0 + f < d.F; f += nw) {
+        // four frames per warp at a time, sharing each load of |g|
+        for (int f = 4 * warp; f < tf && m0 + f < d.F; f += 4 * nw) {
             const float *w = seg + f * d.hop;
-            float a = 0.f;
-            for (int j = lane; j < d.L; j += 32) a = fmaf(w[j], fabsf(__ldg(&d.g[j])), a);
-            best = fmaxf(best, warp_sum(a));
+            const int h = d.hop;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            for (int j = lane; j < d.L; j += 32) {
+                const float gj = fabsf(__ldg(&d.g[j]));
+                a0 = fmaf(w[j], gj, a0);
+                a1 = fmaf(w[j + h], gj, a1);
+                a2 = fmaf(w[j + 2 * h], gj, a2);
+                a3 = fmaf(w[j + 3 * h], gj, a3);
+            }
+            a0 = warp_sum(a0);
+            a1 = warp_sum(a1);
+            a2 = warp_sum(a2);
+            a3 = warp_sum(a3);
+            // frames past the tile's (or the signal's) last read staged samples
+            // that belong to no frame of the tile: only the tile's frames count
+            const int64_t left = min((int64_t)tf - f, d.F - (m0 + f));
+            best = fmaxf(best, a0);
+            if (left > 1) best = fmaxf(best, a1);
+            if (left > 2) best = fmaxf(best, a2);
+            if (left > 3) best = fmaxf(best, a3);
         }
     }
     best = warp_max(best);
@@ -591,7 +610,16 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     // ---- one-pass relative threshold (default for relative plans)
     pl->smem_fwd_spec = pl->smem_fwd_t +
                         (spec_in_frame(nb, nbo, (int)((kt->smem_frame - 128) / sizeof(float2))) ? 0 : spec_smem_bytes(nbo));
-    pl->spec = d.relative && !(p.flags & SST_TWO_PASS) && pl->smem_fwd_spec <= smax;
+    // frames per tile of the A_m bound (k_frame_absmax): its segment of
+    // (tf + 2) H + L floats within 48 KiB where it can be, else one frame per
+    // tile with the kernel's shared-memory limit raised
+    pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop - 2));
+    pl->smem_frame_absmax = sizeof(float) * ((size_t)(pl->spec_tf + 2) * hop + L);
+    bool bound_ok = pl->smem_frame_absmax <= 48 * 1024;
+    if (!bound_ok && pl->smem_frame_absmax <= smax)
+        bound_ok = cudaFuncSetAttribute(k_frame_absmax, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)pl->smem_frame_absmax) == cudaSuccess;
+    pl->spec = d.relative && !(p.flags & SST_TWO_PASS) && pl->smem_fwd_spec <= smax && bound_ok;
     if (pl->spec) {
         ce = raise_smem(kt, pl->kind_fwd_spec, pl->smem_fwd_spec);
         if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "cudaFuncSetAttribute"); }
@@ -605,8 +633,6 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
                 pl->grid_fwd_spec = grid_for(ka, ba, fwd_chunks);
             }
         }
-        // frames per tile of the A_m bound: the tile's segment stays within 48 KiB
-        pl->spec_tf = (int)std::max<int64_t>(1, std::min<int64_t>(32, (12000 - (int64_t)L) / hop + 1));
         // records: 1/64 of the sources, plus the chunk tails each CTA may leave unused
         pl->spec_cap = (int)std::min<int64_t>(std::max<int64_t>(4096, F * (int64_t)nb / 64) +
                                                   (int64_t)SPEC_CHUNK * pl->grid_fwd_spec,
@@ -802,7 +828,7 @@ static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *
     {
         const int64_t tiles = (d.F + pl->spec_tf - 1) / pl->spec_tf;
         const int grid = (int)std::min<int64_t>(tiles, (int64_t)pl->num_sms * 8);
-        const size_t smem = sizeof(float) * ((size_t)(pl->spec_tf - 1) * d.hop + d.L);
+        const size_t smem = pl->smem_frame_absmax;
         SST_LAUNCHED_K(PK_ABSMAX, st,
                        (k_frame_absmax<<<grid, 256, smem, st>>>(d, x, pl->spec_tf, sb.ctl), cudaGetLastError()),
                        "frame bound launch");
