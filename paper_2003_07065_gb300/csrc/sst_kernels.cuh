@@ -1031,15 +1031,15 @@ template <bool NARROW> struct InvTaps {
 };
 
 // The last-pass taps of thread tid: n_i = q or q - NF (q = tid + r NF/16),
-// INT_MIN where outside the window, and omega_i = exp(2 pi i n_i / (z NF)),
-// the sub-grid twiddle of sub-grid 1, whose powers give the others.
+// INT_MIN where outside the window, and (NARROW) omega_i = exp(2 pi i n_i /
+// (z NF)), the sub-grid twiddle of sub-grid 1, whose powers give the others.
 template <int NF, bool NARROW>
 __device__ __forceinline__ void inverse_taps(const SstDev &d, int tid, int (&tap)[InvTaps<NARROW>::NACC],
                                              float2 (&om)[InvTaps<NARROW>::NACC]) {
     using TP = InvTaps<NARROW>;
     constexpr int NS = NF / 16;
     const bool live = (Cfg<NF>::TPF == NS) || tid < NS;
-    const float2 b1 = (d.z > 1 && live) ? __ldg(&d.twb[NS + tid]) : make_float2(1.f, 0.f);
+    const float2 b1 = (NARROW && d.z > 1 && live) ? __ldg(&d.twb[NS + tid]) : make_float2(1.f, 0.f);
 #pragma unroll
     for (int i = 0; i < TP::NACC; ++i) {
         const int r = TP::r_of(i);
@@ -1050,7 +1050,7 @@ __device__ __forceinline__ void inverse_taps(const SstDev &d, int tid, int (&tap
         const bool ok = live && n >= -d.M && n <= d.M && !(i == 16 && tid != 0);
         tap[i] = ok ? n : INT_MIN;
         om[i] = make_float2(1.f, 0.f);
-        if (ok && d.z > 1) om[i] = (i == 16) ? __ldg(&d.twn[1]) : cmul(b1, __ldg(&d.twc[(2 + (n < 0)) * 16 + r]));
+        if (NARROW && ok && d.z > 1) om[i] = cmul(b1, __ldg(&d.twc[(2 + (n < 0)) * 16 + r]));
     }
 }
 
@@ -1131,20 +1131,61 @@ __device__ __forceinline__ void inverse_ola(const SstDev &d, float *seg, int o,
         if (tap[i] != INT_MIN) seg[o + tap[i]] += (__ldg(&d.g[tap[i] + d.M]) * cnorm) * (IMAG ? racc[i].y : racc[i].x);
 }
 
+// The same with the weights read once for both frames of the pair, all loads
+// before the first store: for kernels whose plan descriptor lives in shared
+// memory (batches), where each store to the segment would otherwise make the
+// compiler read the window pointer and M again before the next tap's load.
+template <int NF, bool NARROW>
+__device__ __forceinline__ void inverse_weights(const SstDev &d, const int (&tap)[InvTaps<NARROW>::NACC],
+                                                float (&gw)[InvTaps<NARROW>::NACC]) {
+    const float cnorm = 1.0f / (float)NF;
+    const float *g = d.g + d.M;
+#pragma unroll
+    for (int i = 0; i < InvTaps<NARROW>::NACC; ++i) gw[i] = tap[i] != INT_MIN ? __ldg(&g[tap[i]]) * cnorm : 0.f;
+}
+template <bool NARROW, bool IMAG>
+__device__ __forceinline__ void inverse_ola_w(float *seg, int o, const int (&tap)[InvTaps<NARROW>::NACC],
+                                              const float (&gw)[InvTaps<NARROW>::NACC],
+                                              const float2 (&racc)[InvTaps<NARROW>::NACC]) {
+#pragma unroll
+    for (int i = 0; i < InvTaps<NARROW>::NACC; ++i)
+        if (tap[i] != INT_MIN) seg[o + tap[i]] += gw[i] * (IMAG ? racc[i].y : racc[i].x);
+}
+
 // Tap accumulation of sub-grid s, taken in descending order (Horner's rule
 // in omega): racc = sum_s omega^s v_s, i.e. every tap gets the sub-grid
-// twiddle exp(i 2 pi s n / (z NF)) of Eq. 25's zNf-point inverse.
-template <bool NARROW>
-__device__ __forceinline__ void inverse_accumulate(float2 (&racc)[InvTaps<NARROW>::NACC], const float2 (&v)[16],
-                                                   const float2 (&om)[InvTaps<NARROW>::NACC], bool first) {
+// twiddle exp(i 2 pi s n / (z NF)) of Eq. 25's zNf-point inverse.  The 9
+// taps of a half-length window keep omega in registers (om); the 17 of a
+// wider one form it again from the tables at each sub-grid (holding 17 more
+// complex values would spill).
+template <int NF, bool NARROW>
+__device__ __forceinline__ void inverse_accumulate(const SstDev &d, float2 (&racc)[InvTaps<NARROW>::NACC],
+                                                   const float2 (&v)[16], const float2 (&om)[InvTaps<NARROW>::NACC],
+                                                   const int (&tap)[InvTaps<NARROW>::NACC], int tid, bool first) {
     using TP = InvTaps<NARROW>;
+    if constexpr (NARROW) {
 #pragma unroll
-    for (int i = 0; i < TP::NACC; ++i) {
-        const float2 x = v[TP::r_of(i)];
+        for (int i = 0; i < TP::NACC; ++i) {
+            const float2 x = v[TP::r_of(i)];
+            if (first) {
+                racc[i] = x;
+            } else {
+                const float2 a = racc[i], w = om[i];
+                racc[i] = make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, x.x)), fmaf(a.x, w.y, fmaf(a.y, w.x, x.y)));
+            }
+        }
+    } else {
         if (first) {
-            racc[i] = x;
-        } else {
-            const float2 a = racc[i], w = om[i];
+#pragma unroll
+            for (int i = 0; i < TP::NACC; ++i) racc[i] = v[TP::r_of(i)];
+            return;
+        }
+        const float2 b1 = __ldg(&d.twb[NF / 16 + tid]);
+#pragma unroll
+        for (int i = 0; i < TP::NACC; ++i) {
+            const float2 x = v[TP::r_of(i)];
+            const float2 w = (i == 16) ? __ldg(&d.twn[1]) : cmul(b1, __ldg(&d.twc[(2 + (tap[i] < 0)) * 16 + TP::r_of(i)]));
+            const float2 a = racc[i];
             racc[i] = make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, x.x)), fmaf(a.x, w.y, fmaf(a.y, w.x, x.y)));
         }
     }
@@ -1153,8 +1194,9 @@ __device__ __forceinline__ void inverse_accumulate(float2 (&racc)[InvTaps<NARROW
 // One inverse tile; smem4 is the kernel's dynamic shared memory.  Ends with a
 // barrier-free write of the tile's segment (callers looping over tiles sync
 // before the next tile zeroes the segment).  CLS: band class (see
-// band_class); the spectrum inputs at other positions are not formed.
-template <int NF, bool NARROW, int CLS = 0>
+// band_class); the spectrum inputs at other positions are not formed.  SMEMD:
+// d lives in shared memory (batches; see inverse_weights).
+template <int NF, bool NARROW, int CLS = 0, bool SMEMD = false>
 __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__restrict__ T, float *__restrict__ partial,
                                              int64_t tile, float4 *smem4, int tid) {
     using C = Cfg<NF>;
@@ -1254,13 +1296,21 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             fft_mid<NF, TPF, true>(buf, d.tw, tid);
             float2 v[16];
             fft_out<NF, TPF, true>(buf, d.tw, tid, v);
-            if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
+            if (live) inverse_accumulate<NF, NARROW>(d, racc, v, om, tap, tid, s == d.z - 1);
         }
         // overlap-add a, then b (ascending frame order at every sample)
         const int oa = (int)(a - m0) * d.hop + d.M;
-        inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
-        __syncthreads();
-        if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
+        if constexpr (SMEMD) {
+            float gw[TP::NACC];
+            inverse_weights<NF, NARROW>(d, tap, gw);
+            inverse_ola_w<NARROW, false>(seg, oa, tap, gw, racc);
+            __syncthreads();
+            if (hasb) inverse_ola_w<NARROW, true>(seg, oa + d.hop, tap, gw, racc);
+        } else {
+            inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
+            __syncthreads();
+            if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
+        }
         __syncthreads();
     }
     float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
@@ -1310,6 +1360,7 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
 template <int NF, bool NARROW, int CLS>
 __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 *__restrict__ rowA,
                                                   const float2 *__restrict__ rowB, float2 *buf, int tid,
+                                                  const int (&tap)[InvTaps<NARROW>::NACC],
                                                   const float2 (&om)[InvTaps<NARROW>::NACC],
                                                   float2 (&racc)[InvTaps<NARROW>::NACC]) {
     using C = Cfg<NF>;
@@ -1324,7 +1375,7 @@ __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 
         fft_mid<NF, TPF, true>(buf, d.tw, tid);
         float2 v[16];
         fft_out<NF, TPF, true>(buf, d.tw, tid, v);
-        if (live) inverse_accumulate<NARROW>(racc, v, om, s == d.z - 1);
+        if (live) inverse_accumulate<NF, NARROW>(d, racc, v, om, tap, tid, s == d.z - 1);
     }
 }
 
@@ -1344,7 +1395,6 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     using C = Cfg<NF>;
     using TP = InvTaps<NARROW>;
     constexpr int TPF = C::TPF;
-    constexpr int NS = NF / 16;
     extern __shared__ float4 smem4[];
     const int tid = threadIdx.x;
     float2 *buf = reinterpret_cast<float2 *>(smem4);
@@ -1387,7 +1437,7 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         float2 om[TP::NACC];
         inverse_taps<NF, NARROW>(d, tid, tap, om);
         float2 racc[TP::NACC];
-        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, om, racc);
+        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, tap, om, racc);
         // overlap-add a, then b (ascending frame order at every sample)
         const int oa = (int)(a - m0) * d.hop + d.M;
         inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
@@ -1498,7 +1548,7 @@ k_inverse_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ 
         load_chan(sd, ch, w.chan, tid, C::TPF);
         __syncthreads();
         if (!chan_ok<NF>(sd) || w.begin >= sd.ntiles || !class_ok<NF, CLS>(sd)) continue;
-        inverse_tile<NF, NARROW, CLS>(sd, ch[w.chan].T, ch[w.chan].ola, w.begin, smem4, tid);
+        inverse_tile<NF, NARROW, CLS, true>(sd, ch[w.chan].T, ch[w.chan].ola, w.begin, smem4, tid);
     }
 }
 
