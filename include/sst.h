@@ -204,10 +204,17 @@ sst_status sst_renyi(const float *tfr_dev, int64_t rows, int32_t cols, int64_t l
  * reaches global memory: the inverse of frame m needs only column m of T
  * (Eq. 25), so one kernel per tile of frames runs the forward of each pair
  * of frames into T rows in shared memory and inverts them from there
- * (Eq. 25-26).  A relative threshold then takes max|S^g| from a pre-pass
- * over every frame (as SST_TWO_PASS plans do), since no T is left to settle
- * afterwards.  The result equals that of a SST_TWO_PASS plan with a TFR
- * output up to the rounding of the overlap-add.  Plans whose fused kernel
+ * (Eq. 25-26).  With a relative threshold and the one-pass default, the
+ * sources between the threshold's two bounds are left out of the rows and
+ * recorded per tile; once the forward has found the exact max|S^g|, the
+ * kept ones add their term of Eq. 25-26 to the reconstruction directly (in
+ * the order of frame and source bin, so repeated calls give the same bits).
+ * The kept sources are those of the same plan's call with a TFR output, and
+ * the reconstructions differ by rounding only; should a tile's records
+ * overflow, the call redoes itself with the two-pass kernels (behind a
+ * device-side gate).  SST_TWO_PASS plans take max|S^g| from a pre-pass over
+ * every frame and then carry the same bits as their call with a TFR output.
+ * Plans whose fused kernel
  * would need more shared memory than the device offers per block (large Nf
  * with a wide band and subdivision) return SST_EUNSUPPORTED for a NULL
  * tfr_dev.  xhat_dev: n floats. */
@@ -266,8 +273,9 @@ sst_status sst_fp32_peak(double *tflops, void *stream);
 
 /* The last sst_forward / sst_forward_inverse of a relative plan with the
  * one-pass threshold (the default): how many sources waited for the exact
- * threshold, how many fine bins they fell in, and whether a record buffer
- * overflowed so that the two-pass kernels redid the forward (then 1).  Reads
+ * threshold, how many fine bins they fell in (0 for a call without a TFR
+ * output, which settles sources, not bins), and whether a record buffer
+ * overflowed so that the two-pass kernels redid the call (then 1).  Reads
  * the control words the call left in `workspace` (synchronises the device).
  * Zeros for other plans. */
 sst_status sst_threshold_stats(sst_plan_t plan, const void *workspace, int64_t *waiting, int64_t *bins,
@@ -306,7 +314,8 @@ sst_status sst_test_withhold_sample_copy(sst_plan_t plan);
  * from the parts that computed them into the same places of this part's
  * workspace (sst_part_segments gives where), and sst_part_finalize divides
  * by D on the part's output samples.  The parts' outputs, concatenated,
- * carry the same bits as the unsplit sst_forward_inverse with a NULL tfr. */
+ * carry the same bits as the unsplit sst_forward_inverse with a NULL tfr of
+ * a SST_TWO_PASS plan (the parts' maximum is the exact one). */
 typedef struct {
     int64_t tile_begin, tile_end;    /* the part's inverse tiles */
     int64_t frame_begin, frame_end;  /* its frames, [tile_begin B, min(tile_end B, F)) */

@@ -213,6 +213,73 @@ __global__ void k_spec_fix_bin(SpecBuf sb, const SstScalars *__restrict__ sc, Ss
     }
 }
 
+// Settles the sources that the path without a TFR output deferred (those
+// between the one-pass threshold's two bounds): a source above the exact
+// gamma^2 = frac^2 max |S^g|^2 (the decision k_spec_fix_src takes) adds its
+// share of the reconstruction to its tile's overlap-add segment, the
+// coefficient's term of Eq. 25 times the window of Eq. 26,
+// (g[n] / Nf) w 2 Re(S^g exp(2 pi i (z k_lo + l) n / (z Nf))) for |n| <= M,
+// w = 1/2 at the coarse DC and Nyquist bins (their own Hermitian images).
+// Sources are taken in the order of (frame, source bin) and each thread owns
+// the segment samples tid + i SETTLE_T, so every sample's sum has a fixed
+// order whatever order the records were taken in, and no barrier is needed
+// between sources.  The phase steps along a thread's samples by one complex
+// product.  One CTA per tile; shared memory: the segment, the window, then
+// the records' keys and their order.
+constexpr int SETTLE_T = 256;
+__global__ void __launch_bounds__(SETTLE_T) k_fused_settle(SstDev d, float frac2, float *__restrict__ partial) {
+    extern __shared__ float sseg[];
+    if (d.spec.ctl[3]) return;   // a record list overflowed: the two-pass kernels redo the call
+    const int tid = threadIdx.x;
+    const int64_t tile = d.tile0 + blockIdx.x;
+    const int n = d.fused_count[tile];
+    if (n <= 0) return;
+    float *gs = sseg + d.seg_len;
+    int *key = reinterpret_cast<int *>(gs + d.L);
+    int *ord = key + d.fused_cap;
+    const SpecBin *rec = d.spec.bin + (size_t)tile * d.fused_cap;
+    const int64_t m0 = tile * d.B;
+    float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
+    const float cn = 2.0f / (float)d.nf;
+    for (int i = tid; i < n; i += SETTLE_T) key[i] = (int)(rec[i].m - m0) * d.nb + (int)rec[i].w[3];
+    for (int i = tid; i < d.seg_len; i += SETTLE_T) sseg[i] = out[i];
+    for (int i = tid; i < d.L; i += SETTLE_T) gs[i] = __ldg(&d.g[i]) * cn;
+    __syncthreads();
+    for (int i = tid; i < n; i += SETTLE_T) {   // rank of each (unique) key
+        const int k = key[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += key[j] < k;
+        ord[r] = i;
+    }
+    __syncthreads();
+    const float gamma2 = frac2 * __uint_as_float(d.spec.ctl[0]);
+    const int zn = d.z * d.nf;
+    const int ldc = (d.k_lo <= 0 && d.k_hi >= 0) ? -d.z * d.k_lo : -1;
+    const int lnyq = (d.k_lo <= d.nf / 2 && d.k_hi >= d.nf / 2) ? d.z * (d.nf / 2 - d.k_lo) : -1;
+    for (int r = 0; r < n; ++r) {
+        const SpecBin b = rec[ord[r]];
+        if (!(__uint_as_float(b.w[2]) > gamma2)) continue;
+        const float w = (b.l == ldc || b.l == lnyq) ? 0.5f : 1.f;
+        const float vr = __uint_as_float(b.w[0]) * w, vi = __uint_as_float(b.w[1]) * w;
+        const int fz = d.z * d.k_lo + b.l;   // frequency in units of 1 / (z Nf)
+        const int base = (int)(b.m - m0) * d.hop;   // segment index of the frame's tap -M
+        // this thread's samples o = tid + i SETTLE_T in [base, base + L)
+        int o = tid + ((base - tid + SETTLE_T - 1 > 0 ? base - tid + SETTLE_T - 1 : 0) / SETTLE_T) * SETTLE_T;
+        if (o >= base + d.L) continue;
+        const int t0 = o - base - d.M;   // n of the first sample
+        int j = (int)(((long long)fz * t0) % zn);
+        if (j < 0) j += zn;
+        float2 e = __ldg(&d.twf[j]);
+        const float2 E = __ldg(&d.twf[(int)(((long long)fz * SETTLE_T) % zn)]);
+        for (int tt = o - base; tt < d.L; tt += SETTLE_T, o += SETTLE_T) {
+            sseg[o] += gs[tt] * (vr * e.x - vi * e.y);
+            e = make_float2(e.x * E.x - e.y * E.y, e.x * E.y + e.y * E.x);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < d.seg_len; i += SETTLE_T) out[i] = sseg[i];
+}
+
 __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.n; p += (int64_t)gridDim.x * blockDim.x)
         xhat[p] = finalize_value(d, partial, p);
@@ -471,6 +538,13 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         twn[s_] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
 
+    // the settling pass's phases exp(2 pi i j / (z nf))
+    std::vector<float2> twf((size_t)z * nf);
+    for (int j = 0; j < z * nf; ++j) {
+        const double a = 2.0 * M_PI * (double)j / (double)G;
+        twf[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+
     // ---- one device allocation for all tables
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
@@ -479,7 +553,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
                  o_twc = take(sizeof(float2) * twc.size()), o_twn = take(sizeof(float2) * z),
                  o_rl = take(sizeof(float) * rDl.size()),
                  o_rr = take(sizeof(float) * rDr.size()), o_rp = take(sizeof(float) * hop),
-                 o_w2 = take(sizeof(float2) * L), o_w3 = take(sizeof(float2) * L);
+                 o_w2 = take(sizeof(float2) * L), o_w3 = take(sizeof(float2) * L),
+                 o_twf = take(sizeof(float2) * twf.size());
     cudaError_t ce = cudaMalloc(&pl->dmem, off);
     if (ce != cudaSuccess) { delete pl; return fail(SST_ENOMEM, "cudaMalloc of %zu table bytes failed", off); }
     char *base = (char *)pl->dmem;
@@ -495,6 +570,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     memcpy(host.data() + o_rp, rDp.data(), sizeof(float) * hop);
     memcpy(host.data() + o_w2, win2.data(), sizeof(float2) * L);
     memcpy(host.data() + o_w3, win3.data(), sizeof(float2) * L);
+    memcpy(host.data() + o_twf, twf.data(), sizeof(float2) * twf.size());
     ce = cudaMemcpy(base, host.data(), off, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) { cudaFree(pl->dmem); delete pl; return cuda_fail(ce, "table upload"); }
 
@@ -505,6 +581,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     d.twb = (const float2 *)(base + o_twb);
     d.twc = (const float2 *)(base + o_twc);
     d.twn = (const float2 *)(base + o_twn);
+    d.twf = (const float2 *)(base + o_twf);
     d.rD_left = (const float *)(base + o_rl);
     d.rD_right = (const float *)(base + o_rr);
     d.rD_per = (const float *)(base + o_rp);
@@ -637,6 +714,20 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         pl->spec_cap = (int)std::min<int64_t>(std::max<int64_t>(4096, F * (int64_t)nb / 64) +
                                                   (int64_t)SPEC_CHUNK * pl->grid_fwd_spec,
                                               (int64_t)1 << 28);
+        // the same records serve the path without a TFR output: the bin
+        // records split evenly by inverse tile (at most 1024 per tile), the
+        // per-tile counts in the source records' array
+        if (pl->fused_ok) {
+            const int cap = (int)std::min<int64_t>(1024, pl->spec_cap / d.ntiles);
+            const size_t sm = sizeof(float) * ((size_t)d.seg_len + L) + 2 * sizeof(int) * (size_t)cap;
+            bool ok = cap >= 8 && (size_t)d.ntiles * sizeof(int32_t) <= sizeof(SpecSrc) * (size_t)pl->spec_cap;
+            if (ok && sm > 48 * 1024)
+                ok = sm <= smax && cudaFuncSetAttribute(k_fused_settle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)sm) == cudaSuccess;
+            pl->fused_spec = ok;
+            pl->fused_cap = cap;
+            pl->smem_settle = sm;
+        }
     }
 
     if (fwd_alias) {
@@ -819,8 +910,10 @@ static SpecBuf ws_spec(sst_plan_t pl, void *ws) {
 // path (up to the rounding of max |S^g|).  If a record buffer overflows, the
 // two-pass kernels, launched behind a device-side gate, redo the forward.
 static constexpr int kSpecStride = 16;
-static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *x, float *tfr, void *ws,
-                                   cudaStream_t st) {
+// The one-pass threshold's bounds and scalars: the control words cleared,
+// max_m A_m (k_frame_absmax), the sampled pre-pass, then g_lb2, g_ub2 and the
+// fixed-point scale (k_spec_scalars).
+static sst_status run_spec_bounds(sst_plan_t pl, const SstDev &d, const float *x, void *ws, cudaStream_t st) {
     SstScalars *sc = ws_scalars(pl, ws);
     float *partial = ws_partial(pl, ws);
     const SpecBuf sb = ws_spec(pl, ws);
@@ -842,6 +935,16 @@ static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *
                                                       sc),
                     cudaGetLastError()),
                    "one-pass scalars launch");
+    return SST_OK;
+}
+
+static sst_status run_forward_spec(sst_plan_t pl, const SstDev &d, const float *x, float *tfr, void *ws,
+                                   cudaStream_t st) {
+    SstScalars *sc = ws_scalars(pl, ws);
+    float *partial = ws_partial(pl, ws);
+    const SpecBuf sb = ws_spec(pl, ws);
+    sst_status s = run_spec_bounds(pl, d, x, ws, st);
+    if (s != SST_OK) return s;
     SstDev df = d;
     df.spec = sb;
     SST_LAUNCHED_K(PK_FORWARD, st,
@@ -935,12 +1038,54 @@ SST_API sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64
 // plans: max |S^g| over every frame, as SST_TWO_PASS plans do, since no T
 // exists to settle afterwards), one fused launch over the inverse tiles, and
 // k_finalize.
-static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws, cudaStream_t st) {
-    sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
+// The path without a TFR output with the one-pass relative threshold: the
+// bounds, k_fused (sources between them left out of the rows and recorded
+// per tile, the exact max |S^g| found), k_fused_settle (the recorded sources
+// the exact gamma keeps added to the segments); should a tile's records
+// overflow, the two-pass kernels behind the gate word redo the call.
+static sst_status run_fused_spec(sst_plan_t pl, const float *x, void *ws, cudaStream_t st) {
+    const SstDev &d = pl->d;
+    SstScalars *sc = ws_scalars(pl, ws);
+    float *partial = ws_partial(pl, ws);
+    const SpecBuf sb = ws_spec(pl, ws);
+    sst_status s = run_spec_bounds(pl, d, x, ws, st);
     if (s != SST_OK) return s;
-    SST_LAUNCHED_K(PK_FUSED, st,
-                   pl->kt->fused(pl->d, pl->kind_fused, x, ws_scalars(pl, ws), ws_ola(pl, ws), pl->smem_fused, st),
+    SstDev df = d;
+    df.spec = sb;
+    df.fused_count = reinterpret_cast<int32_t *>(sb.src);
+    df.fused_cap = pl->fused_cap;
+    SST_LAUNCHED_K(PK_FUSED, st, pl->kt->fused(df, pl->kind_fused, x, sc, ws_ola(pl, ws), pl->smem_fused, st),
                    "fused launch");
+    SST_LAUNCHED_K(PK_OTHER, st,
+                   (k_fused_settle<<<(unsigned)d.ntiles, SETTLE_T, pl->smem_settle, st>>>(df, pl->gamma_frac2,
+                                                                                     ws_ola(pl, ws)),
+                    cudaGetLastError()),
+                   "settle launch");
+    SstDev dg = d;
+    dg.gate = sb.ctl + 3;
+    SST_LAUNCHED_K(PK_ABSMAX, st, pl->kt->absmax(dg, pl->absmax_cls, x, partial, pl->grid_absmax, pl->smem_absmax, st),
+                   "absmax launch");
+    SST_LAUNCHED_K(PK_GAMMA, st,
+                   (k_gamma<<<1, 256, 0, st>>>(partial, pl->grid_absmax, pl->gamma_frac2, 0, 1.f, d.log2_nb, sc,
+                                               nullptr, sb.ctl + 3),
+                    cudaGetLastError()),
+                   "gamma launch");
+    SST_LAUNCHED_K(PK_FUSED, st, pl->kt->fused(dg, pl->kind_fused, x, sc, ws_ola(pl, ws), pl->smem_fused, st),
+                   "fused launch");
+    return SST_OK;
+}
+
+static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws, cudaStream_t st) {
+    if (pl->fused_spec) {
+        sst_status s = run_fused_spec(pl, x, ws, st);
+        if (s != SST_OK) return s;
+    } else {
+        sst_status s = run_prepass(pl, x, ws_scalars(pl, ws), ws_partial(pl, ws), st, nullptr);
+        if (s != SST_OK) return s;
+        SST_LAUNCHED_K(PK_FUSED, st,
+                       pl->kt->fused(pl->d, pl->kind_fused, x, ws_scalars(pl, ws), ws_ola(pl, ws), pl->smem_fused, st),
+                       "fused launch");
+    }
     int64_t blocks = (pl->d.n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     SST_LAUNCHED_K(PK_FINALIZE, st,

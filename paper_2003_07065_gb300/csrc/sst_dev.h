@@ -67,6 +67,13 @@ struct SstDev {
     const unsigned *gate;  // when set, the pre-pass and forward kernels run only if *gate != 0
     int sample_stride;     // pre-pass: every sample_stride-th group of four frames (0 or 1: all)
     SpecBuf spec;          // forward MODE_SPEC records
+    // one-pass relative threshold of the path without a TFR output (k_fused;
+    // null otherwise): per inverse tile, the sources between the two bounds
+    // go to spec.bin[tile * fused_cap + i] (m, l, w = S^g re, im, |S^g|^2 as
+    // float bits, source bin) and their count to fused_count[tile]
+    int32_t *fused_count;
+    int fused_cap;
+    const float2 *twf;     // exp(2 pi i j / (z nf)), j in [0, z nf): the settling pass's phases
     // component recovery (sst_inverse_zone): when set, the inverse keeps only
     // the coefficients of output bins l with |l - zone[m]| <= zone_hw (none
     // where zone[m] < 0), the zone of Eq. 15

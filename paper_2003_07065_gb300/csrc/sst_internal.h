@@ -104,6 +104,10 @@ struct sst_plan {
     size_t smem_fwd_spec = 0, ws_off_spec = 0;
     int grid_fwd_spec = 0, spec_tf = 1, spec_cap = 0;
     size_t smem_frame_absmax = 0;
+    // one-pass threshold of the path without a TFR output (k_fused_settle)
+    bool fused_spec = false;
+    int fused_cap = 0;
+    size_t smem_settle = 0;
     std::vector<double> g64, dgs64;   // FP64 window g and s g' (basis of the tensor form)
     bool custom_window = false;       // g was supplied by the caller (not the built-in Gaussian)
     std::atomic<int> test_withhold{0};      // one-shot test hook (sst_test_withhold_row_copy)

@@ -578,6 +578,30 @@ __device__ __forceinline__ void frame_bin(const SstDev &d, const FwdScale &fs, f
             return;
         }
     }
+    if (MODE == MODE_TROW && d.fused_count) {
+        // the one-pass threshold of the path without a TFR output: a source
+        // between the bounds is left out of the row and recorded for the
+        // settling pass, which adds its share of the reconstruction if the
+        // exact threshold keeps it (*nmarg: the tile's record count)
+        *vmax = fmaxf(*vmax, mag2);
+        if (l >= 0 && !(mag2 > fs.g_ub2)) {
+            const int i = atomicAdd(nmarg, 1);
+            if (i < d.fused_cap) {
+                SpecBin r;
+                r.m = m;
+                r.l = l;
+                r.w[0] = __float_as_uint(V.x);
+                r.w[1] = __float_as_uint(V.y);
+                r.w[2] = __float_as_uint(mag2);
+                r.w[3] = (uint32_t)kk;
+                r.pad = 0;
+                d.spec.bin[(size_t)(m / d.B) * d.fused_cap + i] = r;
+            } else {
+                atomicOr(&d.spec.ctl[3], 1u);   // the gated two-pass kernels redo the call
+            }
+            return;
+        }
+    }
     if (l >= 0) tacc_add(acc, tacc_stride(d.nbo), l, V, fs);
 }
 
@@ -1405,12 +1429,21 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     char *after = reinterpret_cast<char *>(rowA) + ((8 * (size_t)d.nbo + 15) & ~(size_t)15);
     float2 *mz = reinterpret_cast<float2 *>(after);
     float *seg = reinterpret_cast<float *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
-    const FwdScale fs = fwd_scale(d, sc, true);
+    __shared__ int ndef;   // sources recorded for the settling pass (one-pass threshold)
+    if (d.gate && *d.gate == 0u) return;
+    FwdScale fs = fwd_scale(d, sc, true);
+    const bool spec = d.fused_count != nullptr;
+    if (spec) {
+        fs.gamma2 = sc->g_lb2;
+        fs.g_ub2 = sc->g_ub2;
+    }
+    float vmax = 0.f;
     const int64_t tile = d.tile0 + blockIdx.x;
     const int64_t m0 = tile * d.B;
 
     for (int i = tid; i < 4 * stride; i += TPF) acc[i] = 0u;
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
+    if (tid == 0) ndef = 0;
     // (the first barrier inside the forward orders these before any use)
 
     for (int pr = 0; pr < d.B / 2; ++pr) {
@@ -1418,12 +1451,12 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         if (a >= d.F) break;
         const bool hasb = b < d.F;
         // forward of a: its row into rowA (the accumulators are cleared on the way)
-        forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, nullptr, nullptr,
+        forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, &ndef, &vmax,
                                           nullptr, mz);
         // forward of b: its row into the frame buffer (free once the frame's
         // bins are read), then moved into the accumulators' first half
         if (hasb) {
-            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, buf, nullptr, b, buf, acc, tid, nullptr, nullptr, nullptr,
+            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, buf, nullptr, b, buf, acc, tid, nullptr, &ndef, &vmax,
                                               nullptr, mz);
         } else {
             __syncthreads();
@@ -1450,6 +1483,14 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     }
     float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
     for (int i = tid; i < d.seg_len; i += TPF) out[i] = seg[i];
+    if (spec) {
+        vmax = warp_max(vmax);
+        if ((tid & 31) == 0 && vmax > 0.f) atomicMax(&d.spec.ctl[0], __float_as_uint(vmax));
+        if (tid == 0) {
+            d.fused_count[tile] = ndef < d.fused_cap ? ndef : d.fused_cap;
+            if (ndef > 0) atomicAdd(&d.spec.ctl[5], (unsigned)ndef);   // (threshold statistics)
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

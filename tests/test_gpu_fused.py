@@ -1,10 +1,21 @@
 """Forward + inverse without a TFR output (sst_forward_inverse with a NULL
 tfr): T stays in shared memory between the forward and the inverse of each
-pair of frames (Eq. 25 needs only the frame's own column).  The
-reconstruction must carry the same bits as a two-pass plan's forward +
-inverse through a TFR in global memory (same per-frame arithmetic, same
-tiles and overlap-add order), and meet the parity bars against the FP64
-oracle (the inverse end to end, with the moved-source bound, and the SNR)."""
+pair of frames (Eq. 25 needs only the frame's own column).
+
+* Two-pass plans (max |S^g| from a pre-pass first): the reconstruction must
+  carry the same bits as the same plan's forward + inverse through a TFR in
+  global memory (same per-frame arithmetic, same tiles and overlap-add
+  order).
+* One-pass plans (the default for a relative threshold): the sources
+  between the threshold's two bounds are left out of the rows and, once the
+  exact maximum is known, the kept ones are added to the reconstruction
+  directly (one coefficient's term of Eq. 25-26).  The kept set is the one
+  the one-pass TFR path keeps (same STFT arithmetic, same bounds), so the two
+  reconstructions differ by rounding only: within the reconstruction bar.
+  Repeated calls give the same bits.  A record overflow falls back to the
+  two-pass kernels and then matches them bit for bit.
+* Both meet the parity bars against the FP64 oracle (the inverse end to end,
+  with the moved-source bound, and the SNR)."""
 import numpy as np
 import pytest
 
@@ -29,23 +40,45 @@ def sst():
     return S
 
 
+XHAT_RTOL = 2e-5
+
+
 def same_bits_as_two_pass(S, params, x32):
     x = torch.from_numpy(x32).cuda()
     two = S.Plan(**params, two_pass=True)
     _, ref = two.forward_inverse(x)
-    plan = S.Plan(**params)
     got = torch.full_like(ref, float("nan"))
-    plan.reconstruct(x, got)
-    got2 = plan.reconstruct(x)
+    two.reconstruct(x, got)
+    got2 = two.reconstruct(x)
     torch.cuda.synchronize()
     assert torch.equal(got, ref), (got - ref).abs().max().item()
     assert torch.equal(got, got2)
     out = got.cpu().numpy().astype(np.float64)
     _, dest = two.reassign_map(x)
     dest = dest.cpu().numpy().astype(np.int64)
-    plan.close()
     two.close()
     return out, dest
+
+
+def one_pass_close(S, params, x32):
+    """The default plan's reconstruction without a TFR output against its
+    TFR path: same kept sources, rounding-level differences only; repeat
+    calls bit-identical.  Returns the reconstruction and the threshold stats."""
+    x = torch.from_numpy(x32).cuda()
+    one = S.Plan(**params)
+    _, ref = one.forward_inverse(x)
+    got = torch.full_like(ref, float("nan"))
+    one.reconstruct(x, got)
+    stats = S.sst_threshold_stats(one.handle, one.workspace)
+    got2 = one.reconstruct(x)
+    torch.cuda.synchronize()
+    assert torch.equal(got, got2)
+    err = (got - ref).abs().max().item()
+    scale = ref.abs().max().item()
+    assert err <= XHAT_RTOL * scale, (err, scale)
+    out = got.cpu().numpy().astype(np.float64)
+    one.close()
+    return out, stats, err / max(scale, 1e-30)
 
 
 def oracle_check(params, x32, xhat, dest, clean=None):
@@ -68,6 +101,9 @@ def test_workloads(sst, name):
     x32 = noisy.astype(np.float32)
     xhat, dest = same_bits_as_two_pass(sst, w.params(), x32)
     print(name, oracle_check(w.params(), x32, xhat, dest, clean))
+    x1, stats, rel = one_pass_close(sst, w.params(), x32)
+    assert not stats["fell_back"], stats
+    print(name, "one pass", stats, rel, oracle_check(w.params(), x32, x1, dest, clean))
 
 
 @pytest.mark.parametrize("params", EDGE, ids=[f"n{p['n']}_nf{p['nfft']}_z{p['z']}" for p in EDGE])
@@ -82,22 +118,52 @@ def test_edge_cases(sst, params):
         assert e.status == 6 and "shared memory" in str(e)
         pytest.skip("fused kernel does not fit this plan: " + str(e))
     print(params, oracle_check(params, x32, xhat, dest))
+    if params["relative"]:
+        x1, stats, rel = one_pass_close(sst, params, x32)
+        print("one pass", stats, rel)
 
 
 def test_runup_16m_full_size(sst):
-    """The benchmark's workload: the same bits as the two-pass path with a TFR."""
+    """The benchmark's workload: a two-pass plan gives the same bits as its
+    TFR path; the default (one-pass) plan stays within the reconstruction bar
+    of its TFR path, without falling back."""
     w = W.RUNUP_16M
     x32 = w.signal()[0].astype(np.float32)
     x = torch.from_numpy(x32).cuda()
     two = sst.Plan(**w.params(), two_pass=True)
     _, ref = two.forward_inverse(x)
-    two.close()
-    torch.cuda.synchronize()
-    plan = sst.Plan(**w.params())
-    got = plan.reconstruct(x)
+    got = two.reconstruct(x)
     torch.cuda.synchronize()
     assert torch.equal(got, ref)
-    plan.close()
+    two.close()
+    del ref, got
+    _, stats, rel = one_pass_close(sst, w.params(), x32)
+    assert not stats["fell_back"], stats
+    print("runup_16m one pass", rel)
+
+
+def test_one_pass_overflow_falls_back(sst):
+    """A transient whose loudest frames fall between the sampled pre-pass
+    frames leaves most sources between the two bounds: the records overflow
+    and the call redoes itself with the two-pass kernels, bit for bit."""
+    n, fs = 65536, 25600.0
+    params = dict(n=n, fs=fs, L=1025, sigma=128.0, hop=16, nfft=1024, f_lo=0.0, f_hi=12800.0, z=1,
+                  gamma=1e-3, relative=True)
+    gen = np.random.default_rng(77)
+    t = np.arange(n) / fs
+    x = 1e-3 * gen.standard_normal(n)
+    env = np.exp(-0.5 * ((np.arange(n) - 1600) / 40.0) ** 2)
+    x = torch.from_numpy((x + env * np.sin(2 * np.pi * 3000 * t)).astype(np.float32)).cuda()
+    one = sst.Plan(**params)
+    two = sst.Plan(**params, two_pass=True)
+    got = one.reconstruct(x)
+    stats = sst.sst_threshold_stats(one.handle, one.workspace)
+    ref = two.reconstruct(x)
+    torch.cuda.synchronize()
+    assert stats["fell_back"], stats
+    assert torch.equal(got, ref)
+    one.close()
+    two.close()
 
 
 def test_unsupported_plan_reported(sst):

@@ -98,7 +98,9 @@ def run_split(S, params, x32, parts):
 
 
 def unsplit(S, params, x32):
-    plan = S.Plan(**params)
+    # the split path takes the exact max |S^g| from its pre-pass (all-reduced
+    # over the parts), as a two-pass plan does
+    plan = S.Plan(**params, two_pass=True)
     out = plan.reconstruct(torch.from_numpy(x32).cuda())
     torch.cuda.synchronize()
     plan.close()
