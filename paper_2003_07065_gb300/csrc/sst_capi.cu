@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(SETTLE_T) k_fused_settle(SstDev d, float frac2
     float *gs = sseg + d.seg_len;
     int *key = reinterpret_cast<int *>(gs + d.L);
     int *ord = key + d.fused_cap;
-    const SpecBin *rec = d.spec.bin + (size_t)tile * d.fused_cap;
+    const SpecBin *rec = d.fused_rec + (size_t)tile * d.fused_cap;
     const int64_t m0 = tile * d.B;
     float *out = partial + (size_t)tslot_of(d, tile) * d.seg_len;
     const float cn = 2.0f / (float)d.nf;
@@ -714,13 +714,12 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         pl->spec_cap = (int)std::min<int64_t>(std::max<int64_t>(4096, F * (int64_t)nb / 64) +
                                                   (int64_t)SPEC_CHUNK * pl->grid_fwd_spec,
                                               (int64_t)1 << 28);
-        // the same records serve the path without a TFR output: the bin
-        // records split evenly by inverse tile (at most 1024 per tile), the
-        // per-tile counts in the source records' array
+        // the path without a TFR output records its waiting sources per
+        // inverse tile: room for 1/32 of a tile's sources (64 .. 2048)
         if (pl->fused_ok) {
-            const int cap = (int)std::min<int64_t>(1024, pl->spec_cap / d.ntiles);
+            const int cap = (int)std::max<int64_t>(64, std::min<int64_t>(2048, (int64_t)d.B * nb / 32));
             const size_t sm = sizeof(float) * ((size_t)d.seg_len + L) + 2 * sizeof(int) * (size_t)cap;
-            bool ok = cap >= 8 && (size_t)d.ntiles * sizeof(int32_t) <= sizeof(SpecSrc) * (size_t)pl->spec_cap;
+            bool ok = true;
             if (ok && sm > 48 * 1024)
                 ok = sm <= smax && cudaFuncSetAttribute(k_fused_settle, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)sm) == cudaSuccess;
@@ -742,12 +741,18 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
 
     // ---- workspace: [scalars 256 B][absmax partials][overlap-add partials]
     //      then, for the one-pass threshold, [control 256 B][source records][bin records]
+    //      and, for its path without a TFR output, [per-tile records][per-tile counts]
     pl->ws_off_partial = 256;
     pl->ws_off_ola = align256(pl->ws_off_partial + sizeof(float) * pl->grid_absmax);
     pl->ws_bytes = align256(pl->ws_off_ola + sizeof(float) * (size_t)d.ntiles * d.seg_len);
     if (pl->spec) {
         pl->ws_off_spec = pl->ws_bytes;
         pl->ws_bytes = align256(pl->ws_off_spec + 256 + (sizeof(SpecSrc) + sizeof(SpecBin)) * (size_t)pl->spec_cap);
+    }
+    if (pl->fused_spec) {   // [per-tile records][per-tile counts]
+        pl->ws_off_fused = pl->ws_bytes;
+        pl->ws_bytes = align256(pl->ws_off_fused + sizeof(SpecBin) * (size_t)pl->fused_cap * (size_t)d.ntiles +
+                                sizeof(int32_t) * (size_t)d.ntiles);
     }
     *out = pl;
     return SST_OK;
@@ -1052,7 +1057,8 @@ static sst_status run_fused_spec(sst_plan_t pl, const float *x, void *ws, cudaSt
     if (s != SST_OK) return s;
     SstDev df = d;
     df.spec = sb;
-    df.fused_count = reinterpret_cast<int32_t *>(sb.src);
+    df.fused_rec = reinterpret_cast<SpecBin *>((char *)ws + pl->ws_off_fused);
+    df.fused_count = reinterpret_cast<int32_t *>(df.fused_rec + (size_t)pl->fused_cap * d.ntiles);
     df.fused_cap = pl->fused_cap;
     SST_LAUNCHED_K(PK_FUSED, st, pl->kt->fused(df, pl->kind_fused, x, sc, ws_ola(pl, ws), pl->smem_fused, st),
                    "fused launch");

@@ -69,8 +69,9 @@ struct SstDev {
     SpecBuf spec;          // forward MODE_SPEC records
     // one-pass relative threshold of the path without a TFR output (k_fused;
     // null otherwise): per inverse tile, the sources between the two bounds
-    // go to spec.bin[tile * fused_cap + i] (m, l, w = S^g re, im, |S^g|^2 as
+    // go to fused_rec[tile * fused_cap + i] (m, l, w = S^g re, im, |S^g|^2 as
     // float bits, source bin) and their count to fused_count[tile]
+    SpecBin *fused_rec;
     int32_t *fused_count;
     int fused_cap;
     const float2 *twf;     // exp(2 pi i j / (z nf)), j in [0, z nf): the settling pass's phases

@@ -107,6 +107,7 @@ struct sst_plan {
     // one-pass threshold of the path without a TFR output (k_fused_settle)
     bool fused_spec = false;
     int fused_cap = 0;
+    size_t ws_off_fused = 0;
     size_t smem_settle = 0;
     std::vector<double> g64, dgs64;   // FP64 window g and s g' (basis of the tensor form)
     bool custom_window = false;       // g was supplied by the caller (not the built-in Gaussian)

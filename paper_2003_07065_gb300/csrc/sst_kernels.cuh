@@ -595,7 +595,7 @@ __device__ __forceinline__ void frame_bin(const SstDev &d, const FwdScale &fs, f
                 r.w[2] = __float_as_uint(mag2);
                 r.w[3] = (uint32_t)kk;
                 r.pad = 0;
-                d.spec.bin[(size_t)(m / d.B) * d.fused_cap + i] = r;
+                d.fused_rec[(size_t)(m / d.B) * d.fused_cap + i] = r;
             } else {
                 atomicOr(&d.spec.ctl[3], 1u);   // the gated two-pass kernels redo the call
             }
