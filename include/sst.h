@@ -222,8 +222,11 @@ sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, f
                                float *xhat_dev, void *workspace_dev, void *stream);
 
 /* End-to-end variant with host buffers: copies x_host (n floats, ideally
- * pinned) into x_dev, runs sst_forward_inverse, copies xhat_dev back into
- * xhat_host, and synchronises `stream` before returning. */
+ * pinned) into x_dev, runs sst_forward_inverse (xhat_dev written as there)
+ * and delivers the reconstruction into xhat_host: where xhat_host is
+ * page-locked memory the device can address, the finalising kernel stores
+ * it there directly, else it is copied from xhat_dev after the kernel.
+ * Synchronises `stream` before returning. */
 sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host, int64_t n,
                                     float *xhat_host, float *x_dev, float *tfr_dev,
                                     float *xhat_dev, void *workspace_dev, void *stream);

@@ -285,6 +285,18 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
         xhat[p] = finalize_value(d, partial, p);
 }
 
+// The same, also storing every sample into a second buffer: page-locked host
+// memory the device addresses directly (the end-to-end call's output, which
+// then needs no copy of its own after the kernel).
+__global__ void k_finalize_to(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat,
+                              float *__restrict__ xhat2) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d.n; p += (int64_t)gridDim.x * blockDim.x) {
+        const float v = finalize_value(d, partial, p);
+        xhat[p] = v;
+        xhat2[p] = v;
+    }
+}
+
 // xhat[p - p0] for p in [p0, p1) (one part of a split signal)
 __global__ void k_finalize_range(SstDev d, const float *__restrict__ partial, float *__restrict__ xhat, int64_t p0,
                                  int64_t p1) {
@@ -990,8 +1002,25 @@ static sst_status run_forward(sst_plan_t pl, const float *x, float *tfr, void *w
 }
 
 
+// xhat[p] (and xhat2[p], if not null) from the overlap-add partials
+static sst_status launch_finalize(sst_plan_t pl, float *xhat, float *xhat2, void *ws, cudaStream_t st) {
+    int64_t blocks = (pl->d.n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (xhat2) {
+        SST_LAUNCHED_K(PK_FINALIZE, st,
+                       (k_finalize_to<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat, xhat2),
+                        cudaGetLastError()),
+                       "finalize launch");
+    } else {
+        SST_LAUNCHED_K(PK_FINALIZE, st,
+                       (k_finalize<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat), cudaGetLastError()),
+                       "finalize launch");
+    }
+    return SST_OK;
+}
+
 static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void *ws, cudaStream_t st,
-                              const int32_t *zone = nullptr, int zone_hw = 0) {
+                              const int32_t *zone = nullptr, int zone_hw = 0, float *xhat2 = nullptr) {
     SstDev d = pl->d;
     d.zone = zone;
     d.zone_hw = zone_hw;
@@ -999,13 +1028,9 @@ static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void
     d.test_withhold = pl->test_withhold.exchange(0) ? 1 : 0;
     SST_LAUNCHED_K(PK_INVERSE, st, pl->kt->inverse(d, pl->inv_kind, (const float2 *)tfr, ws_ola(pl, ws), pl->smem_inv, st),
                    "inverse launch");
-    int64_t blocks = (pl->d.n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    SST_LAUNCHED_K(PK_FINALIZE, st,
-                   (k_finalize<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat), cudaGetLastError()),
-                   "finalize launch");
-    return SST_OK;
+    return launch_finalize(pl, xhat, xhat2, ws, st);
 }
+
 
 SST_API sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *ws, void *stream) {
     sst_status s = check_call(plan, x_dev, n, ws);
@@ -1081,7 +1106,8 @@ static sst_status run_fused_spec(sst_plan_t pl, const float *x, void *ws, cudaSt
     return SST_OK;
 }
 
-static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws, cudaStream_t st) {
+static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws, cudaStream_t st,
+                            float *xhat2 = nullptr) {
     if (pl->fused_spec) {
         sst_status s = run_fused_spec(pl, x, ws, st);
         if (s != SST_OK) return s;
@@ -1092,16 +1118,12 @@ static sst_status run_fused(sst_plan_t pl, const float *x, float *xhat, void *ws
                        pl->kt->fused(pl->d, pl->kind_fused, x, ws_scalars(pl, ws), ws_ola(pl, ws), pl->smem_fused, st),
                        "fused launch");
     }
-    int64_t blocks = (pl->d.n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    SST_LAUNCHED_K(PK_FINALIZE, st,
-                   (k_finalize<<<(unsigned)blocks, 256, 0, st>>>(pl->d, ws_ola(pl, ws), xhat), cudaGetLastError()),
-                   "finalize launch");
-    return SST_OK;
+    return launch_finalize(pl, xhat, xhat2, ws, st);
 }
 
-SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
-                                       float *xhat_dev, void *ws, void *stream) {
+// sst_forward_inverse, the reconstruction also stored into xhat2 when not null
+static sst_status forward_inverse_to(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                                     float *xhat_dev, float *xhat2, void *ws, void *stream) {
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
@@ -1110,13 +1132,18 @@ SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int6
             return fail(SST_EUNSUPPORTED,
                         "no TFR output needs the fused kernel, whose %zu bytes of shared memory this plan exceeds",
                         plan->smem_fused);
-        return run_fused(plan, x_dev, xhat_dev, ws, (cudaStream_t)stream);
+        return run_fused(plan, x_dev, xhat_dev, ws, (cudaStream_t)stream, xhat2);
     }
     s = clear_status(plan, ws, (cudaStream_t)stream);
     if (s != SST_OK) return s;
     s = run_forward(plan, x_dev, tfr_dev, ws, (cudaStream_t)stream);
     if (s != SST_OK) return s;
-    return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream);
+    return run_inverse(plan, tfr_dev, xhat_dev, ws, (cudaStream_t)stream, nullptr, 0, xhat2);
+}
+
+SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
+                                       float *xhat_dev, void *ws, void *stream) {
+    return forward_inverse_to(plan, x_dev, n, tfr_dev, xhat_dev, nullptr, ws, stream);
 }
 
 SST_API sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host, int64_t n, float *xhat_host,
@@ -1125,10 +1152,21 @@ SST_API sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    // an output in page-locked memory that the device addresses is written
+    // by the finalising kernel itself (no copy after it)
+    float *direct = nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, xhat_host) == cudaSuccess) {
+        if (at.type == cudaMemoryTypeHost && at.devicePointer) direct = (float *)at.devicePointer;
+    } else {
+        (void)cudaGetLastError();   // (pageable memory: not an error)
+    }
     SST_CU(cudaMemcpyAsync(x_dev, x_host, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st), "input copy");
-    s = sst_forward_inverse(plan, x_dev, n, tfr_dev, xhat_dev, ws, stream);
+    s = forward_inverse_to(plan, x_dev, n, tfr_dev, xhat_dev, direct, ws, stream);
     if (s != SST_OK) return s;
-    SST_CU(cudaMemcpyAsync(xhat_host, xhat_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st), "output copy");
+    if (!direct)
+        SST_CU(cudaMemcpyAsync(xhat_host, xhat_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st),
+               "output copy");
     SST_CU(cudaStreamSynchronize(st), "stream synchronise");
     return SST_OK;
 }
