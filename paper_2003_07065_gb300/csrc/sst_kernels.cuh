@@ -1410,6 +1410,9 @@ __host__ __device__ __forceinline__ size_t fused_smem_bytes(size_t smem_frame, i
     o += ((size_t)8 * nbo + 15) & ~(size_t)15;     // row a
     if (cls > 0) o += mirror_bytes(nb);            // band mirrors
     o += (4 * (size_t)seg_len + 15) & ~(size_t)15; // overlap-add segment
+    // row b is read out into the frame buffer, or, where it does not fit there
+    // (small Nf with a wide band and subdivision), into a region of its own
+    if ((size_t)8 * nbo > smem_frame - 128) o += ((size_t)8 * nbo + 15) & ~(size_t)15;
     return o;
 }
 
@@ -1429,6 +1432,9 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     char *after = reinterpret_cast<char *>(rowA) + ((8 * (size_t)d.nbo + 15) & ~(size_t)15);
     float2 *mz = reinterpret_cast<float2 *>(after);
     float *seg = reinterpret_cast<float *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
+    float2 *rowT = d.nbo <= C::BUF ? buf
+                                   : reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(seg + d.seg_len) + 15) &
+                                                                ~(uintptr_t)15);
     __shared__ int ndef;   // sources recorded for the settling pass (one-pass threshold)
     if (d.gate && *d.gate == 0u) return;
     FwdScale fs = fwd_scale(d, sc, true);
@@ -1454,16 +1460,17 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, &ndef, &vmax,
                                           nullptr, mz);
         // forward of b: its row into the frame buffer (free once the frame's
-        // bins are read), then moved into the accumulators' first half
+        // bins are read; a region of its own where the row is longer than
+        // the buffer), then moved into the accumulators' first half
         if (hasb) {
-            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, buf, nullptr, b, buf, acc, tid, nullptr, &ndef, &vmax,
+            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowT, nullptr, b, buf, acc, tid, nullptr, &ndef, &vmax,
                                               nullptr, mz);
         } else {
             __syncthreads();
-            for (int l = tid; l < d.nbo; l += TPF) buf[l] = make_float2(0.f, 0.f);
+            for (int l = tid; l < d.nbo; l += TPF) rowT[l] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int l = tid; l < d.nbo; l += TPF) rowB[l] = buf[l];
+        for (int l = tid; l < d.nbo; l += TPF) rowB[l] = rowT[l];
         __syncthreads();
 
         int tap[TP::NACC];

@@ -123,6 +123,22 @@ def test_edge_cases(sst, params):
         print("one pass", stats, rel)
 
 
+@pytest.mark.parametrize("z,f_lo", [(3, 1000.0), (2, 0.0)], ids=["z3_band_to_nyquist", "z2_dc_and_nyquist"])
+def test_one_pass_settling_variants(sst, z, f_lo):
+    """The settling pass where its arithmetic differs most: a phase table of
+    z Nf = 3072 entries (z not a power of two) with a band from above DC up
+    to Nyquist, and a band holding both the DC and the Nyquist bin (weight
+    1/2); sources must actually wait for the exact threshold."""
+    w = W.ALL["chirp_fm_64k"]
+    noisy, clean = w.signal()
+    x32 = noisy.astype(np.float32)
+    params = dict(w.params(), z=z, f_lo=f_lo)
+    x1, stats, rel = one_pass_close(sst, params, x32)
+    assert stats["waiting"] > 0 and not stats["fell_back"], stats
+    _, dest = same_bits_as_two_pass(sst, params, x32)
+    print(params, stats, rel, oracle_check(params, x32, x1, dest, clean))
+
+
 def test_runup_16m_full_size(sst):
     """The benchmark's workload: a two-pass plan gives the same bits as its
     TFR path; the default (one-pass) plan stays within the reconstruction bar
