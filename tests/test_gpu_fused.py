@@ -139,6 +139,30 @@ def test_one_pass_settling_variants(sst, z, f_lo):
     print(params, stats, rel, oracle_check(params, x32, x1, dest, clean))
 
 
+LONG_ROWS = [
+    # T rows longer than the frame buffer (small Nf, wide band, z >= 3)
+    dict(n=40000, fs=16000.0, L=257, sigma=32.0, hop=8, nfft=256, f_lo=0.0, f_hi=8000.0, z=4, gamma=1e-3,
+         relative=True),
+    dict(n=30011, fs=8000.0, L=513, sigma=64.0, hop=16, nfft=512, f_lo=500.0, f_hi=4000.0, z=3, gamma=0.02,
+         relative=False),
+]
+
+
+@pytest.mark.parametrize("params", LONG_ROWS, ids=["nf256_z4_full", "nf512_z3_abs"])
+def test_rows_longer_than_frame_buffer(sst, params):
+    gen = np.random.default_rng(params["n"])
+    t = np.arange(params["n"]) / params["fs"]
+    f0, f1 = 0.2 * params["fs"] / 2, 0.7 * params["fs"] / 2
+    dur = params["n"] / params["fs"]
+    clean = np.cos(2 * np.pi * (f0 * t + 0.5 * (f1 - f0) / dur * t * t))
+    x32 = (clean + 0.2 * gen.standard_normal(params["n"])).astype(np.float32)
+    xhat, dest = same_bits_as_two_pass(sst, params, x32)
+    print(params["nfft"], params["z"], oracle_check(params, x32, xhat, dest))
+    if params["relative"]:
+        x1, stats, rel = one_pass_close(sst, params, x32)
+        print("one pass", stats, rel)
+
+
 def test_runup_16m_full_size(sst):
     """The benchmark's workload: a two-pass plan gives the same bits as its
     TFR path; the default (one-pass) plan stays within the reconstruction bar
