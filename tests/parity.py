@@ -7,7 +7,13 @@ the design notes):
                different bin, and every such pair of destinations is
                adjacent (|dl| = 1); a source kept by one side only must sit
                within 1e-5 max|V| of the threshold (or one step off the grid
-               edge)
+               edge).  Where the oracle's S^g' is given, a source whose
+               destination coordinate z (w - k_lo) + 1/2 lies within the
+               change that the STFT bar allows (both STFTs moved by 1e-5 of
+               their maxima) of an integer may land on either side: such
+               flips are the bar's own rounding and do not count against
+               the rate (a sample of fewer than 1e4 kept sources could not
+               otherwise show one)
   TFR          replay mode: the oracle re-accumulates its FP64 V with the
                GPU's destination map, and |T_gpu - T_replay| <= 1e-5 max|V|
                with no allowance, except for the sources within 1e-5 max|V|
@@ -51,9 +57,31 @@ def check_stft(V_gpu, V_or, what="V"):
     return err / scale if scale > 0 else 0.0
 
 
-def check_map(dest_gpu, dest_or, V_or, gamma, nbo):
+def edge_flips(diff, dg, do, V_or, Vd_or, omega_or, k_lo, nfft, z):
+    """The mismatches between adjacent destinations whose oracle coordinate
+    u = z (w - k_lo) + 1/2 lies within |du| of an integer, |du| the change of
+    u that the STFT bar allows: d = -(Nf / 2 pi) Im(V' / V) moves by at most
+    (Nf / 2 pi) (e max|V'| / |V| + e max|V| |V'| / |V|^2) with e = STFT_RTOL
+    (first order), plus a few FP32 roundings of the coordinate itself."""
+    both = diff & (dg >= 0) & (do >= 0) & (np.abs(dg - do) == 1)
+    if not both.any():
+        return both
+    V = np.abs(V_or)
+    c = nfft / (2 * np.pi)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dd = c * (STFT_RTOL * np.abs(Vd_or).max() / V + STFT_RTOL * V.max() * np.abs(Vd_or) / V ** 2)
+    k = np.arange(V_or.shape[1], dtype=np.float64)[None, :] + k_lo
+    u = z * (np.asarray(omega_or, dtype=np.float64) - k_lo) + 0.5
+    tol = z * dd + 4.0 * 2.0 ** -23 * z * (np.abs(k) + 1.0)
+    near = np.abs(u - np.round(u)) <= tol
+    return both & np.where(np.isfinite(near), near, False)
+
+
+def check_map(dest_gpu, dest_or, V_or, gamma, nbo, Vd_or=None, omega_or=None, k_lo=0, nfft=0, z=1):
     """Returns the boolean mask of sources whose destination differs and the
-    mismatch rate over the sources kept by either side."""
+    mismatch rate over the sources kept by either side (flips at a bin edge
+    within the STFT bar's reach not counted, where Vd_or and omega_or are
+    given)."""
     dg = np.asarray(dest_gpu, dtype=np.int64)
     do = np.asarray(dest_or, dtype=np.int64)
     kept = (dg >= 0) | (do >= 0)
@@ -62,6 +90,8 @@ def check_map(dest_gpu, dest_or, V_or, gamma, nbo):
     n_diff = int(diff.sum())
     if n_kept == 0:
         return diff, 0.0
+    if Vd_or is not None and omega_or is not None:
+        n_diff -= int(edge_flips(diff, dg, do, V_or, Vd_or, omega_or, k_lo, nfft, z).sum())
     rate = n_diff / n_kept
     assert rate <= MAP_RATE, f"map mismatch rate {rate:.2e} ({n_diff}/{n_kept})"
     both = diff & (dg >= 0) & (do >= 0)
@@ -229,7 +259,7 @@ def compare(g, r, params, clean=None, inverse_range=None):
     if params["relative"] and "maxv" in g:
         vmax = np.abs(r.V).max()
         assert abs(g["maxv"] - vmax) <= STFT_RTOL * vmax
-    _, rate = check_map(g["dest"], r.dest, r.V, r.gamma, nbo)
+    _, rate = check_map(g["dest"], r.dest, r.V, r.gamma, nbo, r.Vd, r.omega, r.k_lo, params["nfft"], params["z"])
     stats["map_rate"] = rate
     stats["tfr_replay"] = check_tfr_replay(g["T"], r.V, g["dest"], r.dest, r.gamma, nbo)
     stats["mass"] = check_mass(g["T"], r.T, r.V, g["dest"], r.dest)

@@ -116,3 +116,54 @@ def test_moved_bound_covers_one_move_tightly(case):
     assert np.all(delta <= bound * (1 + 1e-9) + 1e-15)
     j = slice(m * p["hop"] - 100, m * p["hop"] + 100)
     assert delta[j].max() >= 0.9 * bound[j].max() > 0
+
+
+def edge_distance(r, p):
+    """|u - round(u)| of every source and the tolerance the STFT bar allows."""
+    u = p["z"] * (r.omega - r.k_lo) + 0.5
+    V = np.abs(r.V)
+    c = p["nfft"] / (2 * np.pi)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tol = p["z"] * c * (P.STFT_RTOL * np.abs(r.Vd).max() / V + P.STFT_RTOL * V.max() * np.abs(r.Vd) / V ** 2)
+    return np.abs(u - np.round(u)), u, tol
+
+
+def test_many_moves_away_from_edges_fail_the_rate(case):
+    """Adjacent moves of loud sources far from a bin edge are not rounding:
+    more of them than the rate allows fail, with or without the oracle's
+    IF supplied."""
+    _, _, r = case
+    p = PARAMS
+    dist, _, tol = edge_distance(r, p)
+    nbo = r.T.shape[1]
+    cand = (r.dest >= 1) & (r.dest < nbo - 1) & (dist > 0.25) & (dist > 10 * np.nan_to_num(tol, nan=1.0))
+    idx = np.argwhere(cand)
+    n_kept = int((r.dest >= 0).sum())
+    n_move = int(2 * P.MAP_RATE * n_kept) + 2
+    assert len(idx) >= n_move
+    dest = r.dest.copy()
+    for m, k in idx[:n_move]:
+        dest[m, k] += 1
+    with pytest.raises(AssertionError, match="map mismatch rate"):
+        P.check_map(dest, r.dest, r.V, r.gamma, nbo, r.Vd, r.omega, r.k_lo, p["nfft"], p["z"])
+
+
+def test_flips_at_a_bin_edge_within_the_stft_bar_are_allowed(case):
+    """Sources whose destination coordinate sits within the STFT bar's reach
+    of a bin edge may land on either side: moved across the edge, they pass
+    once the oracle's IF is supplied, however many, and fail the rate without
+    it when they are more than it allows."""
+    _, _, r = case
+    p = PARAMS
+    dist, u, tol = edge_distance(r, p)
+    nbo = r.T.shape[1]
+    near = (r.dest >= 1) & (r.dest < nbo - 1) & (dist <= 0.5 * np.nan_to_num(tol, nan=0.0))
+    idx = np.argwhere(near)
+    n_kept = int((r.dest >= 0).sum())
+    assert len(idx) > P.MAP_RATE * n_kept + 1, len(idx)
+    dest = r.dest.copy()
+    for m, k in idx:   # across the nearest edge
+        dest[m, k] += 1 if u[m, k] - np.floor(u[m, k]) > 0.5 else -1
+    P.check_map(dest, r.dest, r.V, r.gamma, nbo, r.Vd, r.omega, r.k_lo, p["nfft"], p["z"])
+    with pytest.raises(AssertionError, match="map mismatch rate"):
+        P.check_map(dest, r.dest, r.V, r.gamma, nbo)
