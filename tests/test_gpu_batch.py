@@ -131,3 +131,26 @@ def test_batch_submit_one_shot(sst):
         sst.sst_batch_submit(items, ws, nbytes - 256)
     for pl in plans:
         pl.close()
+
+
+def test_batch_of_the_sweep_shapes(sst):
+    """The 32 plan shapes of the plan-shape sweep in one batch (a mix of
+    Nf 128 .. 2048, z 1 .. 4, quarter, half and folded windows, absolute and
+    relative thresholds): every channel carries the same bits as its
+    single-plan call."""
+    from test_gpu_sweep import SHAPES, signal as sweep_signal
+    plans, xs, refs = [], [], []
+    for i, p in enumerate(SHAPES):
+        pl = sst.Plan(**p, two_pass=True)
+        x = torch.from_numpy(sweep_signal(p, 100 + i)).cuda()
+        t, xh = pl.forward_inverse(x)
+        plans.append(pl)
+        xs.append(x)
+        refs.append((t.clone(), xh.clone()))
+    torch.cuda.synchronize()
+    outs, _, _ = run_batch(sst, plans, xs, graph=False)
+    for i, ((t, xh), (tr, xr)) in enumerate(zip(outs, refs)):
+        assert torch.equal(t, tr), f"shape {i}: TFR differs"
+        assert torch.equal(xh, xr), f"shape {i}: reconstruction differs"
+    for pl in plans:
+        pl.close()

@@ -134,3 +134,24 @@ def test_split_absolute_threshold_and_more_parts_than_tiles(sst):
     got, lays = run_split(sst, q, x40, 7)
     assert sum(1 for lay in lays if lay["tile_end"] == lay["tile_begin"]) == 4
     assert torch.equal(got, unsplit(sst, q, x40))
+
+
+def sweep_shapes():
+    from test_gpu_sweep import SHAPES, signal
+    return [(i, SHAPES[i], signal) for i in range(0, len(SHAPES), 4)]
+
+
+@pytest.mark.parametrize("case", sweep_shapes(), ids=lambda c: f"shape{c[0]}_nf{c[1]['nfft']}_z{c[1]['z']}")
+def test_split_sweep_shapes(sst, case):
+    """Every fourth shape of the plan-shape sweep, split in two and three:
+    the same bits as unsplit (where the plan's fused kernel fits)."""
+    i, p, signal = case
+    x32 = signal(p, 100 + i)
+    try:
+        ref = unsplit(sst, p, x32)
+    except sst.SstError as e:
+        assert e.status == 6
+        pytest.skip("fused kernel does not fit this plan")
+    for parts in (2, 3):
+        got, _ = run_split(sst, p, x32, parts)
+        assert torch.equal(got, ref), (parts, (got - ref).abs().max().item())
