@@ -207,3 +207,19 @@ def test_second_order_rejects_supplied_window(sst):
         plan.forward2(x)
     assert e.value.status == 6
     plan.close()
+
+
+def sweep_cases():
+    from test_gpu_sweep import SHAPES, signal
+    return [(i, SHAPES[i], signal) for i in range(1, len(SHAPES), 5)]
+
+
+@pytest.mark.parametrize("case", sweep_cases(), ids=lambda c: f"shape{c[0]}_nf{c[1]['nfft']}_z{c[1]['z']}")
+def test_second_order_sweep_shapes(sst, case):
+    """Every fifth shape of the plan-shape sweep through the second-order
+    path, against the oracle's, with the bars above."""
+    i, params, signal = case
+    x32 = signal(params, 100 + i)
+    g = run(sst, params, x32)
+    stats, _ = check(params, x32, g)
+    print(params, stats)
