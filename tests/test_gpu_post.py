@@ -218,3 +218,28 @@ def test_post_argument_checks(sst):
     with pytest.raises(sst.SstError):
         plan.inverse_zone(plan.new_tfr(), torch.zeros(plan.frames, dtype=torch.int32, device="cuda"), -1)
     plan.close()
+
+
+def post_sweep_cases():
+    from test_gpu_sweep import SHAPES, signal
+    return [(i, SHAPES[i], signal) for i in range(2, len(SHAPES), 5)]
+
+
+@pytest.mark.parametrize("case", post_sweep_cases(), ids=lambda c: f"shape{c[0]}_nf{c[1]['nfft']}_z{c[1]['z']}")
+def test_zone_inverse_sweep_shapes(sst, case):
+    """Every fifth shape of the plan-shape sweep through the zone inverse
+    (oracle T in, zone half-width 3), against the oracle's."""
+    i, p, signal = case
+    x = signal(p, 100 + i)
+    r = O.sst(x.astype(np.float64), p["fs"], p["L"], p["sigma"], p["hop"], p["nfft"], p["f_lo"], p["f_hi"],
+              p["z"], p["gamma"], p["relative"])
+    plan = sst.Plan(**p)
+    F, nbo = r.T.shape
+    ridge = _zone_centres(F, nbo, seed=i)
+    g, _ = O.window(p["L"], p["sigma"])
+    want = O.zone_inverse(r.T, ridge, 3, r.k_lo, p["nfft"], p["z"], g, p["hop"], p["n"])
+    got = plan.inverse_zone(_to_gpu(r.T), torch.from_numpy(ridge).cuda(), 3).cpu().numpy().astype(np.float64)
+    plan.close()
+    full = np.abs(O.inverse(r.T, r.k_lo, p["nfft"], p["z"], g, p["hop"], p["n"])).max()
+    err = np.abs(got - want).max()
+    assert err <= XHAT_RTOL * full + 1e-7 * max(np.abs(want).max(), 1e-30), (err, full)
