@@ -311,3 +311,24 @@ def test_bounded_wait_reports_timeout(sst):
     torch.cuda.synchronize()
     assert torch.equal(V0, V1)
     plan.close()
+
+
+def tc_sweep_cases():
+    from test_gpu_sweep import SHAPES, signal
+    return [(i, SHAPES[i], signal) for i in range(3, len(SHAPES), 6)]
+
+
+@pytest.mark.parametrize("case", tc_sweep_cases(), ids=lambda c: f"shape{c[0]}_nf{c[1]['nfft']}_z{c[1]['z']}")
+def test_sweep_shapes_bf16x3(sst, case):
+    """Shapes of the plan-shape sweep through the tensor band form (BF16 hi +
+    lo), against the oracle with the form's bounds (a plan the form rejects
+    is skipped)."""
+    i, params, signal = case
+    x32 = signal(params, 100 + i)
+    r = oracle_of(params, x32)
+    try:
+        g = run_tc(sst, params, x32, "bf16x3")
+    except sst.SstError as e:
+        pytest.skip(f"tensor form rejects this plan: {e}")
+    st = check_form(g, r, params, x32.astype(np.float64), "bf16x3")
+    print(params, {k: (f"{v:.3e}" if isinstance(v, float) else v) for k, v in st.items()})
