@@ -1379,7 +1379,11 @@ __global__ void k_finalize(SstDev d, const float *__restrict__ partial, float *_
 // tile's segment (Eq. 26; k_finalize sums segments and applies 1 / D).  T
 // never reaches global memory.  Shared memory: the frame buffer, the T
 // accumulators (whose first half holds row b while the pair is inverted), row
-// a, the band mirrors (CLS > 0) and the segment.
+// a, the band mirrors (CLS > 0), the segment and, where row b is longer than
+// the frame buffer, the region it is read out into.  With the one-pass
+// threshold (d.fused_count set) the sources between the two bounds are
+// recorded per tile instead of accumulated (k_fused_settle adds the kept ones
+// later) and the exact max |S^g|^2 goes to d.spec.ctl[0].
 // ---------------------------------------------------------------------------
 template <int NF, bool NARROW, int CLS>
 __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 *__restrict__ rowA,
