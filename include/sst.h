@@ -53,6 +53,11 @@ typedef enum {
     SST_EINTERNAL = 7      /* internal invariant violated */
 } sst_status;
 
+/* The longest window a plan takes (L = 2M + 1; any L up to it, longer than
+ * nfft or not: the forward folds the window modulo nfft, exact by Eq. 8, and
+ * the inverse evaluates Eq. 25 at every tap |n| <= M). */
+#define SST_MAX_L 8193
+
 /* flags */
 #define SST_GAMMA_RELATIVE 0x1u  /* gamma is a fraction of max|V| over all frames and in-band bins */
 /* Relative plans only: find max|V| in a separate full pass before the forward
@@ -70,7 +75,7 @@ typedef struct sst_plan *sst_plan_t;
 typedef struct {
     int64_t n;          /* signal length N (samples), >= 1 */
     double fs;          /* sample rate in Hz (maps the band to bins, Eq. 12) */
-    int32_t L;          /* odd window length L = 2M + 1, 1 < L <= nfft + 1 */
+    int32_t L;          /* odd window length L = 2M + 1, 1 < L <= SST_MAX_L; L > nfft is folded (Eq. 8) */
     double sigma;       /* Gaussian sigma in samples (Sec. 2.1), used when g == NULL */
     const double *g;    /* optional host window g[j], j = -M..M (L values), or NULL */
     const double *dg;   /* optional host derivative window g'[j] (Sec. 2.2); both or neither */

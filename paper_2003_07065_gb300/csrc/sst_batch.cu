@@ -188,6 +188,7 @@ sst_status build_items(sst_batch *b) {
     for (int c = 0; c < nch; ++c) {
         const SstDev &d = b->ch[c].d;
         by_inv[{d.nf, d.L <= d.nf / 2 + 1 ? kind_cls(KIND_B_INV, class_of(d, table_for_nf(d.nf)))
+                      : d.L > d.nf + 1    ? KIND_B_INV_LONG
                                           : KIND_B_INV_WIDE}].push_back(c);
     }
     for (auto &kv : by_inv) {
@@ -315,7 +316,7 @@ sst_status enqueue_all(sst_batch *b, void *ws, cudaStream_t st, bool count) {
     if (s != SST_OK) return s;
     s = enqueue_phase(b, st, part, count, [](int k) {
         const int base = k & ((1 << KIND_CLS_SHIFT) - 1);
-        return base == KIND_B_INV || base == KIND_B_INV_WIDE;
+        return base == KIND_B_INV || base == KIND_B_INV_WIDE || base == KIND_B_INV_LONG;
     });
     if (s != SST_OK) return s;
     const int grid = (int)std::min<size_t>(std::max<size_t>(b->fin.size(), 1), (size_t)b->nsm * 8);

@@ -381,8 +381,7 @@ static sst_status validate(const sst_params *p) {
     if (p->nfft < 64 || p->nfft > 8192 || (p->nfft & (p->nfft - 1)))
         return fail(SST_EINVAL, "nfft must be a power of two in [64, 8192] (got %d)", p->nfft);
     if (p->L < 3 || (p->L % 2) == 0) return fail(SST_EINVAL, "L must be odd and >= 3 (got %d)", p->L);
-    if (p->L > p->nfft + 1)
-        return fail(SST_EUNSUPPORTED, "L = %d exceeds nfft + 1 = %d", p->L, p->nfft + 1);
+    if (p->L > SST_MAX_L) return fail(SST_EINVAL, "L must be <= %d (got %d)", SST_MAX_L, p->L);
     const int M = (p->L - 1) / 2;
     if (p->hop < 1 || p->hop > M) return fail(SST_EINVAL, "hop must be in [1, M = %d] (got %d)", M, p->hop);
     if (!(p->f_lo >= 0.0) || !(p->f_hi > p->f_lo) || p->f_hi > p->fs / 2 * (1 + 1e-12))
@@ -650,7 +649,8 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
     // part of the radix-16 first pass empty
     const int bcls = band_class(nf, kt->r1, (int)k_hi);
     const bool half_window = L <= nf / 2 + 1;
-    pl->inv_kind = half_window ? kind_cls(KIND_INV, bcls) : KIND_INV_WIDE;
+    const bool long_window = L > nf + 1;   // taps wrap more than once around the sub-grid transforms
+    pl->inv_kind = half_window ? kind_cls(KIND_INV, bcls) : long_window ? KIND_INV_LONG : KIND_INV_WIDE;
     pl->kind_fwd_t = kind_cls(KIND_FWD_T, half_window ? bcls : 0);
     pl->kind_fwd_spec = kind_cls(KIND_FWD_SPEC, half_window ? bcls : 0);
     if (half_window && bcls > 0) pl->smem_fwd_t += mirror_bytes(nb);
@@ -677,7 +677,7 @@ SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
         return (int)std::max<int64_t>(g_, 1);
     };
     // fused forward + inverse: the plan supports it where its shared memory fits
-    pl->kind_fused = half_window ? kind_cls(KIND_FUSED, bcls) : KIND_FUSED_WIDE;
+    pl->kind_fused = half_window ? kind_cls(KIND_FUSED, bcls) : long_window ? KIND_FUSED_LONG : KIND_FUSED_WIDE;
     pl->smem_fused = fused_smem_bytes(kt->smem_frame, nb, nbo, d.seg_len, half_window ? bcls : 0);
     pl->fused_ok = pl->smem_fused <= smax && raise_smem(kt, pl->kind_fused, pl->smem_fused) == cudaSuccess;
     pl->grid_absmax = grid_for(kind_cls(KIND_ABSMAX, pl->absmax_cls), pl->smem_absmax, (F + 3) / 4);

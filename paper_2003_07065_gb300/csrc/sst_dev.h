@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sst.h"
+
 namespace sst {
 
 // Records of the one-pass relative threshold (run_forward_spec in

@@ -68,11 +68,13 @@ const void *kernel_of(int kind) {
             if (cls == 2) return (const void *)k_inverse<NF, true, CLS2>;
             return (const void *)k_inverse<NF, true>;
         case KIND_INV_WIDE: return (const void *)k_inverse<NF, false>;
+        case KIND_INV_LONG: return (const void *)k_inverse<NF, false, CLS_LONG>;
         case KIND_FUSED:
             if (cls == 1) return (const void *)k_fused<NF, true, CLS1>;
             if (cls == 2) return (const void *)k_fused<NF, true, CLS2>;
             return (const void *)k_fused<NF, true, 0>;
         case KIND_FUSED_WIDE: return (const void *)k_fused<NF, false, 0>;
+        case KIND_FUSED_LONG: return (const void *)k_fused<NF, false, CLS_LONG>;
         case KIND_B_ABSMAX: return (const void *)k_absmax_batch<NF>;
         case KIND_B_FWD:
             if (cls == 1) return (const void *)k_forward_batch<NF, CLS1>;
@@ -83,6 +85,7 @@ const void *kernel_of(int kind) {
             if (cls == 2) return (const void *)k_inverse_batch<NF, true, CLS2>;
             return (const void *)k_inverse_batch<NF, true>;
         case KIND_B_INV_WIDE: return (const void *)k_inverse_batch<NF, false>;
+        case KIND_B_INV_LONG: return (const void *)k_inverse_batch<NF, false, CLS_LONG>;
     }
     return nullptr;
 }
@@ -157,6 +160,8 @@ cudaError_t inverse(const SstDev &d, int kind, const float2 *T, float *partial, 
         k_inverse<NF, true><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
     else if (kind == KIND_INV_WIDE)
         k_inverse<NF, false><<<(unsigned)d.ntiles, C::TPF, smem, st>>>(d, T, partial);
+    else if (kind == KIND_INV_LONG)
+        k_inverse<NF, false, CLS_LONG><<<grid, C::TPF, smem, st>>>(d, T, partial);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -173,6 +178,8 @@ cudaError_t fused(const SstDev &d, int kind, const float *x, const SstScalars *s
         k_fused<NF, true, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
     else if (kind == KIND_FUSED_WIDE)
         k_fused<NF, false, 0><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
+    else if (kind == KIND_FUSED_LONG)
+        k_fused<NF, false, CLS_LONG><<<grid, C::TPF, smem, st>>>(d, x, sc, partial);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -194,6 +201,7 @@ cudaError_t batch(int kind, const BatchChan *ch, const BatchItem *items, int nit
             else k_inverse_batch<NF, true><<<grid, C::TPF, smem, st>>>(ch, items, nitems);
             break;
         case KIND_B_INV_WIDE: k_inverse_batch<NF, false><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
+        case KIND_B_INV_LONG: k_inverse_batch<NF, false, CLS_LONG><<<grid, C::TPF, smem, st>>>(ch, items, nitems); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

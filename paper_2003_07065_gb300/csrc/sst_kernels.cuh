@@ -1215,11 +1215,52 @@ __device__ __forceinline__ void inverse_accumulate(const SstDev &d, float2 (&rac
     }
 }
 
+// The inverse and fused kernels' class for a window longer than NF + 1: no
+// pruning, and the taps go through inverse_long_sub (NARROW false).
+constexpr int CLS_LONG = -1;
+
+// Sub-grid s of a pair for a window longer than NF + 1 (Eq. 25 at every tap
+// n in [-M, M]).  Tap n reads output q = n mod NF of each sub-grid, so thread
+// tid's 16 outputs q = tid + r NF/16 serve the taps n = q + w NF inside the
+// window, any number of them per q; a Horner accumulator per tap would take
+// about 16 L / NF complex registers, so instead each sub-grid's term
+// (g[n] / NF) exp(i 2 pi s n / (z NF)) v_s[q] goes straight into the
+// segment: its real part at frame a's taps, then, after a barrier, its
+// imaginary part at frame b's.  Every sample's sum runs over the sub-grids
+// in descending order, frame a before frame b, whatever the thread count.
+// All threads take the barrier; callers order the next frame-a stores
+// behind this call's frame-b stores with a barrier of their own.
+template <int NF>
+__device__ __forceinline__ void inverse_long_sub(const SstDev &d, float *seg, int oa, bool hasb,
+                                                 const float2 (&v)[16], int s, int tid, bool live) {
+    constexpr int NS = NF / 16;
+    const int G = d.z * NF;
+    const float cnorm = 1.0f / (float)NF;
+    for (int f = 0; f < 2; ++f) {
+        if (f == 1) __syncthreads();
+        if (!live || (f == 1 && !hasb)) continue;
+        const int o = oa + f * d.hop;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int q = tid + r * NS;
+            for (int n = q - NF * ((q + d.M) / NF); n <= d.M; n += NF) {
+                float2 c = v[r];
+                if (s > 0) {
+                    int k = (s * n) % G;
+                    if (k < 0) k += G;
+                    c = cmul(__ldg(&d.twf[k]), c);
+                }
+                seg[o + n] += (__ldg(&d.g[n + d.M]) * cnorm) * (f ? c.y : c.x);
+            }
+        }
+    }
+}
+
 // One inverse tile; smem4 is the kernel's dynamic shared memory.  Ends with a
 // barrier-free write of the tile's segment (callers looping over tiles sync
 // before the next tile zeroes the segment).  CLS: band class (see
-// band_class); the spectrum inputs at other positions are not formed.  SMEMD:
-// d lives in shared memory (batches; see inverse_weights).
+// band_class), or CLS_LONG; the spectrum inputs at other positions are not
+// formed.  SMEMD: d lives in shared memory (batches; see inverse_weights).
 template <int NF, bool NARROW, int CLS = 0, bool SMEMD = false>
 __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__restrict__ T, float *__restrict__ partial,
                                              int64_t tile, float4 *smem4, int tid) {
@@ -1244,9 +1285,11 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
     const float2 *tile_rows = T + (size_t)m0 * d.nbo;
     bool async = d.trow_cap == 0 && m0 + d.B <= d.F && (reinterpret_cast<uintptr_t>(tile_rows) & 15) == 0;
 
+    constexpr bool LONGW = CLS == CLS_LONG;
+    constexpr int PC = LONGW ? 0 : CLS;   // pruning class
     int tap[TP::NACC];
     float2 om[TP::NACC];
-    inverse_taps<NF, NARROW>(d, tid, tap, om);
+    if constexpr (!LONGW) inverse_taps<NF, NARROW>(d, tid, tap, om);
 
     for (int i = tid; i < d.seg_len; i += TPF) seg[i] = 0.f;
     if (async && tid == 0) {
@@ -1310,7 +1353,7 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             const float2 *Ta = Tst + (async ? s : s * nq), *Tam = Tst + (async ? sb : sb * nq);
             const float2 *Tb = Tst + (async ? d.nbo + s : (d.z + s) * nq);
             const float2 *Tbm = Tst + (async ? d.nbo + sb : (d.z + sb) * nq);
-            inverse_first_pass<NF, CLS>(d, Ta, Tam, Tb, Tbm, qstride, s, buf, tid);
+            inverse_first_pass<NF, PC>(d, Ta, Tam, Tb, Tbm, qstride, s, buf, tid);
             __syncthreads();
             // the pair's rows are read for the last time above: fetch the next pair's
             if (async && s == 0 && tid == 0 && 2 * (pr + 1) < d.B) {
@@ -1320,11 +1363,16 @@ __device__ __forceinline__ void inverse_tile(const SstDev &d, const float2 *__re
             fft_mid<NF, TPF, true>(buf, d.tw, tid);
             float2 v[16];
             fft_out<NF, TPF, true>(buf, d.tw, tid, v);
-            if (live) inverse_accumulate<NF, NARROW>(d, racc, v, om, tap, tid, s == d.z - 1);
+            if constexpr (LONGW)
+                inverse_long_sub<NF>(d, seg, (int)(a - m0) * d.hop + d.M, hasb, v, s, tid, live);
+            else if (live)
+                inverse_accumulate<NF, NARROW>(d, racc, v, om, tap, tid, s == d.z - 1);
         }
         // overlap-add a, then b (ascending frame order at every sample)
         const int oa = (int)(a - m0) * d.hop + d.M;
-        if constexpr (SMEMD) {
+        if constexpr (LONGW) {
+            (void)oa;   // (added sub-grid by sub-grid above)
+        } else if constexpr (SMEMD) {
             float gw[TP::NACC];
             inverse_weights<NF, NARROW>(d, tap, gw);
             inverse_ola_w<NARROW, false>(seg, oa, tap, gw, racc);
@@ -1407,6 +1455,27 @@ __device__ __forceinline__ void inverse_pair_rows(const SstDev &d, const float2 
     }
 }
 
+// The pair's sub-grid inverses for a window longer than NF + 1, added to the
+// segment as they come (inverse_long_sub).
+template <int NF>
+__device__ __forceinline__ void inverse_pair_rows_long(const SstDev &d, const float2 *__restrict__ rowA,
+                                                       const float2 *__restrict__ rowB, float2 *buf, int tid,
+                                                       float *seg, int oa, bool hasb) {
+    using C = Cfg<NF>;
+    constexpr int TPF = C::TPF;
+    constexpr int NS = NF / 16;
+    const bool live = (TPF == NS) || tid < NS;
+    for (int s = d.z - 1; s >= 0; --s) {
+        const int sb = (s == 0) ? 0 : d.z - s;
+        inverse_first_pass<NF, 0>(d, rowA + s, rowA + sb, rowB + s, rowB + sb, d.z, s, buf, tid);
+        __syncthreads();
+        fft_mid<NF, TPF, true>(buf, d.tw, tid);
+        float2 v[16];
+        fft_out<NF, TPF, true>(buf, d.tw, tid, v);
+        inverse_long_sub<NF>(d, seg, oa, hasb, v, s, tid, live);
+    }
+}
+
 // bytes of the fused kernel's shared memory (layout in k_fused)
 __host__ __device__ __forceinline__ size_t fused_smem_bytes(size_t smem_frame, int nb, int nbo, int seg_len, int cls) {
     size_t o = smem_frame;                         // frame buffer (+ slack)
@@ -1426,6 +1495,8 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     using C = Cfg<NF>;
     using TP = InvTaps<NARROW>;
     constexpr int TPF = C::TPF;
+    constexpr bool LONGW = CLS == CLS_LONG;   // a window longer than NF + 1
+    constexpr int PC = LONGW ? 0 : CLS;       // pruning class
     extern __shared__ float4 smem4[];
     const int tid = threadIdx.x;
     float2 *buf = reinterpret_cast<float2 *>(smem4);
@@ -1435,7 +1506,7 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
     float2 *rowA = reinterpret_cast<float2 *>(acc + 4 * stride);
     char *after = reinterpret_cast<char *>(rowA) + ((8 * (size_t)d.nbo + 15) & ~(size_t)15);
     float2 *mz = reinterpret_cast<float2 *>(after);
-    float *seg = reinterpret_cast<float *>(after + (CLS > 0 ? mirror_bytes(d.nb) : 0));
+    float *seg = reinterpret_cast<float *>(after + (PC > 0 ? mirror_bytes(d.nb) : 0));
     float2 *rowT = d.nbo <= C::BUF ? buf
                                    : reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(seg + d.seg_len) + 15) &
                                                                 ~(uintptr_t)15);
@@ -1461,14 +1532,14 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         if (a >= d.F) break;
         const bool hasb = b < d.F;
         // forward of a: its row into rowA (the accumulators are cleared on the way)
-        forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, &ndef, &vmax,
-                                          nullptr, mz);
+        forward_frame<NF, MODE_TROW, PC>(d, x, fs, rowA, nullptr, a, buf, acc, tid, nullptr, &ndef, &vmax,
+                                         nullptr, mz);
         // forward of b: its row into the frame buffer (free once the frame's
         // bins are read; a region of its own where the row is longer than
         // the buffer), then moved into the accumulators' first half
         if (hasb) {
-            forward_frame<NF, MODE_TROW, CLS>(d, x, fs, rowT, nullptr, b, buf, acc, tid, nullptr, &ndef, &vmax,
-                                              nullptr, mz);
+            forward_frame<NF, MODE_TROW, PC>(d, x, fs, rowT, nullptr, b, buf, acc, tid, nullptr, &ndef, &vmax,
+                                             nullptr, mz);
         } else {
             __syncthreads();
             for (int l = tid; l < d.nbo; l += TPF) rowT[l] = make_float2(0.f, 0.f);
@@ -1477,16 +1548,20 @@ k_fused(SstDev d, const float *__restrict__ x, const SstScalars *__restrict__ sc
         for (int l = tid; l < d.nbo; l += TPF) rowB[l] = rowT[l];
         __syncthreads();
 
-        int tap[TP::NACC];
-        float2 om[TP::NACC];
-        inverse_taps<NF, NARROW>(d, tid, tap, om);
-        float2 racc[TP::NACC];
-        inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, tap, om, racc);
-        // overlap-add a, then b (ascending frame order at every sample)
-        const int oa = (int)(a - m0) * d.hop + d.M;
-        inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
-        __syncthreads();
-        if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
+        if constexpr (LONGW) {
+            inverse_pair_rows_long<NF>(d, rowA, rowB, buf, tid, seg, (int)(a - m0) * d.hop + d.M, hasb);
+        } else {
+            int tap[TP::NACC];
+            float2 om[TP::NACC];
+            inverse_taps<NF, NARROW>(d, tid, tap, om);
+            float2 racc[TP::NACC];
+            inverse_pair_rows<NF, NARROW, CLS>(d, rowA, rowB, buf, tid, tap, om, racc);
+            // overlap-add a, then b (ascending frame order at every sample)
+            const int oa = (int)(a - m0) * d.hop + d.M;
+            inverse_ola<NF, NARROW, false>(d, seg, oa, tap, racc);
+            __syncthreads();
+            if (hasb) inverse_ola<NF, NARROW, true>(d, seg, oa + d.hop, tap, racc);
+        }
         // the accumulators' first half held row b: clear it for the next pair
         // (ordered before its atomics by the barriers inside the next forward)
         for (int i = tid; i < 2 * stride; i += TPF) acc[i] = 0u;
@@ -1519,7 +1594,7 @@ __device__ __forceinline__ void load_chan(SstDev &sd, const BatchChan *__restric
 // against a corrupt table: such items are skipped)
 template <int NF> __device__ __forceinline__ bool chan_ok(const SstDev &d) {
     return d.nf == NF && d.z >= 1 && d.z <= 16 && d.B >= 2 && d.B <= (1 << 20) && d.hop >= 1 && d.L >= 3 &&
-           d.L <= NF + 1 && d.n >= 1 && d.F >= 1 && d.nbo >= 1 && d.nb >= 1 && d.seg_len >= d.L;
+           d.L <= SST_MAX_L && d.n >= 1 && d.F >= 1 && d.nbo >= 1 && d.nb >= 1 && d.seg_len >= d.L;
 }
 
 template <int NF>
@@ -1550,10 +1625,13 @@ k_absmax_batch(const BatchChan *__restrict__ ch, const BatchItem *__restrict__ i
 }
 
 // a channel the kernels of pruning class CLS may run: a half-length window
-// and a band of class 1 .. CLS (class 1's positions are a subset of class 2's)
+// and a band of class 1 .. CLS (class 1's positions are a subset of class 2's);
+// CLS_LONG: a window longer than NF + 1
 template <int NF, int CLS> __device__ __forceinline__ bool class_ok(const SstDev &d) {
     if constexpr (CLS == 0) {
         return true;
+    } else if constexpr (CLS == CLS_LONG) {
+        return d.L > NF + 1;
     } else {
         const int c = band_class(NF, FftPlan<NF>::R1, d.k_hi);
         return d.L <= NF / 2 + 1 && c >= 1 && c <= CLS;

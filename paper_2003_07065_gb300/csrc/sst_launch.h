@@ -12,7 +12,9 @@ namespace sst {
 enum { KIND_ABSMAX = 0, KIND_FWD_T = 1, KIND_FWD_STFT = 2, KIND_FWD_MAP = 3, KIND_INV = 4, KIND_INV_WIDE = 5,
        KIND_B_ABSMAX = 6, KIND_B_FWD = 7, KIND_B_INV = 8, KIND_B_INV_WIDE = 9, KIND_FWD_SPEC = 10,
        KIND_FUSED = 11, KIND_FUSED_WIDE = 12, KIND_FWD_TA = 13, KIND_FWD_SPECA = 14, KIND_FWD_SO_T = 15,
-       KIND_FWD_SO_MAP = 16, KIND_COUNT = 17 };
+       KIND_FWD_SO_MAP = 16, KIND_INV_LONG = 17, KIND_FUSED_LONG = 18, KIND_B_INV_LONG = 19, KIND_COUNT = 20 };
+// KIND_*_LONG: a window longer than nf + 1 (the inverse, fused and batched
+// inverse kernels of class CLS_LONG).
 // KIND_FWD_SO_T / KIND_FWD_SO_MAP: the second-order forward (k_forward_so).
 // KIND_FWD_TA / KIND_FWD_SPECA: the forward with its accumulators in the frame
 // buffer (k_forward_alias), pruning classes 1 and 2 only.
@@ -38,10 +40,10 @@ struct KernelTable {
                           cudaStream_t st);
     cudaError_t (*forward)(const SstDev &d, int kind, const float *x, const SstScalars *sc, void *out0,
                            void *out1, int grid, size_t smem, cudaStream_t st);
-    // kind: KIND_INV (window L <= nf/2 + 1) or KIND_INV_WIDE (L <= nf + 1)
+    // kind: KIND_INV (window L <= nf/2 + 1), KIND_INV_WIDE (L <= nf + 1) or KIND_INV_LONG
     cudaError_t (*inverse)(const SstDev &d, int kind, const float2 *T, float *partial, size_t smem, cudaStream_t st);
     // fused forward + inverse over the plan's inverse tiles (kind: KIND_FUSED
-    // with its class, or KIND_FUSED_WIDE); partial is the overlap-add buffer
+    // with its class, KIND_FUSED_WIDE or KIND_FUSED_LONG); partial is the overlap-add buffer
     cudaError_t (*fused)(const SstDev &d, int kind, const float *x, const SstScalars *sc, float *partial,
                          size_t smem, cudaStream_t st);
     // batched kernels over a work-item table (kind: KIND_B_*)

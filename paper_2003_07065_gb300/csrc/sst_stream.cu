@@ -25,6 +25,11 @@ namespace {
 constexpr int kStreamB = 16;          // frames per inverse tile of a stream
 constexpr int kFwdFrames = 16;        // frames per forward work item
 
+// the batched inverse kind for a stream's window (half length, up to nf + 1, longer)
+int inv_kind_of(const SstDev &d) {
+    return d.L <= d.nf / 2 + 1 ? KIND_B_INV : d.L > d.nf + 1 ? KIND_B_INV_LONG : KIND_B_INV_WIDE;
+}
+
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -267,7 +272,7 @@ SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, f
     // kernel attributes for this stream's shapes
     const size_t smem_f = plan->kt->smem_frame + tacc_bytes(d.nbo);
     const size_t smem_i = inverse_smem_bytes(plan->kt->smem_frame, d.z, d.k_hi - d.k_lo + 1, d.seg_len);
-    const int ik = d.L <= d.nf / 2 + 1 ? KIND_B_INV : KIND_B_INV_WIDE;
+    const int ik = inv_kind_of(d);
     if (raise_smem(plan->kt, KIND_B_FWD, smem_f) != cudaSuccess || raise_smem(plan->kt, ik, smem_i) != cudaSuccess) {
         cudaFree(S.dmem);
         sst_plan_destroy(plan);
@@ -427,16 +432,16 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
         c.ola = S.ola;
         c.poff = S.p_next;
         const int nf = c.d.nf;
-        const int ik = c.d.L <= nf / 2 + 1 ? KIND_B_INV : KIND_B_INV_WIDE;
+        const int ikey = nf * 32 + inv_kind_of(c.d);   // inverse group: (nf, kernel kind)
         for (int64_t m = S.m_next; m < work[i].m_ready; m += kFwdFrames)
             fwd[nf].push_back({(int)i, 0, m, std::min<int64_t>(work[i].m_ready, m + kFwdFrames)});
-        for (int64_t t = S.t_next; t < work[i].t_ready; ++t) inv[nf * 16 + ik].push_back({(int)i, 0, t, t + 1});
+        for (int64_t t = S.t_next; t < work[i].t_ready; ++t) inv[ikey].push_back({(int)i, 0, t, t + 1});
         for (int64_t p = S.p_next; p < work[i].p_ready; p += 65536)
             fin.push_back({(int)i, 0, p, std::min<int64_t>(work[i].p_ready, p + 65536)});
         smem_f[nf] = std::max(smem_f[nf], S.plan->kt->smem_frame + tacc_bytes(c.d.nbo));
         maxnbo[nf] = std::max(maxnbo[nf], c.d.nbo);
-        smem_i[nf * 16 + ik] = std::max(smem_i[nf * 16 + ik], inverse_smem_bytes(S.plan->kt->smem_frame, c.d.z,
-                                                                                  c.d.k_hi - c.d.k_lo + 1, c.d.seg_len));
+        smem_i[ikey] = std::max(smem_i[ikey], inverse_smem_bytes(S.plan->kt->smem_frame, c.d.z, c.d.k_hi - c.d.k_lo + 1,
+                                                                  c.d.seg_len));
     }
     std::vector<BatchItem> all;
     std::vector<std::pair<size_t, size_t>> spans_f, spans_i;
@@ -477,7 +482,8 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
         count_launch();
     }
     for (size_t g = 0; g < keys_i.size(); ++g) {
-        const int nf = keys_i[g] / 16, kind = keys_i[g] % 16;
+        const int nf = keys_i[g] / 32, kind = keys_i[g] % 32;
+        if (smem_i.count(keys_i[g]) == 0) return fail(SST_EINTERNAL, "stream inverse group without its shared memory");
         const KernelTable *kt = table_for_nf(nf);
         int occ = 1;
         if (kt->occupancy(kind, smem_i[keys_i[g]], &occ) != cudaSuccess || occ < 1) occ = 1;

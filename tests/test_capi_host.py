@@ -115,10 +115,14 @@ def test_invalid_parameters_rejected_on_host(lib, change, msg):
     assert msg in str(e.value)
 
 
-def test_window_longer_than_nfft_plus_one_unsupported(lib):
+def test_window_longer_than_the_limit_rejected(lib):
+    """Any odd L up to SST_MAX_L = 8193 is valid for every nfft (a window
+    longer than nfft is folded, Eq. 8); a longer one is an argument error,
+    found before any device call."""
     with pytest.raises(lib.SstError) as e:
-        lib.sst_plan_create(n=1000, fs=1000.0, L=67, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
-    assert e.value.status == 6
+        lib.sst_plan_create(n=100000, fs=1000.0, L=8195, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
+    assert e.value.status == 1
+    assert "8193" in str(e.value)
 
 
 def test_null_arguments(lib):

@@ -107,3 +107,14 @@ def test_invalid_parameters_rejected(S):
     assert e.value.status == 1
     with pytest.raises(S.SstError):
         S.sst_params_check(n=1000, fs=1000.0, L=65, hop=8, nfft=64, f_lo=0.0, f_hi=500.0, sigma=0.0)
+
+
+def test_window_length_limit(S):
+    """Windows up to SST_MAX_L = 8193 taps are valid for every nfft (a window
+    longer than nfft is folded, Eq. 8); a longer one is an argument error."""
+    r = S.sst_params_check(n=100000, fs=8000.0, L=8193, hop=64, nfft=64, f_lo=0.0, f_hi=4000.0, sigma=1024.0)
+    assert r["hf_max_eq38"] > 0
+    S.sst_params_check(n=100000, fs=8000.0, L=67, hop=8, nfft=64, f_lo=0.0, f_hi=4000.0, sigma=8.0)
+    with pytest.raises(S.SstError) as e:
+        S.sst_params_check(n=100000, fs=8000.0, L=8195, hop=64, nfft=8192, f_lo=0.0, f_hi=4000.0, sigma=1024.0)
+    assert e.value.status == 1
