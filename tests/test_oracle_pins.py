@@ -50,11 +50,12 @@ def test_window_closed_form():
 
 
 # ------------------------------------------------------------------ STFT
-@pytest.mark.parametrize("L", [33, 65])
+@pytest.mark.parametrize("L", [33, 65, 161, 289])
 def test_stft_matches_brute_force_eq8(L):
-    """Eq. 9 (FFT, phase factor, folding for L > Nf) against Eq. 8 summed
-    directly on a tiny input."""
-    n, hop, nfft, sigma = 256, 4, 64, 6.0
+    """Eq. 9 (FFT, phase factor, folding for L > Nf, up to four and a half
+    times Nf) against Eq. 8 summed directly on a tiny input."""
+    n, hop, nfft = 256, 4, 64
+    sigma = max(6.0, (L - 1) / 4.0)   # the window's ends carry weight (e^-2)
     x = np.random.default_rng(L).standard_normal(n)
     g, dg = O.window(L, sigma)
     V, Vd = O.stft(x, g, dg, hop, nfft, 0, nfft // 2)
@@ -265,12 +266,15 @@ def test_normaliser_continuous_limit_eq22():
     np.testing.assert_allclose(D * hop, math.sqrt(2.0), rtol=1e-10)
 
 
-def test_inverse_matches_brute_force_eq25():
+@pytest.mark.parametrize("L", [49, 161, 289])
+def test_inverse_matches_brute_force_eq25(L):
     """The zNf-point zero-padded IDFT route against Eq. 25-26 summed directly
-    over the fine bins, on a tiny input, for several z."""
-    n, hop, nfft, L = 512, 8, 64, 49
+    over the fine bins, on a tiny input, for several z; windows shorter than
+    Nf and longer than zNf (taps |j| > zNf / 2, where the IDFT route reads
+    its transform periodically and the direct sum needs no period)."""
+    n, hop, nfft = 512, 8, 64
     x = np.random.default_rng(21).standard_normal(n)
-    g, dg = O.window(L, 6.0)
+    g, dg = O.window(L, max(6.0, (L - 1) / 4.0))   # long windows: ends of weight e^-2
     M = (L - 1) // 2
     for z, (k_lo, k_hi) in ((1, (0, 32)), (2, (4, 20)), (3, (0, 12)), (4, (10, 32))):
         V, Vd = O.stft(x, g, dg, hop, nfft, k_lo, k_hi)
