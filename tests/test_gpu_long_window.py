@@ -168,3 +168,36 @@ def test_long_window_tensor_form(sst, i):
     g = run_tc(sst, p, x32, "bf16x3")
     st = check_form(g, r, p, x32.astype(np.float64), "bf16x3")
     print(p, st)
+
+
+@pytest.mark.parametrize("i", [1, 4], ids=[IDS[1], IDS[4]])
+def test_long_window_second_order(sst, i):
+    """The second-order path (five STFTs packed into three FFTs, folded as the
+    first-order ones) on long windows, against the oracle's second order."""
+    from test_gpu_sst2 import check, run
+    p = LONG[i]
+    x32 = signal(p, 300 + i)
+    g = run(sst, p, x32)
+    stats, _ = check(p, x32, g)
+    print(p, stats)
+
+
+@pytest.mark.parametrize("i", [2, 6], ids=[IDS[2], IDS[6]])
+def test_long_window_zone_inverse(sst, i):
+    """The zone inverse (the oracle's T in, zone half-width 3) on long
+    windows, against the oracle's zone inverse."""
+    from test_gpu_post import _to_gpu, _zone_centres
+    p = LONG[i]
+    x = signal(p, 300 + i)
+    r = O.sst(x.astype(np.float64), p["fs"], p["L"], p["sigma"], p["hop"], p["nfft"], p["f_lo"], p["f_hi"],
+              p["z"], p["gamma"], p["relative"])
+    plan = sst.Plan(**p)
+    F, nbo = r.T.shape
+    ridge = _zone_centres(F, nbo, seed=i)
+    g, _ = O.window(p["L"], p["sigma"])
+    want = O.zone_inverse(r.T, ridge, 3, r.k_lo, p["nfft"], p["z"], g, p["hop"], p["n"])
+    got = plan.inverse_zone(_to_gpu(r.T), torch.from_numpy(ridge).cuda(), 3).cpu().numpy().astype(np.float64)
+    plan.close()
+    full = np.abs(O.inverse(r.T, r.k_lo, p["nfft"], p["z"], g, p["hop"], p["n"])).max()
+    err = np.abs(got - want).max()
+    assert err <= XHAT_RTOL * full + 1e-7 * max(np.abs(want).max(), 1e-30), (err, full)
