@@ -1042,8 +1042,9 @@ k_forward_alias(SstDev d, const float *__restrict__ x, const SstScalars *__restr
 // staged in shared memory; the spectrum build is fused into the first FFT
 // pass and the tap accumulation into the last, whose thread j holds the
 // outputs q = j + r NF/16.  NARROW (L <= NF/2 + 1) keeps the 9 accumulators of
-// r in [0, 4] and [12, 15]; otherwise all 16 plus the tap -NF/2 (which shares
-// q = NF/2 with +NF/2).  The windowed frames are overlap-added into a
+// r in [0, 4] and [12, 15]; otherwise (L <= NF + 1) all 16 plus the tap -NF/2
+// (which shares q = NF/2 with +NF/2); a longer window has no accumulators
+// (inverse_long_sub).  The windowed frames are overlap-added into a
 // shared-memory segment in ascending frame order, written to the partial
 // buffer, and k_finalize sums overlapping segments in tile order and applies
 // 1 / D[p] (Eq. 26).
