@@ -58,14 +58,22 @@ def part_job(x, parts, r, allreduce_max, exchange, relative=True, align=4):
     return p_b, O.part_finalise(received, p_b, p_e, P["L"], P["sigma"], P["hop"], N)
 
 
+# a window longer than zNf (halo M = 512 samples, the inverse's transform read
+# periodically), for the split mode's long-window case
+P_LONG = dict(fs=8000.0, L=1025, sigma=200.0, hop=16, nfft=128, f_lo=300.0, f_hi=2500.0, z=3, gamma=1e-3)
+
+
 @pytest.mark.parametrize("parts", [1, 2, 3, 4])
 @pytest.mark.parametrize("relative", [True, False])
-def test_oracle_split_equals_unsplit(parts, relative):
+@pytest.mark.parametrize("long_window", [False, True])
+def test_oracle_split_equals_unsplit(parts, relative, long_window):
     """In one process: every part's maximum first, then every part's
     numerator under the reduced threshold, then each part's samples from the
     shares of all parts (ascending)."""
+    P = P_LONG if long_window else globals()["P"]
     x = signal()
-    ref = unsplit(x, relative)
+    ref = O.sst(x, P["fs"], P["L"], P["sigma"], P["hop"], P["nfft"], P["f_lo"], P["f_hi"], P["z"], P["gamma"],
+                relative, inverse_range=(0, N)).xhat
     maxes = [0.0] * parts
     shares = [None] * parts
     F = O.frames(N, P["hop"])
@@ -184,7 +192,7 @@ def synthetic_layouts(ntiles, parts, B, hop, L, n):
 
 
 @pytest.mark.parametrize("parts", [1, 2, 3, 7])
-@pytest.mark.parametrize("B,hop,L", [(64, 32, 2049), (2, 8, 257), (6, 16, 1025)])
+@pytest.mark.parametrize("B,hop,L", [(64, 32, 2049), (2, 8, 257), (6, 16, 1025), (2, 16, 8193)])
 def test_exchange_lists_deliver_every_needed_tile_once(parts, B, hop, L):
     n = 300000
     F = -(-n // hop)
