@@ -639,9 +639,33 @@ def sst_last_error() -> str:
 
 
 # ------------------------------------------------------------------ torch helper
+def check_tensor(t, name: str, dtype, min_numel: int = 0, device=None):
+    """The checks a raw pointer cannot carry through the C ABI: t is a torch
+    tensor of element type dtype, contiguous, with at least min_numel
+    elements, on `device` (a torch.device; None: in host memory).  Raises
+    ValueError; returns t."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if device is None:
+        if t.is_cuda:
+            raise ValueError(f"{name}: expected a host tensor, got one on {t.device}")
+    elif t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}, got one on {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: has {t.numel()} elements, the call needs {min_numel}")
+    return t
+
+
 class Plan:
     """Owns a plan handle and the device buffers one signal needs (torch
-    tensors on the current device): workspace, TFR and reconstruction."""
+    tensors on the current device): workspace, TFR and reconstruction.
+    Tensor arguments are checked (element type, device, contiguity, size)
+    before their pointers are passed on."""
 
     def __init__(self, **kw):
         import torch
@@ -659,30 +683,46 @@ class Plan:
         import torch
         return torch.empty((self.frames, self.bins, 2), dtype=torch.float32, device=self.device)
 
+    # argument checks (check_tensor) for the signal, a TFR and the outputs
+    def _x(self, x, name="x"):
+        import torch
+        return check_tensor(x, name, torch.float32, self.n, self.device)
+
+    def _tfr(self, tfr):
+        import torch
+        return check_tensor(tfr, "tfr", torch.float32, 2 * self.frames * self.bins, self.device)
+
+    def _out(self, t, name, dtype, numel):
+        return check_tensor(t, name, dtype, numel, self.device)
+
     def forward(self, x, tfr=None):
-        tfr = self.new_tfr() if tfr is None else tfr
-        sst_forward(self.handle, x, self.n, tfr, self.workspace)
+        tfr = self.new_tfr() if tfr is None else self._tfr(tfr)
+        sst_forward(self.handle, self._x(x), self.n, tfr, self.workspace)
         return tfr
 
     def inverse(self, tfr, xhat=None):
         import torch
-        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
-        sst_inverse(self.handle, tfr, self.n, xhat, self.workspace)
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else \
+            self._out(xhat, "xhat", torch.float32, self.n)
+        sst_inverse(self.handle, self._tfr(tfr), self.n, xhat, self.workspace)
         return xhat
 
     def inverse_zone(self, tfr, ridge, half_width, xhat=None):
         """Component recovery: the inverse restricted to |l - ridge[m]| <= half_width."""
         import torch
-        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
-        sst_inverse_zone(self.handle, tfr, self.n, ridge, half_width, xhat, self.workspace)
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else \
+            self._out(xhat, "xhat", torch.float32, self.n)
+        self._out(ridge, "ridge", torch.int32, self.frames)
+        sst_inverse_zone(self.handle, self._tfr(tfr), self.n, ridge, half_width, xhat, self.workspace)
         return xhat
 
     def ridge(self, tfr, l_lo=0, l_hi=None, smooth=0, out=None):
         """Ridge (output bin per frame) of the component in [l_lo, l_hi]."""
         import torch
         l_hi = self.bins - 1 if l_hi is None else l_hi
-        out = torch.empty(self.frames, dtype=torch.int32, device=self.device) if out is None else out
-        sst_ridge(tfr, self.frames, self.bins, l_lo, l_hi, smooth, out)
+        out = torch.empty(self.frames, dtype=torch.int32, device=self.device) if out is None else \
+            self._out(out, "out", torch.int32, self.frames)
+        sst_ridge(self._tfr(tfr), self.frames, self.bins, l_lo, l_hi, smooth, out)
         return out
 
     def renyi(self, tfr, alpha=3.0, cell=1.0, out=None):
@@ -691,55 +731,58 @@ class Plan:
         if getattr(self, "_renyi_ws", None) is None:
             self._renyi_ws = torch.empty(max(sst_renyi_workspace_bytes(), 256), dtype=torch.uint8,
                                          device=self.device)
-        out = torch.empty(1, dtype=torch.float64, device=self.device) if out is None else out
-        sst_renyi(tfr, self.frames, self.bins, self.bins, alpha, cell, out, self._renyi_ws)
+        out = torch.empty(1, dtype=torch.float64, device=self.device) if out is None else \
+            self._out(out, "out", torch.float64, 1)
+        sst_renyi(self._tfr(tfr), self.frames, self.bins, self.bins, alpha, cell, out, self._renyi_ws)
         return out
 
     def forward_inverse(self, x, tfr=None, xhat=None):
         import torch
-        tfr = self.new_tfr() if tfr is None else tfr
-        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
-        sst_forward_inverse(self.handle, x, self.n, tfr, xhat, self.workspace)
+        tfr = self.new_tfr() if tfr is None else self._tfr(tfr)
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else \
+            self._out(xhat, "xhat", torch.float32, self.n)
+        sst_forward_inverse(self.handle, self._x(x), self.n, tfr, xhat, self.workspace)
         return tfr, xhat
 
     def reconstruct(self, x, xhat=None):
         """Forward + inverse without a TFR output (T stays on chip)."""
         import torch
-        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else xhat
-        sst_forward_inverse(self.handle, x, self.n, None, xhat, self.workspace)
+        xhat = torch.empty(self.n, dtype=torch.float32, device=self.device) if xhat is None else \
+            self._out(xhat, "xhat", torch.float32, self.n)
+        sst_forward_inverse(self.handle, self._x(x), self.n, None, xhat, self.workspace)
         return xhat
 
     def stft(self, x):
         import torch
         V = torch.empty((self.frames, self.nb, 2), dtype=torch.float32, device=self.device)
         Vd = torch.empty_like(V)
-        sst_stft(self.handle, x, self.n, V, Vd, self.workspace)
+        sst_stft(self.handle, self._x(x), self.n, V, Vd, self.workspace)
         return V, Vd
 
     def reassign_map(self, x):
         import torch
         om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
         de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
-        sst_reassign_map(self.handle, x, self.n, om, de, self.workspace)
+        sst_reassign_map(self.handle, self._x(x), self.n, om, de, self.workspace)
         return om, de
 
     def forward2(self, x, tfr=None):
         """Second-order forward (sst_forward2)."""
-        tfr = self.new_tfr() if tfr is None else tfr
-        sst_forward2(self.handle, x, self.n, tfr, self.workspace)
+        tfr = self.new_tfr() if tfr is None else self._tfr(tfr)
+        sst_forward2(self.handle, self._x(x), self.n, tfr, self.workspace)
         return tfr
 
     def reassign_map2(self, x):
         import torch
         om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
         de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
-        sst_reassign_map2(self.handle, x, self.n, om, de, self.workspace)
+        sst_reassign_map2(self.handle, self._x(x), self.n, om, de, self.workspace)
         return om, de
 
     def max_abs_v(self, x):
         import torch
         out = torch.empty(1, dtype=torch.float32, device=self.device)
-        sst_max_abs_v(self.handle, x, self.n, out, self.workspace)
+        sst_max_abs_v(self.handle, self._x(x), self.n, out, self.workspace)
         return out
 
     def close(self):
@@ -760,8 +803,8 @@ class Plan:
         return self._tc[form]
 
     def tc_forward(self, x, form: str, tfr=None):
-        tfr = self.new_tfr() if tfr is None else tfr
-        sst_tc_forward(self._tc_handle(form), x, self.n, tfr)
+        tfr = self.new_tfr() if tfr is None else self._tfr(tfr)
+        sst_tc_forward(self._tc_handle(form), self._x(x), self.n, tfr)
         sst_tc_check(self._tc_handle(form))
         return tfr
 
@@ -769,7 +812,7 @@ class Plan:
         import torch
         V = torch.empty((self.frames, self.nb, 2), dtype=torch.float32, device=self.device)
         Vd = torch.empty_like(V)
-        sst_tc_stft(self._tc_handle(form), x, self.n, V, Vd)
+        sst_tc_stft(self._tc_handle(form), self._x(x), self.n, V, Vd)
         sst_tc_check(self._tc_handle(form))
         return V, Vd
 
@@ -777,7 +820,7 @@ class Plan:
         import torch
         om = torch.empty((self.frames, self.nb), dtype=torch.float32, device=self.device)
         de = torch.empty((self.frames, self.nb), dtype=torch.int32, device=self.device)
-        sst_tc_reassign_map(self._tc_handle(form), x, self.n, om, de)
+        sst_tc_reassign_map(self._tc_handle(form), self._x(x), self.n, om, de)
         sst_tc_check(self._tc_handle(form))
         return om, de
 

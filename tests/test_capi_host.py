@@ -173,3 +173,18 @@ def test_post_steps_reject_bad_arguments_on_host(lib):
     assert L.sst_renyi(t, 10, 20, 19, 3.0, 1.0, out, ws, None) == 1   # row stride below the columns
     assert L.sst_renyi(t, 10, 20, 20, 3.0, 1.0, out, ws + 8, None) == 1   # workspace alignment
     assert L.sst_inverse_zone(None, t, 10, r, 3, out, ws, None) == 1
+
+
+def test_binding_checks_tensor_arguments():
+    """The checks a raw pointer cannot carry through the C ABI (element type,
+    device, contiguity, size), made by the binding before a call."""
+    torch = pytest.importorskip("torch")
+    from paper_2003_07065_gb300.sst import check_tensor
+    x = torch.zeros(100, dtype=torch.float32)
+    assert check_tensor(x, "x", torch.float32, 100) is x            # a host tensor where a host one is wanted
+    for bad, why in [(x.double(), "expected torch.float32"), (x[::2], "contiguous"), (x[:99], "needs 100"),
+                     (x.numpy(), "expected a torch tensor")]:
+        with pytest.raises(ValueError, match=why):
+            check_tensor(bad, "x", torch.float32, 100)
+    with pytest.raises(ValueError, match="expected a tensor on cuda:0"):
+        check_tensor(x, "x", torch.float32, 100, torch.device("cuda", 0))
