@@ -3,7 +3,9 @@ tensor-core band form's libsst_tc.so (include/sst_tc.h).
 
 Argument marshalling only: every function here forwards to the C entry point
 of the same name, passing device pointers (``tensor.data_ptr()``) and the
-``cudaStream_t`` of a torch stream.  The libraries must have been built
+``cudaStream_t`` of a torch stream (the ``Plan`` class first checks each
+tensor argument's element type, device, contiguity and size, which a raw
+pointer cannot carry).  The libraries must have been built
 (``paper_2003_07065_gb300.build.build()``, ``build.build_tc()``); loading
 fails loudly otherwise, and there is no CPU fallback.  libsst_tc.so is loaded
 only when a ``sst_tc_*`` function is first called.
