@@ -134,13 +134,15 @@ def measured_peaks() -> dict:
 
 
 def measured_traffic_per_frame(kernel: str):
-    """DRAM bytes per frame of `kernel` from the committed ncu capture
-    (profiles/dram_traffic_runup.json), or None when the kernel sources have
-    changed since the capture."""
+    """(DRAM bytes per frame of `kernel` from the committed ncu capture
+    (profiles/dram_traffic_runup.json), a note on where it comes from).  The
+    bytes are None when there is no capture or the kernel sources have
+    changed since it was taken; the note then says so and gives the
+    capture's figure for reference."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "dram_traffic_runup.json")
     if not os.path.exists(p):
-        return None
+        return None, "no ncu capture of the DRAM traffic is committed"
     with open(p) as f:
         rec = json.load(f)
     # the files that define the FFT-path kernels (device code, launch shapes)
@@ -149,9 +151,12 @@ def measured_traffic_per_frame(kernel: str):
     for name in rec.get("kernel_sources", []):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    bpf = rec["dram_bytes_per_frame"].get(kernel)
     if h.hexdigest() != rec.get("kernel_source_sha256"):
-        return None
-    return rec["dram_bytes_per_frame"].get(kernel)
+        return None, (f"null: the kernel sources changed after the committed ncu capture "
+                      f"(profiles/dram_traffic_runup.json, {bpf:.0f} B per frame then)" if bpf is not None else
+                      "null: the kernel sources changed after the committed ncu capture")
+    return bpf, "ncu dram__bytes_read+write of one runup_4m launch scaled by frames"
 
 
 def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
@@ -989,11 +994,11 @@ def main():
         sm_max = peaks.get("sm_max_mhz") or 2070.0
         nominal = fp32_peak_tflops(num_sms, sm_max)
         peak = sst.sst_fp32_peak(stream)
-        tpf = measured_traffic_per_frame(dom)
+        tpf, tnote = measured_traffic_per_frame(dom)
         step_flops = sum(fl[k] for k in ("forward", "inverse")) * units
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tpf * units if tpf is not None else None),
-                "traffic_note": "ncu dram__bytes_read+write of one runup_4m launch scaled by frames",
+                "traffic_note": tnote,
                 "peak_note": ("FP32 FMA throughput measured in this run (sst_fp32_peak: independent fmaf "
                               f"chains); nominal {nominal:.1f} = {num_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"),
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": per_launch_ms,
