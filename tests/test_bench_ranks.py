@@ -76,3 +76,29 @@ def test_oracle_baseline_sample_is_bounded():
     from paper_2003_07065_gb300 import workloads as W
     v, threads, sample, el = bench.oracle_sample_rate(W.RUNUP_16M, budget_s=0.0, n_max=1 << 12)
     assert v > 0 and threads >= 1 and "first 4096 samples of runup_16m" in sample
+
+
+def test_roofline_traffic_only_from_a_capture_of_the_current_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu capture only while the
+    kernel sources hash as they did when it was taken; otherwise it is null
+    and its note says why, with the capture's figure."""
+    import hashlib
+    import json
+    import shutil
+
+    import bench
+    csrc = tmp_path / "paper_2003_07065_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cuh").write_text("kernel v1\n")
+    rec = {"kernel_sources": ["k.cuh"], "dram_bytes_per_frame": {"inverse": 16622.5},
+           "kernel_source_sha256": hashlib.sha256(b"kernel v1\n").hexdigest()}
+    (tmp_path / "profiles" / "dram_traffic_runup.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    bpf, note = bench.measured_traffic_per_frame("inverse")
+    assert bpf == 16622.5 and "scaled by frames" in note
+    (csrc / "k.cuh").write_text("kernel v2\n")
+    bpf, note = bench.measured_traffic_per_frame("inverse")
+    assert bpf is None and note.startswith("null") and "16622" in note
+    shutil.rmtree(tmp_path / "profiles")
+    assert bench.measured_traffic_per_frame("inverse")[0] is None
