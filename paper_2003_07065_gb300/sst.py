@@ -17,6 +17,7 @@ import os
 
 from . import build as _build
 
+SST_MAX_L = 8193            # the longest window a plan takes (any Nf; longer than Nf is folded)
 SST_GAMMA_RELATIVE = 0x1
 SST_TWO_PASS = 0x2
 SST_STREAM_XHAT_ONLY = 0x100

@@ -120,9 +120,11 @@ def test_window_longer_than_the_limit_rejected(lib):
     longer than nfft is folded, Eq. 8); a longer one is an argument error,
     found before any device call."""
     with pytest.raises(lib.SstError) as e:
-        lib.sst_plan_create(n=100000, fs=1000.0, L=8195, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
+        lib.sst_plan_create(n=100000, fs=1000.0, L=lib.SST_MAX_L + 2, sigma=8.0, hop=8, nfft=64, f_lo=0, f_hi=500)
     assert e.value.status == 1
-    assert "8193" in str(e.value)
+    assert str(lib.SST_MAX_L) in str(e.value)
+    hdr = open(os.path.join(build.INCLUDE, "sst.h")).read()
+    assert re.search(r"#define SST_MAX_L (\d+)", hdr).group(1) == str(lib.SST_MAX_L)
 
 
 def test_null_arguments(lib):
