@@ -190,3 +190,20 @@ def test_binding_checks_tensor_arguments():
             check_tensor(bad, "x", torch.float32, 100)
     with pytest.raises(ValueError, match="expected a tensor on cuda:0"):
         check_tensor(x, "x", torch.float32, 100, torch.device("cuda", 0))
+
+
+def test_binding_constants_match_the_headers():
+    """Every SST_* constant the binding mirrors has the header's value, and the
+    status names follow the header's enum."""
+    from paper_2003_07065_gb300 import sst as S
+    seen = 0
+    for h in ("sst.h", "sst_tc.h"):
+        text = open(os.path.join(build.INCLUDE, h)).read()
+        for name, val in re.findall(r"#define (SST_\w+) (0x[0-9a-fA-F]+|\d+)u?\b", text):
+            if hasattr(S, name):
+                assert getattr(S, name) == int(val, 0), name
+                seen += 1
+    assert seen >= 10
+    enum = re.search(r"typedef enum \{(.*?)\} sst_status;", open(os.path.join(build.INCLUDE, "sst.h")).read(), re.S)
+    for name, val in re.findall(r"(SST_\w+) = (\d+)", enum.group(1)):
+        assert S.STATUS[int(val)] == name
