@@ -207,3 +207,25 @@ def test_binding_constants_match_the_headers():
     enum = re.search(r"typedef enum \{(.*?)\} sst_status;", open(os.path.join(build.INCLUDE, "sst.h")).read(), re.S)
     for name, val in re.findall(r"(SST_\w+) = (\d+)", enum.group(1)):
         assert S.STATUS[int(val)] == name
+
+
+def test_binding_signatures_match_the_headers(lib):
+    """Each entry point the binding declares takes as many arguments as its
+    prototype in include/sst.h or include/sst_tc.h (a wrong count would
+    misplace every argument after it)."""
+    from paper_2003_07065_gb300 import sst as S
+    protos = {}
+    for h in ("sst.h", "sst_tc.h"):
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(build.INCLUDE, h)).read(), flags=re.S)
+        for name, args in re.findall(r"\b(sst_\w+)\s*\(([^;{]*?)\)\s*;", text):
+            args = " ".join(args.split())
+            protos[name] = 0 if args in ("", "void") else args.count(",") + 1
+    tc = S.load_tc()
+    checked = 0
+    for so in (S.load(), tc):
+        for name, n in protos.items():
+            f = getattr(so, name, None)
+            if f is not None and f.argtypes is not None:
+                assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+                checked += 1
+    assert checked >= 40
