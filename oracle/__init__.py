@@ -339,8 +339,8 @@ def if2(x, L: int, sigma: float, hop: int, nfft: int, k_lo: int, k_hi: int, m0: 
         den = Vt * Vd - Vtd * V
         q = 1j * (Vd * Vd - V2 * V) / den
         w2 = np.where(np.abs(den) > IF2_MIN_DT * np.abs(V) ** 2, (wt - q * Vt / V).real, wt.real)
-    to_bins = nfft / (2 * np.pi)
-    return V, wt.real * to_bins, w2 * to_bins, q * to_bins
+        to_bins = nfft / (2 * np.pi)
+        return V, wt.real * to_bins, w2 * to_bins, q * to_bins   # (q is not finite where den = 0)
 
 
 def reassign2(V, omega2, k_lo: int, k_hi: int, z: int, gamma: float):
