@@ -153,7 +153,8 @@ def _brute_dest(omega, mag, k_lo, k_hi, z, gamma):
     return out
 
 
-@pytest.mark.parametrize("z,band", [(1, (0, 64)), (2, (10, 40)), (3, (5, 50)), (4, (0, 32))])
+@pytest.mark.parametrize("z,band", [(1, (0, 64)), (2, (10, 40)), (3, (5, 50)), (4, (0, 32)), (7, (20, 64)),
+                                    (16, (0, 64))])
 def test_reassign_brute_force(z, band):
     n, hop, nfft, L = 1024, 8, 128, 97
     x = np.random.default_rng(z).standard_normal(n)
@@ -276,7 +277,7 @@ def test_inverse_matches_brute_force_eq25(L):
     x = np.random.default_rng(21).standard_normal(n)
     g, dg = O.window(L, max(6.0, (L - 1) / 4.0))   # long windows: ends of weight e^-2
     M = (L - 1) // 2
-    for z, (k_lo, k_hi) in ((1, (0, 32)), (2, (4, 20)), (3, (0, 12)), (4, (10, 32))):
+    for z, (k_lo, k_hi) in ((1, (0, 32)), (2, (4, 20)), (3, (0, 12)), (4, (10, 32)), (7, (20, 32)), (16, (0, 32))):
         V, Vd = O.stft(x, g, dg, hop, nfft, k_lo, k_hi)
         _, _, T, _ = O.reassign(V, Vd, k_lo, k_hi, nfft, z, 0.0)
         xr = O.inverse(T, k_lo, nfft, z, g, hop, n)
