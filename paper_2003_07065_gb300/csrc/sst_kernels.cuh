@@ -434,8 +434,8 @@ __device__ __forceinline__ void spec_records(const SstDev &d, SpecFrame *sf, int
 }
 // bytes of the band's mirror values (forward kernels of class > 0)
 __host__ __device__ constexpr size_t mirror_bytes(int nb) { return (8 * (size_t)nb + 15) & ~(size_t)15; }
-// bytes of MODE_SPEC shared state
-__host__ __device__ __forceinline__ size_t spec_smem_bytes(int nbo) {
+// bytes of MODE_SPEC shared state (one SpecFrame, whatever the row length)
+__host__ __device__ __forceinline__ size_t spec_smem_bytes(int /*nbo*/) {
     return sizeof(SpecFrame);
 }
 // whether it fits in a frame buffer of buf float2 after the 2 nb band values
