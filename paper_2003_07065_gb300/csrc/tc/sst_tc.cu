@@ -811,10 +811,12 @@ float tf32_round(float v) {
     memcpy(&v, &u, 4);
     return v;
 }
+// a BF16 bit pattern's value: BF16 is the upper half of an FP32 (exact)
 float bf16_val(uint16_t r) {
-    __nv_bfloat16 b;
-    memcpy(&b, &r, 2);
-    return __bfloat162float(b);
+    const uint32_t u = (uint32_t)r << 16;
+    float v;
+    memcpy(&v, &u, 4);
+    return v;
 }
 
 }  // namespace
@@ -991,9 +993,10 @@ static sst_status tc_contract(sst_tc_plan_t t, const float *x, cudaStream_t st) 
     const bool tf32 = t->form == SST_FORM_TF32;
     const int blocks = (int)std::min<int64_t>((t->xlen + 255) / 256, 4096);
     SST_LAUNCHED_K(PK_OTHER, st,
-                   (k_tc_prep_x<<<blocks, 256, 0, st>>>(x, d.n, d.M, t->xlen, tf32 ? 1 : 0, (__nv_bfloat16 *)t->xp0,
-                                                        (__nv_bfloat16 *)t->xp1, (float *)t->xp0,
-                                                        (unsigned *)t->partial),
+                   (k_tc_prep_x<<<blocks, 256, 0, st>>>(x, d.n, d.M, t->xlen, tf32 ? 1 : 0,
+                                                        tf32 ? nullptr : (__nv_bfloat16 *)t->xp0,
+                                                        tf32 ? nullptr : (__nv_bfloat16 *)t->xp1,
+                                                        tf32 ? (float *)t->xp0 : nullptr, (unsigned *)t->partial),
                     cudaGetLastError()),
                    "tensor-form signal prep");
     if (!t->hankel) {
