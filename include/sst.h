@@ -481,7 +481,13 @@ sst_status sst_sync(void *stream);
  * entry points, all threads). */
 uint64_t sst_launch_count(void);
 
-/* Per-kernel timing.  While enabled, each kernel launch of this library is
+/* Tracing: every call that launches work (the transforms, the split-signal
+ * parts, the batch and service calls, the post steps, plan creation, the
+ * tensor form) opens an NVTX range named as the call for its duration, so a
+ * timeline tool shows the calls above their kernels; without such a tool
+ * attached NVTX does nothing.
+ *
+ * Per-kernel timing.  While enabled, each kernel launch of this library is
  * bracketed by two CUDA events recorded on the launch's own stream;
  * sst_profile_collect waits for them, adds the elapsed times per kernel kind
  * into ms[kind] and counts[kind] (arrays of SST_PROFILE_KINDS entries),

@@ -407,6 +407,7 @@ void cache_store_file(const std::string &sig, const Knobs &k) {
 }  // namespace
 
 SST_API sst_status sst_batch_create(const sst_batch_item *items, int32_t count, uint32_t flags, sst_batch_t *out) {
+    SST_NVTX_RANGE();
     if (!out) return fail(SST_EINVAL, "out is NULL");
     *out = nullptr;
     if (!items || count < 1) return fail(SST_EINVAL, "need at least one batch item");
@@ -465,6 +466,7 @@ SST_API sst_status sst_batch_workspace(sst_batch_t b, size_t *bytes) {
 }
 
 SST_API sst_status sst_batch_run(sst_batch_t b, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     if (!b) return fail(SST_EINVAL, "batch is NULL");
     if (!ws || (((uintptr_t)ws) & 255)) return fail(SST_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     int dev = -1;
@@ -474,6 +476,7 @@ SST_API sst_status sst_batch_run(sst_batch_t b, void *ws, void *stream) {
 }
 
 SST_API sst_status sst_batch_tune(sst_batch_t b, void *ws, void *stream, double *untuned_ms, double *tuned_ms) {
+    SST_NVTX_RANGE();
     if (!b) return fail(SST_EINVAL, "batch is NULL");
     if (!ws || (((uintptr_t)ws) & 255)) return fail(SST_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
@@ -564,6 +567,7 @@ SST_API void sst_batch_destroy(sst_batch_t b) {
 
 SST_API sst_status sst_batch_submit(const sst_batch_item *items, int32_t count, void *ws, size_t ws_bytes,
                                     void *stream) {
+    SST_NVTX_RANGE();
     sst_batch_t b = nullptr;
     sst_status s = sst_batch_create(items, count, 0, &b);
     if (s != SST_OK) return s;

@@ -395,6 +395,7 @@ static sst_status validate(const sst_params *p) {
 }
 
 SST_API sst_status sst_plan_create(const sst_params *params, sst_plan_t *out) {
+    SST_NVTX_RANGE();
     if (!out) return fail(SST_EINVAL, "out is NULL");
     *out = nullptr;
     sst_status st = validate(params);
@@ -1033,6 +1034,7 @@ static sst_status run_inverse(sst_plan_t pl, const float *tfr, float *xhat, void
 
 
 SST_API sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
@@ -1043,6 +1045,7 @@ SST_API sst_status sst_forward(sst_plan_t plan, const float *x_dev, int64_t n, f
 
 SST_API sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n, float *xhat_dev, void *ws,
                                void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, tfr_dev, n, ws);
     if (s != SST_OK) return s;
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
@@ -1053,6 +1056,7 @@ SST_API sst_status sst_inverse(sst_plan_t plan, const float *tfr_dev, int64_t n,
 
 SST_API sst_status sst_inverse_zone(sst_plan_t plan, const float *tfr_dev, int64_t n, const int32_t *ridge_dev,
                                     int32_t half_width, float *xhat_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, tfr_dev, n, ws);
     if (s != SST_OK) return s;
     if (!xhat_dev) return fail(SST_EINVAL, "xhat pointer is NULL");
@@ -1143,11 +1147,13 @@ static sst_status forward_inverse_to(sst_plan_t plan, const float *x_dev, int64_
 
 SST_API sst_status sst_forward_inverse(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
                                        float *xhat_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     return forward_inverse_to(plan, x_dev, n, tfr_dev, xhat_dev, nullptr, ws, stream);
 }
 
 SST_API sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host, int64_t n, float *xhat_host,
                                             float *x_dev, float *tfr_dev, float *xhat_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     if (!x_host || !xhat_host) return fail(SST_EINVAL, "host pointer is NULL");
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
@@ -1173,6 +1179,7 @@ SST_API sst_status sst_forward_inverse_host(sst_plan_t plan, const float *x_host
 
 SST_API sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, float *V_dev, float *Vd_dev, void *ws,
                             void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!V_dev || !Vd_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1185,6 +1192,7 @@ SST_API sst_status sst_stft(sst_plan_t plan, const float *x_dev, int64_t n, floa
 
 SST_API sst_status sst_reassign_map(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
                                     int32_t *dest_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1231,6 +1239,7 @@ static sst_status run_forward_so(sst_plan_t pl, int kind, const float *x, void *
 
 SST_API sst_status sst_forward2(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev, void *ws,
                                 void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
@@ -1239,6 +1248,7 @@ SST_API sst_status sst_forward2(sst_plan_t plan, const float *x_dev, int64_t n, 
 
 SST_API sst_status sst_reassign_map2(sst_plan_t plan, const float *x_dev, int64_t n, float *omega_dev,
                                      int32_t *dest_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1247,6 +1257,7 @@ SST_API sst_status sst_reassign_map2(sst_plan_t plan, const float *x_dev, int64_
 
 SST_API sst_status sst_max_abs_v(sst_plan_t plan, const float *x_dev, int64_t n, float *maxv_dev, void *ws,
                                  void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = check_call(plan, x_dev, n, ws);
     if (s != SST_OK) return s;
     if (!maxv_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1325,6 +1336,7 @@ SST_API sst_status sst_part_segments(sst_plan_t plan, size_t *ola_offset, int32_
 
 SST_API sst_status sst_part_prepass(sst_plan_t plan, const sst_part *part, const float *x_dev, float *r_dev,
                                     void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = part_check(plan, part, ws);
     if (s != SST_OK) return s;
     if (!r_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1360,6 +1372,7 @@ SST_API sst_status sst_part_prepass(sst_plan_t plan, const sst_part *part, const
 
 SST_API sst_status sst_part_forward_inverse(sst_plan_t plan, const sst_part *part, const float *x_dev,
                                             const float *r_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = part_check(plan, part, ws);
     if (s != SST_OK) return s;
     if (!r_dev) return fail(SST_EINVAL, "pre-pass maximum pointer is NULL");
@@ -1385,6 +1398,7 @@ SST_API sst_status sst_part_forward_inverse(sst_plan_t plan, const sst_part *par
 
 SST_API sst_status sst_part_finalize(sst_plan_t plan, const sst_part *part, void *ws, float *xhat_dev,
                                      void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = part_check(plan, part, ws);
     if (s != SST_OK) return s;
     if (part->out_end < part->out_begin || part->out_begin < 0 || part->out_end > plan->d.n)
@@ -1429,6 +1443,7 @@ static sst_status static_scratch_address(int dev, float **out) {
 
 SST_API sst_status sst_forward_static(sst_plan_t plan, const float *x_dev, int64_t n, float *tfr_dev,
                                       void *stream) {
+    SST_NVTX_RANGE();
     if (!plan) return fail(SST_EINVAL, "plan is NULL");
     if (!x_dev || !tfr_dev) return fail(SST_EINVAL, "input or output pointer is NULL");
     if (n != plan->d.n)
@@ -1461,6 +1476,7 @@ SST_API sst_status sst_test_static_capacity(size_t floats) {
 }
 
 SST_API sst_status sst_check(sst_plan_t plan, const void *ws, void *stream) {
+    SST_NVTX_RANGE();
     if (!plan || !ws) return fail(SST_EINVAL, "plan or workspace is NULL");
     SST_CU(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronise");
     unsigned w = 0;
@@ -1550,6 +1566,7 @@ SST_API sst_status sst_fp32_peak(double *tflops, void *stream) {
 }
 
 SST_API sst_status sst_sync(void *stream) {
+    SST_NVTX_RANGE();
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
     return SST_OK;

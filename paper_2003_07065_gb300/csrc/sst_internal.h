@@ -6,6 +6,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sst.h"
 #include "sst_dev.h"
 #include "sst_launch.h"
@@ -17,6 +19,16 @@
 #define SST_SHARED __attribute__((visibility("default")))
 
 namespace sst {
+
+// An NVTX range over one C-ABI call, named as the call, for timeline tools
+// (Nsight Systems); NVTX does nothing unless such a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define SST_NVTX_RANGE() ::sst::NvtxRange sst_nvtx_range_(__func__)
 
 // error reporting: sets the thread-local message returned by sst_last_error
 SST_SHARED sst_status fail(sst_status s, const char *fmt, ...);

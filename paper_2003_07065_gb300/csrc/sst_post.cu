@@ -236,6 +236,7 @@ using namespace sst;
 
 SST_API sst_status sst_ridge(const float *tfr_dev, int64_t frames, int32_t bins, int32_t l_lo, int32_t l_hi,
                              int32_t smooth, int32_t *ridge_dev, void *stream) {
+    SST_NVTX_RANGE();
     if (!tfr_dev || !ridge_dev) return fail(SST_EINVAL, "tfr or ridge pointer is NULL");
     if (((uintptr_t)tfr_dev) & 7) return fail(SST_EINVAL, "tfr must be 8-byte aligned");
     if (((uintptr_t)ridge_dev) & 3) return fail(SST_EINVAL, "ridge must be 4-byte aligned");
@@ -272,6 +273,7 @@ SST_API size_t sst_renyi_workspace_bytes(void) { return 256 + sizeof(RenyiPart) 
 
 SST_API sst_status sst_renyi(const float *tfr_dev, int64_t rows, int32_t cols, int64_t ld, double alpha, double cell,
                              double *out_dev, void *ws, void *stream) {
+    SST_NVTX_RANGE();
     if (!tfr_dev || !out_dev || !ws) return fail(SST_EINVAL, "tfr, out or workspace pointer is NULL");
     if (((uintptr_t)tfr_dev) & 7) return fail(SST_EINVAL, "tfr must be 8-byte aligned");
     if (((uintptr_t)out_dev) & 7) return fail(SST_EINVAL, "out must be 8-byte aligned");

@@ -173,6 +173,7 @@ SST_API sst_status sst_service_create(int32_t max_streams, size_t mem_budget, ss
 
 SST_API sst_status sst_stream_open(sst_service_t sv, const sst_params *params, float amp_bound, int64_t max_chunk,
                                    int32_t *id) {
+    SST_NVTX_RANGE();
     if (!sv || !params || !id) return fail(SST_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (params->flags & SST_GAMMA_RELATIVE)
@@ -311,6 +312,7 @@ SST_API sst_status sst_stream_close(sst_service_t sv, int32_t id) {
 }
 
 SST_API sst_status sst_service_tick(sst_service_t sv) {
+    SST_NVTX_RANGE();
     if (!sv) return fail(SST_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(sv->mu);
     int dev = -1;
@@ -553,6 +555,7 @@ SST_API sst_status sst_service_tick(sst_service_t sv) {
 SST_API sst_status sst_stream_poll(sst_service_t sv, int32_t id, float *tfr_host, int64_t max_cols, int64_t *cols,
                                    int64_t *first_col, float *xhat_host, int64_t max_samples, int64_t *samples,
                                    int64_t *first_sample, int32_t *finished) {
+    SST_NVTX_RANGE();
     if (!sv) return fail(SST_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(sv->mu);
     if (id < 0 || id >= sv->max_streams || !sv->s[id].used) return fail(SST_EINVAL, "no open stream %d", id);

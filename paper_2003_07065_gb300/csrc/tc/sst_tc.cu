@@ -822,6 +822,7 @@ float bf16_val(uint16_t r) {
 }  // namespace
 
 SST_API sst_status sst_tc_plan_create(sst_plan_t base, int32_t form, sst_tc_plan_t *out) {
+    SST_NVTX_RANGE();
     if (!out) return fail(SST_EINVAL, "out is NULL");
     *out = nullptr;
     if (!base) return fail(SST_EINVAL, "base plan is NULL");
@@ -1048,6 +1049,7 @@ SST_API sst_status sst_tc_plan_test_withhold(sst_tc_plan_t t) {
 
 SST_API sst_status sst_tc_plan_tune(sst_tc_plan_t t, const float *x_dev, int64_t n, void *stream, int32_t *cluster,
                                     float *ms_out) {
+    SST_NVTX_RANGE();
     if (!t) return fail(SST_EINVAL, "plan is NULL");
     if (!x_dev) return fail(SST_EINVAL, "input pointer is NULL");
     if (n != t->base->d.n) return fail(SST_EINVAL, "n = %lld differs from the plan's n", (long long)n);
@@ -1111,6 +1113,7 @@ SST_API sst_status sst_tc_plan_set_cluster(sst_tc_plan_t t, int32_t cluster) {
 }
 
 SST_API sst_status sst_tc_check(sst_tc_plan_t t, void *stream) {
+    SST_NVTX_RANGE();
     if (!t) return fail(SST_EINVAL, "plan is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     int h = 0;
@@ -1167,6 +1170,7 @@ static sst_status tc_check(sst_tc_plan_t t, const void *x, int64_t n) {
 }
 
 SST_API sst_status sst_tc_forward(sst_tc_plan_t t, const float *x_dev, int64_t n, float *tfr_dev, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = tc_check(t, x_dev, n);
     if (s != SST_OK) return s;
     if (!tfr_dev) return fail(SST_EINVAL, "tfr pointer is NULL");
@@ -1179,6 +1183,7 @@ SST_API sst_status sst_tc_forward(sst_tc_plan_t t, const float *x_dev, int64_t n
 
 SST_API sst_status sst_tc_stft(sst_tc_plan_t t, const float *x_dev, int64_t n, float *V_dev, float *Vd_dev,
                                void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = tc_check(t, x_dev, n);
     if (s != SST_OK) return s;
     if (!V_dev || !Vd_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1190,6 +1195,7 @@ SST_API sst_status sst_tc_stft(sst_tc_plan_t t, const float *x_dev, int64_t n, f
 
 SST_API sst_status sst_tc_reassign_map(sst_tc_plan_t t, const float *x_dev, int64_t n, float *omega_dev,
                                        int32_t *dest_dev, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = tc_check(t, x_dev, n);
     if (s != SST_OK) return s;
     if (!omega_dev || !dest_dev) return fail(SST_EINVAL, "output pointer is NULL");
@@ -1202,6 +1208,7 @@ SST_API sst_status sst_tc_reassign_map(sst_tc_plan_t t, const float *x_dev, int6
 
 // the contraction alone (for timing): enqueue only, no synchronisation
 SST_API sst_status sst_tc_contract(sst_tc_plan_t t, const float *x_dev, int64_t n, void *stream) {
+    SST_NVTX_RANGE();
     sst_status s = tc_check(t, x_dev, n);
     if (s != SST_OK) return s;
     return tc_contract(t, x_dev, (cudaStream_t)stream);
